@@ -1,0 +1,358 @@
+"""Benchmark of the GB300 two-phase SpGEMM.
+
+Default workload (one GPU): C = A*A with A the 3D 27-point stencil on a 100^3
+grid (1,000,000 rows, 26,463,592 nonzeros, values 26 / -1), C 120,553,784
+nonzeros, 704,969,000 multiply-adds.  One step = symbolic phase + numeric phase
+(row analysis, binning, per-bin symbolic kernels, row-pointer scan, value split,
+per-bin numeric kernels with sorted output).  Metric: GFLOP/s with
+GFLOP = 2 * multiply-adds.  Inputs (A: 318 MB) are larger than L2 (129 MB), so
+no flush is needed between steps.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (the
+reference arm: a plain single-threaded Gustavson on the host cores, on a
+bounded sample of the same workload).  Under torchrun with N > 1 every rank
+runs an independent replica (the workload does not shard on one product);
+rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "stencil3d27_100"
+WORKLOAD_DESC = ("C=A*A, A = 3D 27-point stencil on 100^3 (1,000,000 rows, 26,463,592 nnz, "
+                 "26/-1), CSR int32/f64; C 120,553,784 nnz")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(m, n, nnz_a, nnz_b, nnz_c):
+    """Compulsory traffic (each input array read once, each output written once)
+    with int64 C row pointers: symbolic reads A and B structure and writes C's
+    row pointers; numeric reads A, B (structure + values) and C's row pointers
+    and writes C's columns and values."""
+    sym = 4 * (m + 1) + 4 * nnz_a + 4 * (n + 1) + 4 * nnz_b + 8 * (m + 1)
+    num = 12 * nnz_a + 4 * (m + 1) + 12 * nnz_b + 4 * (n + 1) + 8 * (m + 1) + 12 * nnz_c
+    return sym, num
+
+
+def cpu_oracle_rate(A, B, madds_per_row, budget_s: float):
+    """Times the CPU oracle on consecutive row blocks of the workload until about
+    budget_s seconds of work; returns (GFLOP/s, rows, seconds)."""
+    import oracle
+    m = A.m
+    block = max(1, m // 64)
+    done_rows, done_flops, t_total = 0, 0, 0.0
+    r0 = 0
+    while t_total < budget_s and done_rows < m:
+        r1 = min(m, r0 + block)
+        t = time.perf_counter()
+        oracle.spgemm(A, B, r0, r1)
+        t_total += time.perf_counter() - t
+        done_flops += int(madds_per_row[r0:r1].sum())
+        done_rows += r1 - r0
+        r0 = r1 % m
+    return 2.0 * done_flops / t_total / 1e9, done_rows, t_total
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle (plain single-threaded Gustavson)."""
+    if rank != 0:
+        return
+    from paper_2103_11991_gb300 import inputs as I
+    import oracle
+    d = I.config_inputs(WORKLOAD)
+    A, B = d["A"], d["B"]
+    flops_row = oracle.row_flops(A, B)
+    m = A.m
+    sample_rows = max(1, m // 32)  # ~0.15 s of oracle work per step on one core
+    for _ in range(args.warmup):
+        oracle.spgemm(A, B, 0, sample_rows)
+    times, madds = [], 0
+    r0 = 0
+    for _ in range(args.steps):
+        r1 = min(m, r0 + sample_rows)
+        t = time.perf_counter()
+        oracle.spgemm(A, B, r0, r1)
+        times.append(time.perf_counter() - t)
+        madds += int(flops_row[r0:r1].sum())
+        r0 = r1 if r1 < m else 0
+    total = sum(times)
+    value = 2.0 * madds / total / 1e9
+    out = {
+        "impl": "reference", "metric": "spgemm_gflops", "value": value, "unit": "GFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC,
+                   "sample": f"{sample_rows} consecutive rows per step"},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample_rows} rows of {m} per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2103_11991_gb300 import inputs as I
+    from paper_2103_11991_gb300 import spgemm as K
+
+    torch.cuda.set_device(local_rank)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    d = I.config_inputs(WORKLOAD)
+    A, B = d["A"], d["B"]
+    dA, dB = K.DeviceCSR.from_host(A), K.DeviceCSR.from_host(B)
+    op = K.SpGEMM()
+    # warm-up (also sizes the handle's scratch and C)
+    rp, nnz = op.symbolic(dA, dB)
+    ci, va = op.numeric(dA, dB, rp, nnz)
+    for _ in range(max(0, args.warmup - 1)):
+        rp, nnz = op.symbolic(dA, dB)
+        op.numeric(dA, dB, rp, nnz, ci, va)
+    op.sync()
+    st = op.stats()
+    madds = st["flops"]
+
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local_rank)
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        rp, nnz = op.symbolic(dA, dB)
+        op.numeric(dA, dB, rp, nnz, ci, va)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    op.sync()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+        tdist.barrier()
+    value = 2.0 * madds * world / (ms * 1e-3) / 1e9
+
+    # per-kernel durations on the launching stream (separate, timed handle)
+    top = K.SpGEMM(timing=1)
+    for _ in range(2):
+        trp, tnnz = top.symbolic(dA, dB)
+        tci, tva = top.numeric(dA, dB, trp, tnnz)
+    top.kernel_times(reset=True)
+    reps = 5
+    for _ in range(reps):
+        trp, tnnz = top.symbolic(dA, dB)
+        top.numeric(dA, dB, trp, tnnz, tci, tva)
+    kt = top.kernel_times()
+    launches_per_step = top.stats()["launches_sym"] + top.stats()["launches_num"]
+    top.close()
+    del tci, tva, trp
+
+    sym_b, num_b = algorithmic_bytes(A.m, B.m, A.nnz, B.nnz, nnz)
+    dom_name, (dom_ms, dom_n) = max(kt.items(), key=lambda kv: kv[1][0])
+    dom_avg_ms = dom_ms / dom_n
+    num_kernels = {k: v for k, v in kt.items() if k.startswith("num_")}
+    sym_kernels = {k: v for k, v in kt.items() if k.startswith("sym_")}
+    # For this workload every numeric row falls in the dominant numeric kind, so
+    # its algorithmic bytes per step are the numeric phase's; likewise symbolic.
+    if dom_name.startswith("num_") and len(num_kernels) == 1:
+        per_step_bytes = num_b
+    elif dom_name.startswith("sym_") and len(sym_kernels) == 1:
+        per_step_bytes = sym_b
+    else:
+        per_step_bytes = None
+    peak, peak_kind = _peaks()
+    launches_of_dom_per_step = dom_n / reps
+    if per_step_bytes is not None:
+        achieved = (per_step_bytes / launches_of_dom_per_step) / (dom_avg_ms * 1e-3) / 1e9
+    else:
+        achieved = None
+    roofline = {
+        "bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
+        "peak_kind": peak_kind, "unit": "GB/s",
+        "frac": (achieved / peak) if achieved else None, "traffic": args.traffic,
+        "algorithmic_bytes_per_launch": (per_step_bytes / launches_of_dom_per_step) if per_step_bytes else None,
+        "avg_launch_ms": dom_avg_ms,
+        "step_frac": (sym_b + num_b) / (ms * 1e-3) / 1e9 / peak,
+    }
+    kernels = {k: {"ms_per_step": v[0] / reps, "launches_per_step": v[1] / reps} for k, v in kt.items()}
+
+    # end to end through the API with host buffers: H2D of A (pinned), both
+    # phases, D2H of C (row pointers, columns, values)
+    hA = {k: torch.from_numpy(np.ascontiguousarray(getattr(A, k))).pin_memory()
+          for k in ("rowptr", "colind", "vals")}
+    hC_rp = torch.empty(A.m + 1, dtype=torch.int64).pin_memory()
+    hC_ci = torch.empty(nnz, dtype=torch.int32).pin_memory()
+    hC_va = torch.empty(nnz, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    h2d = sum(t.numel() * t.element_size() for t in hA.values())
+    d2h = (hC_rp.numel() * 8) + nnz * 12
+
+    def e2e_step():
+        gA = K.DeviceCSR(A.m, A.n, hA["rowptr"].cuda(non_blocking=True),
+                         hA["colind"].cuda(non_blocking=True), hA["vals"].cuda(non_blocking=True))
+        grp, gnnz = op.symbolic(gA, gA)
+        gci, gva = op.numeric(gA, gA, grp, gnnz, ci, va)
+        hC_rp.copy_(grp, non_blocking=True)
+        hC_ci.copy_(gci, non_blocking=True)
+        hC_va.copy_(gva, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = 2.0 * madds * world / (e2e_ms * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        flops_row = None
+        import oracle
+        flops_row = oracle.row_flops(A, B)
+        rate, rows, secs = cpu_oracle_rate(A, B, flops_row, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"{rows} rows of {A.m} (consecutive blocks), {secs:.1f} s single-threaded"}
+
+    if rank == 0:
+        out = {
+            "metric": "spgemm_gflops", "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "nnz_c": nnz,
+                       "madds": madds, "l2": "inputs larger than L2 (A 318 MB); no flush",
+                       "arith": {1: "fp64", 2: "df32"}.get(op.last_arith(), "?"),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(round(launches_per_step)) * args.steps,
+            "clocks": clk,
+            "kernels": kernels,
+            "hbm_gbs_step": (sym_b + num_b) / (ms * 1e-3) / 1e9,
+        }
+        print(json.dumps(out), flush=True)
+    op.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu DRAM bytes per launch of the dominant kernel, if captured")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

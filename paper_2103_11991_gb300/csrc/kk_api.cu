@@ -1,0 +1,917 @@
+// C ABI and host orchestration of the two-phase SpGEMM (Kokkos Kernels paper,
+// Sec. "Standard SpGEMM Kernel"): allocate C's row pointers, symbolic phase,
+// nnz(C) to the host, then the numeric phase into caller-allocated arrays.
+//
+// Symbolic call sequence on the handle's stream:
+//   analyze B (strictly ascending rows?, column range)  ->  analyze A (per-row
+//   flop bound sum_{j in A(i,:)} nnz(B(j,:)), column range, bin id)  ->  stable
+//   binning of rows  ->  [sync: bin sizes]  ->  one symbolic kernel per non-empty
+//   bin  ->  exclusive scan of the counts into C's int64 row pointers, fused with
+//   the numeric bin id (from nnz(C(i,:)))  ->  stable binning  ->  [sync: nnz(C),
+//   bin sizes].
+// Numeric call sequence: split B's values into DF32 pairs (range-checked), one
+// numeric kernel per non-empty bin.  No host synchronisation.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kk_internal.h"
+#include "kk_device.cuh"
+
+namespace kk {
+
+// ---------------------------------------------------------------------------
+// Kernel timer
+// ---------------------------------------------------------------------------
+struct KernelTimer {
+  struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  std::vector<const char*> names;
+  std::vector<double> total_ms;
+  std::vector<long long> launches;
+  cudaEvent_t take() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void collect() {
+    for (auto& r : pending) {
+      cudaEventSynchronize(r.b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      size_t k = 0;
+      for (; k < names.size(); ++k)
+        if (std::strcmp(names[k], r.name) == 0) break;
+      if (k == names.size()) {
+        names.push_back(r.name);
+        total_ms.push_back(0.0);
+        launches.push_back(0);
+      }
+      total_ms[k] += ms;
+      launches[k] += 1;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+  }
+  ~KernelTimer() {
+    for (auto& r : pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+void timer_begin(KernelTimer* t, cudaStream_t s, const char* name) {
+  if (!t) return;
+  KernelTimer::Rec r{name, t->take(), t->take()};
+  cudaEventRecord(r.a, s);
+  t->pending.push_back(r);
+}
+
+void timer_end(KernelTimer* t, cudaStream_t s) {
+  if (!t || t->pending.empty()) return;
+  cudaEventRecord(t->pending.back().b, s);
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Grow-only device buffer
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    size_t b = need < 256 ? 256 : need;
+    b += b / 4;  // slack for growth
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = b;
+    return cudaSuccess;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+constexpr int kMaxBins = 32;
+constexpr uint8_t kSkipBin = 0xFF;
+
+// Device-side classifier: first bin whose hi bound covers q and whose mode
+// (0 = vector only, 1 = flattened only, 2 = either) admits the row's mode.
+struct BinTable {
+  int32_t nb;
+  long long hi[kMaxBins];
+  int32_t mode[kMaxBins];
+};
+
+__device__ __forceinline__ uint8_t classify(const BinTable& t, long long q, int flat) {
+  if (q <= 0) return kSkipBin;
+  for (int b = 0; b < t.nb; ++b)
+    if (q <= t.hi[b] && (t.mode[b] == 2 || t.mode[b] == flat)) return (uint8_t)b;
+  return (uint8_t)(t.nb - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Analysis kernels
+// ---------------------------------------------------------------------------
+constexpr int kAnaTeam = 8;
+
+// B rows: strictly ascending columns?  column range [0, k)?
+__global__ void k_analyze_b(CsrView B, int32_t* sorted_flag, int* status) {
+  const int tl = threadIdx.x % kAnaTeam;
+  const unsigned mask = team_mask<kAnaTeam>();
+  const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kAnaTeam;
+  const long long nteams = (long long)gridDim.x * blockDim.x / kAnaTeam;
+  int unsorted = 0, bad = 0;
+  if (team0 == 0 && tl == 0 && B.rowptr[0] != 0) bad = 1;
+  for (long long r = team0; r < B.m; r += nteams) {
+    const int bs = B.rowptr[r], be = B.rowptr[r + 1];
+    if (bs < 0 || be < bs || be > B.nnz) {
+      bad = 1;
+      continue;
+    }
+    for (int q = bs + tl; q < be; q += kAnaTeam) {
+      const int c = B.colind[q];
+      if ((unsigned)c >= (unsigned)B.n) bad = 1;
+      if (q > bs && B.colind[q - 1] >= c) unsorted = 1;
+    }
+  }
+  unsorted = __any_sync(0xffffffffu, unsorted);
+  bad = __any_sync(0xffffffffu, bad);
+  (void)mask;
+  if ((threadIdx.x & 31) == 0) {
+    if (unsorted) atomicAnd(sorted_flag, 0);
+    if (bad) set_status(status, KK_ERR_BAD_INDEX);
+  }
+}
+
+// A rows: flop bound, column range, symbolic bin id; optional total flops.
+__global__ void k_analyze_a(CsrView A, const int32_t* __restrict__ brp, int32_t nb_rows,
+                            BinTable tab, int32_t vec_min_len, long long* __restrict__ flop,
+                            uint8_t* __restrict__ bin, unsigned long long* total_flop,
+                            int* status) {
+  const int tl = threadIdx.x % kAnaTeam;
+  const unsigned mask = team_mask<kAnaTeam>();
+  const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kAnaTeam;
+  const long long nteams = (long long)gridDim.x * blockDim.x / kAnaTeam;
+  const long long iters = (A.m + nteams - 1) / nteams;
+  unsigned long long acc = 0;
+  for (long long it = 0; it < iters; ++it) {
+    const long long r = team0 + it * nteams;
+    long long f = 0;
+    int bad = 0;
+    int pa = 0, pe = 0;
+    if (r < A.m) {
+      pa = A.rowptr[r];
+      pe = A.rowptr[r + 1];
+      if (pa < 0 || pe < pa || pe > A.nnz || (r == 0 && pa != 0)) {
+        bad = 1;
+        pe = pa;
+      }
+      for (int p = pa + tl; p < pe; p += kAnaTeam) {
+        const int j = A.colind[p];
+        if ((unsigned)j >= (unsigned)nb_rows) {
+          bad = 1;
+          continue;
+        }
+        f += brp[j + 1] - brp[j];
+      }
+    }
+#pragma unroll
+    for (int o = kAnaTeam / 2; o > 0; o >>= 1) f += __shfl_xor_sync(mask, f, o, kAnaTeam);
+    if (bad) set_status(status, KK_ERR_BAD_INDEX);
+    if (r < A.m && tl == 0) {
+      flop[r] = f;
+      const int flat = (f < (long long)vec_min_len * (pe - pa)) ? 1 : 0;
+      bin[r] = classify(tab, f, flat);
+      acc += (unsigned long long)f;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total_flop, acc);
+}
+
+// ---------------------------------------------------------------------------
+// Stable binning: rows grouped by bin id, ascending row order within a bin.
+// ---------------------------------------------------------------------------
+constexpr int kBinBlock = 256;
+constexpr int kBinPerThread = 8;
+constexpr int kBinRows = kBinBlock * kBinPerThread;
+
+__global__ void __launch_bounds__(kBinBlock)
+k_bin_count(int32_t m, const uint8_t* __restrict__ bin, int32_t nb, int32_t nblk,
+            int32_t* __restrict__ blk_counts) {
+  __shared__ int c[kMaxBins];
+  if (threadIdx.x < kMaxBins) c[threadIdx.x] = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * kBinRows;
+  for (int t = 0; t < kBinPerThread; ++t) {
+    const long long r = base + t * kBinBlock + threadIdx.x;
+    if (r < m) {
+      const uint8_t b = bin[r];
+      if (b != kSkipBin) atomicAdd(&c[b], 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nb) blk_counts[(long long)threadIdx.x * nblk + blockIdx.x] = c[threadIdx.x];
+}
+
+// Single CTA: exclusive scan (bin-major) of the per-block counts in place;
+// bin_start[b] = first position of bin b, bin_start[nb] = total.
+__global__ void __launch_bounds__(1024)
+k_bin_scan(int32_t nb, int32_t nblk, int32_t* __restrict__ blk, int32_t* __restrict__ bin_start) {
+  __shared__ int warp_tot[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const long long total = (long long)nb * nblk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long long c0 = 0; c0 < total; c0 += blockDim.x) {
+    const long long idx = c0 + threadIdx.x;
+    const int v = idx < total ? blk[idx] : 0;
+    int incl = team_inclusive_scan<32>(v, lane, 0xffffffffu);
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const int w = warp_tot[lane];
+      const int wi = team_inclusive_scan<32>(w, lane, 0xffffffffu);
+      warp_tot[lane] = wi - w;
+    }
+    __syncthreads();
+    const int excl = carry + warp_tot[warp] + incl - v;
+    if (idx < total) {
+      blk[idx] = excl;
+      if (idx % nblk == 0) bin_start[idx / nblk] = excl;
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bin_start[nb] = carry;
+}
+
+__global__ void __launch_bounds__(kBinBlock)
+k_bin_scatter(int32_t m, const uint8_t* __restrict__ bin, int32_t nb, int32_t nblk,
+              const int32_t* __restrict__ blk_off, int32_t* __restrict__ rows_out) {
+  constexpr int NW = kBinBlock / 32;
+  __shared__ int wcount[NW][kMaxBins];
+  __shared__ int running[kMaxBins];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < NW * kMaxBins; t += blockDim.x) (&wcount[0][0])[t] = 0;
+  if (threadIdx.x < nb) running[threadIdx.x] = blk_off[(long long)threadIdx.x * nblk + blockIdx.x];
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * kBinRows;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int t = 0; t < kBinPerThread; ++t) {
+    const long long r = base + t * kBinBlock + threadIdx.x;
+    const int b = r < m ? (int)bin[r] : (int)kSkipBin;
+    const unsigned same = __match_any_sync(0xffffffffu, b);
+    const int rank = __popc(same & lt);
+    if (b != kSkipBin && rank == 0) wcount[warp][b] = __popc(same);
+    __syncthreads();
+    if (b != kSkipBin) {
+      int pre = running[b];
+      for (int w = 0; w < warp; ++w) pre += wcount[w][b];
+      rows_out[pre + rank] = (int32_t)r;
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) {
+      int s = 0;
+      for (int w = 0; w < NW; ++w) s += wcount[w][threadIdx.x];
+      running[threadIdx.x] += s;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NW * kMaxBins; q += blockDim.x) (&wcount[0][0])[q] = 0;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Scan of row counts into int64 row pointers, fused with numeric bin ids.
+// ---------------------------------------------------------------------------
+constexpr int kScanBlock = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanRows = kScanBlock * kScanPer;
+
+__device__ __forceinline__ long long block_excl_scan_ll(long long v, long long* scratch,
+                                                        long long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  long long incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    long long w = lane < nw ? scratch[lane] : 0;
+    long long wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long u = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += u;
+    }
+    if (lane < nw) scratch[lane] = wi - w;
+    if (lane == 31) scratch[32] = wi;
+  }
+  __syncthreads();
+  const long long r = scratch[warp] + incl - v;
+  *total = scratch[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+k_scan_partial(int32_t m, const int32_t* __restrict__ cnt, long long* __restrict__ blk_sum) {
+  __shared__ long long scratch[33];
+  const long long base = (long long)blockIdx.x * kScanRows + (long long)threadIdx.x * kScanPer;
+  long long s = 0;
+  for (int t = 0; t < kScanPer; ++t)
+    if (base + t < m) s += cnt[base + t];
+  long long tot;
+  block_excl_scan_ll(s, scratch, &tot);
+  if (threadIdx.x == 0) blk_sum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024)
+k_scan_top(int32_t nblk, long long* __restrict__ blk_sum, long long* __restrict__ grand) {
+  __shared__ long long scratch[33];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < nblk; c0 += blockDim.x) {
+    const int idx = c0 + threadIdx.x;
+    const long long v = idx < nblk ? blk_sum[idx] : 0;
+    long long tot;
+    const long long ex = block_excl_scan_ll(v, scratch, &tot);
+    if (idx < nblk) blk_sum[idx] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *grand = carry;
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+k_scan_final(int32_t m, const int32_t* __restrict__ cnt, const long long* __restrict__ blk_off,
+             const long long* __restrict__ flop, const int32_t* __restrict__ arp,
+             int32_t vec_min_len, BinTable ntab, int64_t* __restrict__ rowptr,
+             uint8_t* __restrict__ nbin) {
+  __shared__ long long scratch[33];
+  const long long base = (long long)blockIdx.x * kScanRows + (long long)threadIdx.x * kScanPer;
+  int v[kScanPer];
+  long long s = 0;
+  for (int t = 0; t < kScanPer; ++t) {
+    v[t] = base + t < m ? cnt[base + t] : 0;
+    s += v[t];
+  }
+  long long tot;
+  long long run = blk_off[blockIdx.x] + block_excl_scan_ll(s, scratch, &tot);
+  for (int t = 0; t < kScanPer; ++t) {
+    const long long r = base + t;
+    if (r < m) {
+      rowptr[r] = run;
+      const int nza = arp[r + 1] - arp[r];
+      const int flat = (flop[r] < (long long)vec_min_len * nza) ? 1 : 0;
+      nbin[r] = classify(ntab, v[t], flat);
+      if (r == m - 1) rowptr[m] = run + v[t];
+    }
+    run += v[t];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// DF32 split of B's values, with the window check.
+// ---------------------------------------------------------------------------
+__global__ void k_split_values(long long n, const double* __restrict__ v, float2* __restrict__ out,
+                               int32_t* range_bad) {
+  int bad = 0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    DF d;
+    bad |= df_split(v[q], d) ? 0 : 1;
+    out[q] = make_float2(d.hi, d.lo);
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  if (bad && (threadIdx.x & 31) == 0) atomicOr(range_bad, 1);
+}
+
+}  // namespace
+}  // namespace kk
+
+using namespace kk;
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+struct kk_spgemm_handle_s {
+  cudaStream_t stream = nullptr;
+  kk_spgemm_options opt{};
+  int device = 0;
+  int num_sms = 0;
+  int max_smem = 0;
+  KernelTimer* timer = nullptr;
+  std::string last_error;
+  // scratch
+  DevBuf d_misc;       // status int, sorted flag, range flag, total flop (u64), grand total (ll)
+  DevBuf d_flop;       // long long[m]
+  DevBuf d_sbin;       // uint8[m]
+  DevBuf d_nbin;       // uint8[m]
+  DevBuf d_srows;      // int32[m]
+  DevBuf d_nrows;      // int32[m]
+  DevBuf d_cnt;        // int32[m]
+  DevBuf d_blk;        // int32[kMaxBins * nblk]
+  DevBuf d_binstart;   // int32[2 * (kMaxBins + 1)]
+  DevBuf d_scan;       // long long[nblk]
+  DevBuf d_bsplit;     // float2[nnzB]
+  void* h_pinned = nullptr;  // host staging for readbacks
+  // symbolic state
+  bool have_symbolic = false;
+  int32_t am = 0, an = 0, bn = 0, annz = 0, bnnz = 0;
+  int64_t nnz_c = 0;
+  int32_t b_sorted = 1;
+  std::vector<BinSpec> sym_bins, num_bins;
+  std::vector<int32_t> num_start;  // nb + 1
+  int64_t stats[16] = {0};
+  int32_t last_arith = kArithDF32;
+};
+
+namespace {
+
+struct Misc {
+  int status;
+  int32_t sorted;
+  int32_t range_bad;
+  int32_t pad;
+  unsigned long long total_flop;
+  long long grand;
+};
+
+kk_status fail(kk_spgemm_handle h, kk_status s, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return s;
+}
+
+kk_status cuda_fail(kk_spgemm_handle h, cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(h, KK_ERR_OOM, std::string(where) + ": " + cudaGetErrorString(e));
+  }
+  return fail(h, KK_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define KK_CUDA(h, call, where)                       \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+kk_status check_csr(kk_spgemm_handle h, const kk_csr* M, const char* name, bool need_vals) {
+  if (!M) return fail(h, KK_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  if (M->m < 0 || M->n < 0 || M->nnz < 0)
+    return fail(h, KK_ERR_INVALID_ARG, std::string(name) + ": negative size");
+  if (!M->rowptr) return fail(h, KK_ERR_INVALID_ARG, std::string(name) + ".rowptr is NULL");
+  if (M->nnz > 0 && !M->colind) return fail(h, KK_ERR_INVALID_ARG, std::string(name) + ".colind is NULL");
+  if (need_vals && M->nnz > 0 && !M->vals)
+    return fail(h, KK_ERR_INVALID_ARG, std::string(name) + ".vals is NULL");
+  return KK_OK;
+}
+
+CsrView view(const kk_csr* M) {
+  return CsrView{M->m, M->n, M->nnz, M->rowptr, M->colind, M->vals};
+}
+
+// Bin tables from the options.  Symbolic bins are keyed by the flop bound,
+// numeric bins by nnz(C(i,:)).  Team bins come in a vector and a flattened
+// flavour; the CTA and dense tiers always flatten.
+void build_bins(const kk_spgemm_options& o, bool numeric, std::vector<BinSpec>& out) {
+  out.clear();
+  const int force = o.force_tier;
+  if (!numeric) {
+    if (force < 1) {
+      for (int ls = 5; ls <= 12; ++ls) {
+        const long long S = 1ll << ls;
+        const long long hi = (S * 3) / 4;
+        if (hi > o.sym_team_max_flop && ls > 5) break;
+        out.push_back(BinSpec{kTierTeam, 32, (int)S, 0, 0, hi});
+        out.push_back(BinSpec{kTierTeam, S <= 64 ? 8 : 32, (int)S, 1, 0, hi});
+      }
+    }
+    if (force < 2) {
+      for (int ls = 13; ls <= 15; ++ls) {
+        const long long S = 1ll << ls;
+        const long long hi = (S * 3) / 4;
+        if (hi > o.sym_cta_max_flop && ls > 13) break;
+        out.push_back(BinSpec{kTierCta, 512, (int)S, 1, 0, hi});
+      }
+    }
+    out.push_back(BinSpec{kTierDense, 512, 1 << 20, 1, 0, (long long)9e18});
+  } else {
+    if (force < 1) {
+      for (int ls = 5; ls <= 11; ++ls) {
+        const long long S = 1ll << ls;
+        const long long hi = S / 2;
+        if (hi > o.num_team_max_nnz && ls > 5) break;
+        out.push_back(BinSpec{kTierTeam, 32, (int)S, 0, 0, hi});
+        out.push_back(BinSpec{kTierTeam, S <= 64 ? 8 : 32, (int)S, 1, 0, hi});
+      }
+    }
+    if (force < 2) {
+      for (int ls = 12; ls <= 13; ++ls) {
+        const long long S = 1ll << ls;
+        const long long hi = S / 2;
+        if (hi > o.num_cta_max_nnz && ls > 12) break;
+        out.push_back(BinSpec{kTierCta, 512, (int)S, 1, 0, hi});
+      }
+    }
+    out.push_back(BinSpec{kTierDense, 512, 16384, 1, 0, (long long)9e18});
+  }
+  for (size_t b = 0; b < out.size(); ++b) out[b].lo = b == 0 ? 1 : out[b - 1].hi + 1;
+}
+
+BinTable to_table(const std::vector<BinSpec>& bins) {
+  BinTable t{};
+  t.nb = (int32_t)bins.size();
+  for (size_t b = 0; b < bins.size(); ++b) {
+    t.hi[b] = bins[b].hi;
+    t.mode[b] = bins[b].tier == kTierTeam ? bins[b].flat : 2;
+  }
+  return t;
+}
+
+LaunchCtx ctx_of(kk_spgemm_handle h) {
+  return LaunchCtx{h->stream, h->timer, &h->d_misc.as<Misc>()->status, h->num_sms, h->max_smem};
+}
+
+int grid_for(long long work, int per_block, int cap) {
+  long long g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+// Stable binning of m rows by `bin` into rows_out; writes bin_start (device,
+// nb+1 entries).
+kk_status run_binning(kk_spgemm_handle h, int32_t m, const uint8_t* bin, int nb, int32_t* rows_out,
+                      int32_t* bin_start) {
+  const int nblk = (int)((m + kBinRows - 1) / kBinRows);
+  if (nblk == 0) {
+    KK_CUDA(h, cudaMemsetAsync(bin_start, 0, sizeof(int32_t) * (nb + 1), h->stream), "memset");
+    return KK_OK;
+  }
+  KK_CUDA(h, h->d_blk.ensure(sizeof(int32_t) * (size_t)nb * nblk), "alloc bins");
+  int32_t* blk = h->d_blk.as<int32_t>();
+  timer_begin(h->timer, h->stream, "binning");
+  k_bin_count<<<nblk, kBinBlock, 0, h->stream>>>(m, bin, nb, nblk, blk);
+  k_bin_scan<<<1, 1024, 0, h->stream>>>(nb, nblk, blk, bin_start);
+  k_bin_scatter<<<nblk, kBinBlock, 0, h->stream>>>(m, bin, nb, nblk, blk, rows_out);
+  timer_end(h->timer, h->stream);
+  KK_CUDA(h, cudaGetLastError(), "binning launch");
+  return KK_OK;
+}
+
+kk_status check_device_status(kk_spgemm_handle h, int status) {
+  if (status == 0) return KK_OK;
+  const char* what = "device error";
+  switch (status) {
+    case KK_ERR_BAD_INDEX: what = "a column index lies outside its range"; break;
+    case KK_ERR_CAPACITY: what = "an accumulator overflowed"; break;
+    case KK_ERR_STRUCTURE_MISMATCH: what = "the structure differs from the symbolic phase"; break;
+    case KK_ERR_TIMEOUT: what = "a bounded device wait ran out"; break;
+    default: break;
+  }
+  return fail(h, (kk_status)status, what);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* kk_status_string(kk_status s) {
+  switch (s) {
+    case KK_OK: return "KK_OK";
+    case KK_ERR_INVALID_ARG: return "KK_ERR_INVALID_ARG";
+    case KK_ERR_CUDA: return "KK_ERR_CUDA";
+    case KK_ERR_OOM: return "KK_ERR_OOM";
+    case KK_ERR_STRUCTURE_MISMATCH: return "KK_ERR_STRUCTURE_MISMATCH";
+    case KK_ERR_CAPACITY: return "KK_ERR_CAPACITY";
+    case KK_ERR_TIMEOUT: return "KK_ERR_TIMEOUT";
+    case KK_ERR_NOT_SYMBOLIC: return "KK_ERR_NOT_SYMBOLIC";
+    case KK_ERR_BAD_INDEX: return "KK_ERR_BAD_INDEX";
+  }
+  return "KK_ERR_UNKNOWN";
+}
+
+kk_status kk_spgemm_options_default(kk_spgemm_options* opt) {
+  if (!opt) return KK_ERR_INVALID_ARG;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->arith = KK_ARITH_AUTO;
+  opt->debug_checks = 0;
+  opt->timing = 0;
+  opt->force_tier = -1;
+  opt->team_vec_min_len = 12;
+  opt->sym_team_max_flop = 3072;
+  opt->sym_cta_max_flop = 24576;
+  opt->num_team_max_nnz = 1024;
+  opt->num_cta_max_nnz = 4096;
+  return KK_OK;
+}
+
+kk_status kk_spgemm_handle_create(kk_spgemm_handle* out, const kk_spgemm_options* opt,
+                                  void* cuda_stream) {
+  if (!out) return KK_ERR_INVALID_ARG;
+  *out = nullptr;
+  kk_spgemm_handle h = new (std::nothrow) kk_spgemm_handle_s();
+  if (!h) return KK_ERR_OOM;
+  if (opt) h->opt = *opt; else kk_spgemm_options_default(&h->opt);
+  if (h->opt.arith < 0 || h->opt.arith > 2 || h->opt.force_tier < -1 || h->opt.force_tier > 2 ||
+      h->opt.team_vec_min_len < 0) {
+    delete h;
+    return KK_ERR_INVALID_ARG;
+  }
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&h->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (e == cudaSuccess) e = h->d_misc.ensure(sizeof(Misc));
+  if (e == cudaSuccess) e = h->d_binstart.ensure(sizeof(int32_t) * 2 * (kMaxBins + 1));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_pinned, 4096);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_misc.p, 0, sizeof(Misc), h->stream);
+  if (e != cudaSuccess) {
+    h->d_misc.release();
+    h->d_binstart.release();
+    if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? KK_ERR_OOM : KK_ERR_CUDA;
+  }
+  if (h->opt.timing) h->timer = new (std::nothrow) KernelTimer();
+  *out = h;
+  return KK_OK;
+}
+
+kk_status kk_spgemm_set_stream(kk_spgemm_handle h, void* cuda_stream) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  return KK_OK;
+}
+
+const char* kk_spgemm_last_error(kk_spgemm_handle h) { return h ? h->last_error.c_str() : ""; }
+
+int32_t kk_spgemm_last_arith(kk_spgemm_handle h) { return h ? h->last_arith : 0; }
+
+kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[16]) {
+  if (!h || !stats) return KK_ERR_INVALID_ARG;
+  for (int i = 0; i < 16; ++i) stats[i] = h->stats[i];
+  return KK_OK;
+}
+
+kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B,
+                             int64_t* c_rowptr, int64_t* nnz_c) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  kk_status st;
+  if ((st = check_csr(h, A, "A", false)) != KK_OK) return st;
+  if ((st = check_csr(h, B, "B", false)) != KK_OK) return st;
+  if (A->n != B->m) return fail(h, KK_ERR_INVALID_ARG, "A.n != B.m");
+  if (!c_rowptr || !nnz_c) return fail(h, KK_ERR_INVALID_ARG, "c_rowptr / nnz_c is NULL");
+  h->have_symbolic = false;
+  const int32_t m = A->m;
+  const CsrView av = view(A), bv = view(B);
+  cudaStream_t s = h->stream;
+  Misc* dm = h->d_misc.as<Misc>();
+  Misc* hm = static_cast<Misc*>(h->h_pinned);
+  int32_t* h_start = reinterpret_cast<int32_t*>(static_cast<char*>(h->h_pinned) + 256);
+
+  build_bins(h->opt, false, h->sym_bins);
+  build_bins(h->opt, true, h->num_bins);
+  const int nbs = (int)h->sym_bins.size(), nbn = (int)h->num_bins.size();
+
+  KK_CUDA(h, h->d_flop.ensure(sizeof(long long) * (size_t)(m > 0 ? m : 1)), "alloc flop");
+  KK_CUDA(h, h->d_sbin.ensure((size_t)(m > 0 ? m : 1)), "alloc bins");
+  KK_CUDA(h, h->d_nbin.ensure((size_t)(m > 0 ? m : 1)), "alloc bins");
+  KK_CUDA(h, h->d_srows.ensure(sizeof(int32_t) * (size_t)(m > 0 ? m : 1)), "alloc rows");
+  KK_CUDA(h, h->d_nrows.ensure(sizeof(int32_t) * (size_t)(m > 0 ? m : 1)), "alloc rows");
+  KK_CUDA(h, h->d_cnt.ensure(sizeof(int32_t) * (size_t)(m > 0 ? m : 1)), "alloc counts");
+  const int nblk_scan = (int)((m + kScanRows - 1) / kScanRows);
+  KK_CUDA(h, h->d_scan.ensure(sizeof(long long) * (size_t)(nblk_scan > 0 ? nblk_scan : 1)), "alloc scan");
+
+  Misc init{};
+  init.sorted = 1;
+  KK_CUDA(h, cudaMemcpyAsync(dm, &init, sizeof(Misc), cudaMemcpyHostToDevice, s), "init");
+  // NOTE: &init is pageable; cudaMemcpyAsync from pageable memory is staged
+  // synchronously with respect to the host, so the stack copy is safe.
+
+  int32_t* sym_start = h->d_binstart.as<int32_t>();
+  int32_t* num_start = sym_start + (kMaxBins + 1);
+  if (m > 0) {
+    timer_begin(h->timer, s, "analyze");
+    if (bv.m > 0)
+      k_analyze_b<<<grid_for((long long)bv.m * kAnaTeam, 256, h->num_sms * 8), 256, 0, s>>>(
+          bv, &dm->sorted, &dm->status);
+    k_analyze_a<<<grid_for((long long)m * kAnaTeam, 256, h->num_sms * 8), 256, 0, s>>>(
+        av, bv.rowptr, bv.m, to_table(h->sym_bins), h->opt.team_vec_min_len,
+        h->d_flop.as<long long>(), h->d_sbin.as<uint8_t>(), &dm->total_flop, &dm->status);
+    timer_end(h->timer, s);
+    KK_CUDA(h, cudaGetLastError(), "analyze launch");
+    if ((st = run_binning(h, m, h->d_sbin.as<uint8_t>(), nbs, h->d_srows.as<int32_t>(), sym_start)) != KK_OK)
+      return st;
+  } else {
+    KK_CUDA(h, cudaMemsetAsync(sym_start, 0, sizeof(int32_t) * (nbs + 1), s), "memset");
+  }
+  KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
+  KK_CUDA(h, cudaMemcpyAsync(h_start, sym_start, sizeof(int32_t) * (nbs + 1), cudaMemcpyDeviceToHost, s),
+          "readback");
+  KK_CUDA(h, cudaStreamSynchronize(s), "sync");
+  if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
+  h->b_sorted = hm->sorted;
+  h->stats[6] = (int64_t)hm->total_flop;
+  h->stats[7] = hm->sorted;
+
+  // symbolic kernels per bin
+  if (m > 0) {
+    KK_CUDA(h, cudaMemsetAsync(h->d_cnt.p, 0, sizeof(int32_t) * (size_t)m, s), "memset counts");
+    LaunchCtx ctx = ctx_of(h);
+    int64_t tier_rows[3] = {0, 0, 0};
+    for (int b = 0; b < nbs; ++b) {
+      const int cnt = h_start[b + 1] - h_start[b];
+      if (cnt <= 0) continue;
+      tier_rows[h->sym_bins[b].tier] += cnt;
+      cudaError_t e = launch_symbolic_bin(ctx, h->sym_bins[b], av, bv, h->b_sorted,
+                                          h->d_srows.as<int32_t>() + h_start[b], cnt,
+                                          h->d_cnt.as<int32_t>());
+      if (e != cudaSuccess) return cuda_fail(h, e, "symbolic launch");
+    }
+    for (int t = 0; t < 3; ++t) h->stats[t] = tier_rows[t];
+    int64_t nb_launched = 0;
+    for (int b = 0; b < nbs; ++b) nb_launched += (h_start[b + 1] - h_start[b]) > 0 ? 1 : 0;
+    // analyze (2) + binning (3) + symbolic bins + scan (3) + numeric binning (3)
+    h->stats[8] = (bv.m > 0 ? 1 : 0) + 1 + 3 + nb_launched + 3 + 3;
+    // scan + numeric bins
+    timer_begin(h->timer, s, "scan");
+    k_scan_partial<<<nblk_scan, kScanBlock, 0, s>>>(m, h->d_cnt.as<int32_t>(), h->d_scan.as<long long>());
+    k_scan_top<<<1, 1024, 0, s>>>(nblk_scan, h->d_scan.as<long long>(), &dm->grand);
+    k_scan_final<<<nblk_scan, kScanBlock, 0, s>>>(
+        m, h->d_cnt.as<int32_t>(), h->d_scan.as<long long>(), h->d_flop.as<long long>(), av.rowptr,
+        h->opt.team_vec_min_len, to_table(h->num_bins), c_rowptr, h->d_nbin.as<uint8_t>());
+    timer_end(h->timer, s);
+    KK_CUDA(h, cudaGetLastError(), "scan launch");
+    if ((st = run_binning(h, m, h->d_nbin.as<uint8_t>(), nbn, h->d_nrows.as<int32_t>(), num_start)) != KK_OK)
+      return st;
+  } else {
+    KK_CUDA(h, cudaMemsetAsync(c_rowptr, 0, sizeof(int64_t), s), "memset rowptr");
+    KK_CUDA(h, cudaMemsetAsync(num_start, 0, sizeof(int32_t) * (nbn + 1), s), "memset");
+  }
+  KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
+  KK_CUDA(h, cudaMemcpyAsync(h_start, num_start, sizeof(int32_t) * (nbn + 1), cudaMemcpyDeviceToHost, s),
+          "readback");
+  KK_CUDA(h, cudaStreamSynchronize(s), "sync");
+  if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
+  h->nnz_c = m > 0 ? hm->grand : 0;
+  h->num_start.assign(h_start, h_start + nbn + 1);
+  int64_t ntier[3] = {0, 0, 0};
+  for (int b = 0; b < nbn; ++b) ntier[h->num_bins[b].tier] += h_start[b + 1] - h_start[b];
+  for (int t = 0; t < 3; ++t) h->stats[3 + t] = ntier[t];
+  h->am = m;
+  h->an = A->n;
+  h->bn = B->n;
+  h->annz = A->nnz;
+  h->bnnz = B->nnz;
+  h->have_symbolic = true;
+  *nnz_c = h->nnz_c;
+  return KK_OK;
+}
+
+kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B,
+                            const int64_t* c_rowptr, int32_t* c_colind, double* c_vals) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  if (!h->have_symbolic) return fail(h, KK_ERR_NOT_SYMBOLIC, "numeric before symbolic");
+  kk_status st;
+  if ((st = check_csr(h, A, "A", true)) != KK_OK) return st;
+  if ((st = check_csr(h, B, "B", true)) != KK_OK) return st;
+  if (A->m != h->am || A->n != h->an || B->n != h->bn || A->nnz != h->annz || B->nnz != h->bnnz)
+    return fail(h, KK_ERR_STRUCTURE_MISMATCH, "A/B dims or nnz differ from the symbolic call");
+  if (!c_rowptr) return fail(h, KK_ERR_INVALID_ARG, "c_rowptr is NULL");
+  if (h->nnz_c > 0 && (!c_colind || !c_vals)) return fail(h, KK_ERR_INVALID_ARG, "C arrays are NULL");
+  const CsrView av = view(A), bv = view(B);
+  cudaStream_t s = h->stream;
+  Misc* dm = h->d_misc.as<Misc>();
+  const int32_t arith = h->opt.arith == KK_ARITH_FP64 ? kArithF64 : kArithDF32;
+  h->last_arith = arith;
+  if (h->am == 0 || h->nnz_c == 0) return KK_OK;
+  const float2* bsplit = nullptr;
+  if (arith == kArithDF32) {
+    KK_CUDA(h, h->d_bsplit.ensure(sizeof(float2) * (size_t)(bv.nnz > 0 ? bv.nnz : 1)), "alloc split");
+    KK_CUDA(h, cudaMemsetAsync(&dm->range_bad, 0, sizeof(int32_t), s), "memset");
+    if (bv.nnz > 0) {
+      timer_begin(h->timer, s, "split_b");
+      k_split_values<<<grid_for(bv.nnz, 256, h->num_sms * 16), 256, 0, s>>>(
+          bv.nnz, bv.vals, h->d_bsplit.as<float2>(), &dm->range_bad);
+      timer_end(h->timer, s);
+      KK_CUDA(h, cudaGetLastError(), "split launch");
+    }
+    bsplit = h->d_bsplit.as<float2>();
+  }
+  LaunchCtx ctx = ctx_of(h);
+  const int nbn = (int)h->num_bins.size();
+  h->stats[9] = (arith == kArithDF32 && bv.nnz > 0) ? 1 : 0;
+  for (int b = 0; b < nbn; ++b) {
+    const int cnt = h->num_start[b + 1] - h->num_start[b];
+    if (cnt <= 0) continue;
+    h->stats[9] += 1;
+    cudaError_t e = launch_numeric_bin(ctx, h->num_bins[b], av, bv, h->b_sorted, bsplit,
+                                       &dm->range_bad, arith, c_rowptr,
+                                       h->d_nrows.as<int32_t>() + h->num_start[b], cnt, c_colind,
+                                       c_vals, h->opt.debug_checks);
+    if (e != cudaSuccess) return cuda_fail(h, e, "numeric launch");
+  }
+  return KK_OK;
+}
+
+kk_status kk_spgemm_sync(kk_spgemm_handle h) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  Misc* hm = static_cast<Misc*>(h->h_pinned);
+  KK_CUDA(h, cudaMemcpyAsync(hm, h->d_misc.p, sizeof(Misc), cudaMemcpyDeviceToHost, h->stream), "readback");
+  KK_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+  if (h->last_arith == kArithDF32 && hm->range_bad) h->last_arith = kArithF64;
+  const int status = hm->status;
+  if (status != 0) {
+    KK_CUDA(h, cudaMemsetAsync(&h->d_misc.as<Misc>()->status, 0, sizeof(int), h->stream), "memset");
+    KK_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+  }
+  return check_device_status(h, status);
+}
+
+kk_status kk_spgemm_kernel_times(kk_spgemm_handle h, int32_t max_kernels, const char** names,
+                                 double* total_ms, int64_t* launches, int32_t* count,
+                                 int32_t reset) {
+  if (!h || !count) return KK_ERR_INVALID_ARG;
+  *count = 0;
+  if (!h->timer) return KK_OK;
+  KK_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+  h->timer->collect();
+  const int n = (int)h->timer->names.size();
+  for (int i = 0; i < n && i < max_kernels; ++i) {
+    if (names) names[i] = h->timer->names[i];
+    if (total_ms) total_ms[i] = h->timer->total_ms[i];
+    if (launches) launches[i] = h->timer->launches[i];
+  }
+  *count = n;
+  if (reset) {
+    h->timer->names.clear();
+    h->timer->total_ms.clear();
+    h->timer->launches.clear();
+  }
+  return KK_OK;
+}
+
+kk_status kk_spgemm_destroy(kk_spgemm_handle h) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->stream);
+  delete h->timer;
+  h->d_misc.release();
+  h->d_flop.release();
+  h->d_sbin.release();
+  h->d_nbin.release();
+  h->d_srows.release();
+  h->d_nrows.release();
+  h->d_cnt.release();
+  h->d_blk.release();
+  h->d_binstart.release();
+  h->d_scan.release();
+  h->d_bsplit.release();
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  delete h;
+  return KK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,534 @@
+// Numeric phase kernels: column indices and values of C (Kokkos Kernels paper,
+// Sec. "Standard SpGEMM Kernel": the numeric phase inserts (column, value) pairs
+// into the accumulator, value := value + A(i,j) * B(j,c)).  Every row's count is
+// known from the symbolic phase, so each row's accumulator is sized from it.
+//
+// Tiers (as in the symbolic phase):
+//   team  - TEAM lanes per row: shared-memory hash map (keys, values), then a
+//           team-level bitonic sort of the occupied slots (paper, Sec. "Multi-
+//           Level Bitonic Sorting": team-level sort in shared memory) so each row
+//           is written with ascending columns;
+//   CTA   - one CTA per row, same structure with block-wide sort;
+//   dense - one CTA per row, dense value array + bit vector over a window of
+//           columns swept across [0, k); set bits are enumerated in column order,
+//           so no sort is needed.
+//
+// Arithmetic: DF32 (float64 emulated by float32 pairs on the FP32 pipe) when the
+// values of B and of the row's A entries lie in the DF32 window, native float64
+// otherwise.  In vector mode with distinct columns per B row the updates of one
+// output entry happen in A-row storage order without atomics.
+#include "kk_internal.h"
+#include "kk_visit.cuh"
+
+namespace kk {
+namespace {
+
+constexpr int kTeamBlock = 256;
+constexpr int kCtaBlock = 512;
+constexpr int kDenseBlock = 512;
+
+using u64 = unsigned long long;
+
+struct NumArgs {
+  CsrView A, B;
+  int32_t b_sorted;
+  const float2* b_split;
+  const int32_t* b_range_bad;
+  int32_t arith;
+  const int64_t* c_rowptr;
+  const int32_t* rows;
+  int32_t nrows;
+  int32_t* c_colind;
+  double* c_vals;
+  int* status;
+  int32_t k;
+  int32_t W;  // dense chunk width
+};
+
+struct FullRange {
+  const int32_t* acol;
+  const int32_t* brp;
+  __device__ __forceinline__ void operator()(int p, int& bs, int& bl) const {
+    const int j = acol[p];
+    bs = brp[j];
+    bl = brp[j + 1] - bs;
+  }
+};
+
+struct PrepF64 {
+  const double* av;
+  __device__ __forceinline__ double operator()(int p) const { return av[p]; }
+};
+struct PrepDF {
+  const double* av;
+  __device__ __forceinline__ DF operator()(int p) const {
+    DF t;
+    df_split(av[p], t);
+    return t;
+  }
+};
+
+__device__ __forceinline__ DF load_b(const float2* bs, int q) {
+  const float2 v = bs[q];
+  DF d;
+  d.hi = v.x;
+  d.lo = v.y;
+  return d;
+}
+
+// Accumulate one product into slot `slot` of a u64 value array.
+__device__ __forceinline__ void upd_df(u64* vals, int slot, DF a, DF b, bool atomic, int* status) {
+  if (atomic) {
+    df_atomic_fma(&vals[slot], a, b, status);
+  } else {
+    DF s = df_unpack(vals[slot]);
+    df_fma(s, a, b);
+    vals[slot] = df_pack(s);
+  }
+}
+__device__ __forceinline__ void upd_f64(u64* vals, int slot, double a, double b, bool atomic) {
+  double* v = reinterpret_cast<double*>(&vals[slot]);
+  if (atomic) atomicAdd(v, a * b);
+  else *v = fma(a, b, *v);
+}
+
+// True if every A value of the row lies in the DF32 window (team vote).
+template <int TEAM>
+__device__ __forceinline__ bool row_df_ok(const double* av, int pa, int pe, int tl, unsigned mask) {
+  int bad = 0;
+  for (int p = pa + tl; p < pe; p += TEAM) {
+    DF t;
+    bad |= df_split(av[p], t) ? 0 : 1;
+  }
+  return __any_sync(mask, bad) == 0;
+}
+
+__device__ __forceinline__ bool block_df_ok(const double* av, int pa, int pe, int* flag) {
+  if (threadIdx.x == 0) *flag = 0;
+  __syncthreads();
+  for (int p = pa + threadIdx.x; p < pe; p += blockDim.x) {
+    DF t;
+    if (!df_split(av[p], t)) *flag = 1;
+  }
+  __syncthreads();
+  const bool ok = *flag == 0;
+  __syncthreads();
+  return ok;
+}
+
+__device__ __forceinline__ double out_value(u64 v, bool df) {
+  return df ? df_to_double(df_unpack(v)) : __longlong_as_double((long long)v);
+}
+
+// Bitonic sort of P (a power of two) u64 items in shared memory by a team.
+template <int TEAM>
+__device__ __forceinline__ void team_bitonic(u64* buf, int P, int tl, unsigned mask) {
+  for (int kk = 2; kk <= P; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int t = tl; t < (P >> 1); t += TEAM) {
+        const int lo = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+        const int hi = lo + j;
+        const bool up = (lo & kk) == 0;
+        const u64 x = buf[lo], y = buf[hi];
+        if ((x > y) == up) {
+          buf[lo] = y;
+          buf[hi] = x;
+        }
+      }
+      __syncwarp(mask);
+    }
+  }
+}
+
+__device__ __forceinline__ void block_bitonic(u64* buf, int P) {
+  for (int kk = 2; kk <= P; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+        const int lo = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+        const int hi = lo + j;
+        const bool up = (lo & kk) == 0;
+        const u64 x = buf[lo], y = buf[hi];
+        if ((x > y) == up) {
+          buf[lo] = y;
+          buf[hi] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Exclusive scan of v over the block (blockDim.x a multiple of 32, <= 1024);
+// returns this thread's prefix and the block total in *total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* scratch, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  int incl = team_inclusive_scan<32>(v, lane, 0xffffffffu);
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < nw ? scratch[lane] : 0;
+    int wi = team_inclusive_scan<32>(w, lane, 0xffffffffu);
+    if (lane < nw) scratch[lane] = wi - w;
+    if (lane == 31) scratch[32] = wi;
+  }
+  __syncthreads();
+  const int r = scratch[warp] + incl - v;
+  *total = scratch[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ int pow2ceil(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// Team tier
+// ---------------------------------------------------------------------------
+// Teams per CTA for a team-tier map of 2^LOG2S slots (16 bytes per slot: key,
+// value, half a sort item): at most 96 KB per CTA.
+template <int TEAM, int LOG2S>
+struct NumTeamGeom {
+  static constexpr int kByTable = (96 * 1024) / ((1 << LOG2S) * 16);
+  static constexpr int TPB = (kTeamBlock / TEAM) < kByTable ? (kTeamBlock / TEAM)
+                                                             : (kByTable < 1 ? 1 : kByTable);
+};
+
+template <int TEAM, int LOG2S, bool FLAT>
+__global__ void __launch_bounds__(kTeamBlock) k_num_team(NumArgs g) {
+  extern __shared__ u64 smem_u[];
+  constexpr int S = 1 << LOG2S;
+  constexpr int H = S / 2;
+  constexpr int TPB = NumTeamGeom<TEAM, LOG2S>::TPB;
+  const int team = threadIdx.x / TEAM;
+  const int tl = threadIdx.x % TEAM;
+  const int lane = threadIdx.x & 31;
+  const unsigned mask = team_mask<TEAM>();
+  u64* vals = smem_u + team * S;
+  u64* sbuf = smem_u + TPB * S + team * H;
+  int* keys = reinterpret_cast<int*>(smem_u + TPB * S + TPB * H) + team * S;
+  const bool df_all = g.arith == kArithDF32 && *g.b_range_bad == 0;
+  const bool atomic = FLAT || !g.b_sorted;
+  const FullRange rng{g.A.colind, g.B.rowptr};
+  const int32_t* bcol = g.B.colind;
+  const double* bval = g.B.vals;
+  const float2* bspl = g.b_split;
+  int* status = g.status;
+  for (int r = blockIdx.x * TPB + team; r < g.nrows; r += gridDim.x * TPB) {
+    const int i = g.rows[r];
+    const int64_t off = g.c_rowptr[i];
+    const int cnt = (int)(g.c_rowptr[i + 1] - off);
+    for (int s = tl; s < S; s += TEAM) {
+      keys[s] = kEmptyKey;
+      vals[s] = 0ull;
+    }
+    __syncwarp(mask);
+    const int pa = g.A.rowptr[i], pe = g.A.rowptr[i + 1];
+    const bool df = df_all && row_df_ok<TEAM>(g.A.vals, pa, pe, tl, mask);
+    if (df) {
+      visit_products<TEAM, FLAT, DF>(pa, pe, 0, 1, tl, mask, rng, PrepDF{g.A.vals},
+                                     [&](DF a, int, int q) {
+                                       const int slot = map_slot(keys, bcol[q], LOG2S, status);
+                                       if (slot >= 0) upd_df(vals, slot, a, load_b(bspl, q), atomic, status);
+                                     });
+    } else {
+      visit_products<TEAM, FLAT, double>(pa, pe, 0, 1, tl, mask, rng, PrepF64{g.A.vals},
+                                         [&](double a, int, int q) {
+                                           const int slot = map_slot(keys, bcol[q], LOG2S, status);
+                                           if (slot >= 0) upd_f64(vals, slot, a, bval[q], atomic);
+                                         });
+    }
+    __syncwarp(mask);
+    // compaction of occupied slots into (key << 32 | slot) items
+    int base = 0;
+    const int tbase = lane & ~(TEAM - 1);
+    for (int s0 = 0; s0 < S; s0 += TEAM) {
+      const int s = s0 + tl;
+      const int key = keys[s];
+      const bool occ = key != kEmptyKey;
+      const unsigned bal = __ballot_sync(mask, occ);
+      unsigned seg;
+      if constexpr (TEAM == 32) seg = bal; else seg = (bal >> tbase) & ((1u << TEAM) - 1u);
+      const int pos = base + __popc(seg & ((1u << tl) - 1u));
+      if (occ && pos < H) sbuf[pos] = ((u64)(uint32_t)key << 32) | (u64)s;
+      base += __popc(seg);
+    }
+    if (base != cnt && tl == 0) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    const int n = max(0, min(min(base, cnt), H));
+    const int P = pow2ceil(n);
+    for (int t = n + tl; t < P; t += TEAM) sbuf[t] = ~0ull;
+    __syncwarp(mask);
+    team_bitonic<TEAM>(sbuf, P, tl, mask);
+    for (int t = tl; t < n; t += TEAM) {
+      const u64 it = sbuf[t];
+      g.c_colind[off + t] = (int32_t)(it >> 32);
+      g.c_vals[off + t] = out_value(vals[(uint32_t)it], df);
+    }
+    __syncwarp(mask);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CTA tier: warps of the CTA share one hash map; flattened traversal, atomics.
+// ---------------------------------------------------------------------------
+template <int LOG2S>
+__global__ void __launch_bounds__(kCtaBlock) k_num_cta(NumArgs g) {
+  extern __shared__ u64 smem_u[];
+  constexpr int S = 1 << LOG2S;
+  constexpr int H = S / 2;
+  __shared__ int scan_scratch[33];
+  __shared__ int flag;
+  u64* vals = smem_u;
+  u64* sbuf = smem_u + S;
+  int* keys = reinterpret_cast<int*>(smem_u + S + H);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const bool df_all = g.arith == kArithDF32 && *g.b_range_bad == 0;
+  const FullRange rng{g.A.colind, g.B.rowptr};
+  const int32_t* bcol = g.B.colind;
+  const double* bval = g.B.vals;
+  const float2* bspl = g.b_split;
+  int* status = g.status;
+  for (int r = blockIdx.x; r < g.nrows; r += gridDim.x) {
+    const int i = g.rows[r];
+    const int64_t off = g.c_rowptr[i];
+    const int cnt = (int)(g.c_rowptr[i + 1] - off);
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+      keys[s] = kEmptyKey;
+      vals[s] = 0ull;
+    }
+    const int pa = g.A.rowptr[i], pe = g.A.rowptr[i + 1];
+    const bool df = df_all && block_df_ok(g.A.vals, pa, pe, &flag);  // contains __syncthreads
+    if (df) {
+      visit_products<32, true, DF>(pa, pe, warp, nwarps, lane, 0xffffffffu, rng, PrepDF{g.A.vals},
+                                   [&](DF a, int, int q) {
+                                     const int slot = map_slot(keys, bcol[q], LOG2S, status);
+                                     if (slot >= 0) upd_df(vals, slot, a, load_b(bspl, q), true, status);
+                                   });
+    } else {
+      visit_products<32, true, double>(pa, pe, warp, nwarps, lane, 0xffffffffu, rng,
+                                       PrepF64{g.A.vals}, [&](double a, int, int q) {
+                                         const int slot = map_slot(keys, bcol[q], LOG2S, status);
+                                         if (slot >= 0) upd_f64(vals, slot, a, bval[q], true);
+                                       });
+    }
+    __syncthreads();
+    int base = 0;
+    for (int s0 = 0; s0 < S; s0 += blockDim.x) {
+      const int s = s0 + threadIdx.x;
+      const int key = keys[s];
+      const int occ = key != kEmptyKey ? 1 : 0;
+      int tot;
+      const int pos = base + block_exclusive_scan(occ, scan_scratch, &tot);
+      if (occ && pos < H) sbuf[pos] = ((u64)(uint32_t)key << 32) | (u64)s;
+      base += tot;
+    }
+    if (base != cnt && threadIdx.x == 0) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    const int n = max(0, min(min(base, cnt), H));
+    const int P = pow2ceil(n);
+    for (int t = n + threadIdx.x; t < P; t += blockDim.x) sbuf[t] = ~0ull;
+    __syncthreads();
+    block_bitonic(sbuf, P);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const u64 it = sbuf[t];
+      g.c_colind[off + t] = (int32_t)(it >> 32);
+      g.c_vals[off + t] = out_value(vals[(uint32_t)it], df);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dense tier: value array + bit vector over columns [c0, c0 + W).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kDenseBlock) k_num_dense(NumArgs g) {
+  extern __shared__ u64 smem_u[];
+  __shared__ int scan_scratch[33];
+  __shared__ int flag;
+  const int W = g.W;
+  const int words = W >> 5;
+  u64* vals = smem_u;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(smem_u + W);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const bool df_all = g.arith == kArithDF32 && *g.b_range_bad == 0;
+  const int32_t* acol = g.A.colind;
+  const int32_t* brp = g.B.rowptr;
+  const int32_t* bcol = g.B.colind;
+  const double* bval = g.B.vals;
+  const float2* bspl = g.b_split;
+  int* status = g.status;
+  const int k = g.k;
+  for (int r = blockIdx.x; r < g.nrows; r += gridDim.x) {
+    const int i = g.rows[r];
+    const int64_t off = g.c_rowptr[i];
+    const int64_t cnt = g.c_rowptr[i + 1] - off;
+    const int pa = g.A.rowptr[i], pe = g.A.rowptr[i + 1];
+    const bool df = df_all && block_df_ok(g.A.vals, pa, pe, &flag);
+    int64_t run = 0;
+    for (long long c0l = 0; c0l < k; c0l += W) {
+      const int c0 = (int)c0l;
+      const int cend = (k - c0 > W) ? c0 + W : k;
+      const bool whole = (k <= W) || !g.b_sorted;
+      for (int w = threadIdx.x; w < W; w += blockDim.x) vals[w] = 0ull;
+      for (int w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
+      __syncthreads();
+      auto rng = [&](int p, int& bs, int& bl) {
+        const int j = acol[p];
+        int lo = brp[j], hi = brp[j + 1];
+        if (!whole) {
+          lo = lower_bound_i32(bcol, lo, hi, c0);
+          hi = lower_bound_i32(bcol, lo, hi, cend);
+        }
+        bs = lo;
+        bl = hi - lo;
+      };
+      if (df) {
+        visit_products<32, true, DF>(pa, pe, warp, nwarps, lane, 0xffffffffu, rng,
+                                     PrepDF{g.A.vals}, [&](DF a, int, int q) {
+                                       const uint32_t o = (uint32_t)(bcol[q] - c0);
+                                       if (o < (uint32_t)W) {
+                                         atomicOr(&bits[o >> 5], 1u << (o & 31));
+                                         df_atomic_fma(&vals[o], a, load_b(bspl, q), status);
+                                       }
+                                     });
+      } else {
+        visit_products<32, true, double>(pa, pe, warp, nwarps, lane, 0xffffffffu, rng,
+                                         PrepF64{g.A.vals}, [&](double a, int, int q) {
+                                           const uint32_t o = (uint32_t)(bcol[q] - c0);
+                                           if (o < (uint32_t)W) {
+                                             atomicOr(&bits[o >> 5], 1u << (o & 31));
+                                             atomicAdd(reinterpret_cast<double*>(&vals[o]), a * bval[q]);
+                                           }
+                                         });
+      }
+      __syncthreads();
+      for (int w0 = 0; w0 < words; w0 += blockDim.x) {
+        const int w = w0 + threadIdx.x;
+        const uint32_t word = w < words ? bits[w] : 0u;
+        int tot;
+        const int pre = block_exclusive_scan(__popc(word), scan_scratch, &tot);
+        int64_t pos = run + pre;
+        uint32_t rest = word;
+        while (rest) {
+          const int b = __ffs(rest) - 1;
+          rest &= rest - 1;
+          if (pos < cnt) {
+            const int o = w * 32 + b;
+            g.c_colind[off + pos] = c0 + o;
+            g.c_vals[off + pos] = out_value(vals[o], df);
+          }
+          ++pos;
+        }
+        run += tot;
+      }
+      __syncthreads();
+    }
+    if (run != cnt && threadIdx.x == 0) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+  }
+}
+
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int TEAM, int LOG2S, bool FLAT>
+cudaError_t launch_team(const LaunchCtx& ctx, const NumArgs& g) {
+  constexpr int TPB = NumTeamGeom<TEAM, LOG2S>::TPB;
+  const size_t smem = (size_t)TPB * (1u << LOG2S) * (8 + 4 + 4);
+  auto kern = k_num_team<TEAM, LOG2S, FLAT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  long long blocks = (g.nrows + TPB - 1) / TPB;
+  blocks = blocks > (long long)ctx.num_sms * 32 ? (long long)ctx.num_sms * 32 : blocks;
+  kern<<<(unsigned)blocks, TPB * TEAM, smem, ctx.stream>>>(g);
+  return cudaGetLastError();
+}
+
+template <int TEAM, bool FLAT>
+cudaError_t dispatch_team(const LaunchCtx& ctx, int log2s, const NumArgs& g) {
+  switch (log2s) {
+    case 5: return launch_team<TEAM, 5, FLAT>(ctx, g);
+    case 6: return launch_team<TEAM, 6, FLAT>(ctx, g);
+    case 7: return launch_team<TEAM, 7, FLAT>(ctx, g);
+    case 8: return launch_team<TEAM, 8, FLAT>(ctx, g);
+    case 9: return launch_team<TEAM, 9, FLAT>(ctx, g);
+    case 10: return launch_team<TEAM, 10, FLAT>(ctx, g);
+    case 11: return launch_team<TEAM, 11, FLAT>(ctx, g);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int LOG2S>
+cudaError_t launch_cta(const LaunchCtx& ctx, const NumArgs& g) {
+  const size_t smem = (size_t)(1u << LOG2S) * (8 + 4 + 4);
+  auto kern = k_num_cta<LOG2S>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  long long blocks = g.nrows < ctx.num_sms * 4 ? g.nrows : ctx.num_sms * 4;
+  kern<<<(unsigned)blocks, kCtaBlock, smem, ctx.stream>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t numeric_smem_bytes(const BinSpec& bin) {
+  if (bin.tier == kTierTeam) {
+    int tpb = kTeamBlock / bin.team, by = (96 * 1024) / (bin.slots * 16);
+    if (by < 1) by = 1;
+    return (size_t)(tpb < by ? tpb : by) * bin.slots * 16;
+  }
+  if (bin.tier == kTierCta) return (size_t)bin.slots * 16;
+  return (size_t)bin.slots * 8 + (size_t)bin.slots / 8;
+}
+
+cudaError_t launch_numeric_bin(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,
+                               const CsrView& B, int32_t b_sorted, const float2* b_split,
+                               const int32_t* b_range_bad, int32_t arith,
+                               const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
+                               int32_t* c_colind, double* c_vals, int32_t) {
+  if (nrows <= 0) return cudaSuccess;
+  NumArgs g{A, B, b_sorted, b_split, b_range_bad, arith, c_rowptr, rows, nrows,
+            c_colind, c_vals, ctx.status, B.n, bin.slots};
+  int log2s = 0;
+  while ((1 << log2s) < bin.slots) ++log2s;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (bin.tier == kTierTeam) {
+    timer_begin(ctx.timer, ctx.stream, bin.flat ? "num_team_flat" : "num_team_vec");
+    if (bin.flat) {
+      if (bin.team == 8) e = dispatch_team<8, true>(ctx, log2s, g);
+      else if (bin.team == 32) e = dispatch_team<32, true>(ctx, log2s, g);
+    } else {
+      if (bin.team == 8) e = dispatch_team<8, false>(ctx, log2s, g);
+      else if (bin.team == 32) e = dispatch_team<32, false>(ctx, log2s, g);
+    }
+    timer_end(ctx.timer, ctx.stream);
+    return e;
+  }
+  if (bin.tier == kTierCta) {
+    timer_begin(ctx.timer, ctx.stream, "num_cta");
+    switch (log2s) {
+      case 12: e = launch_cta<12>(ctx, g); break;
+      case 13: e = launch_cta<13>(ctx, g); break;
+      default: e = cudaErrorInvalidValue;
+    }
+    timer_end(ctx.timer, ctx.stream);
+    return e;
+  }
+  timer_begin(ctx.timer, ctx.stream, "num_dense");
+  const size_t smem = numeric_smem_bytes(bin);
+  e = set_smem(k_num_dense, smem);
+  if (e == cudaSuccess) {
+    long long blocks = nrows < ctx.num_sms ? nrows : ctx.num_sms;
+    k_num_dense<<<(unsigned)blocks, kDenseBlock, smem, ctx.stream>>>(g);
+    e = cudaGetLastError();
+  }
+  timer_end(ctx.timer, ctx.stream);
+  return e;
+}
+
+}  // namespace kk

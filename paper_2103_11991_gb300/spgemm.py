@@ -1,0 +1,300 @@
+"""Python binding of the C ABI in include/kk_spgemm.h (argument marshalling only).
+
+Every function named ``kk_*`` here calls the C function of the same name in
+``libkk_spgemm.so`` with raw device pointers taken from torch tensors; all
+computation runs in the library's CUDA kernels.  Loading fails loudly when the
+library is missing: there is no CPU fallback.
+
+Higher-level helpers (``DeviceCSR``, ``SpGEMM``, ``spgemm``) allocate C's arrays
+with torch between the symbolic and numeric phases, as the two-phase method
+requires (Kokkos Kernels paper, Sec. "Standard SpGEMM Kernel": row pointers
+first, symbolic, then column indices and values of size nnz(C), numeric).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libkk_spgemm.so")
+_lock = threading.Lock()
+_lib = None
+
+KK_OK = 0
+STATUS_NAMES = {
+    0: "KK_OK", 1: "KK_ERR_INVALID_ARG", 2: "KK_ERR_CUDA", 3: "KK_ERR_OOM",
+    4: "KK_ERR_STRUCTURE_MISMATCH", 5: "KK_ERR_CAPACITY", 6: "KK_ERR_TIMEOUT",
+    7: "KK_ERR_NOT_SYMBOLIC", 8: "KK_ERR_BAD_INDEX",
+}
+KK_ARITH_AUTO, KK_ARITH_FP64, KK_ARITH_DF32 = 0, 1, 2
+
+
+class KKError(RuntimeError):
+    def __init__(self, status: int, detail: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {detail}")
+
+
+class KkCsr(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("nnz", ctypes.c_int32),
+                ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p), ("vals", ctypes.c_void_p)]
+
+
+class KkOptions(ctypes.Structure):
+    _fields_ = [("arith", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
+                ("timing", ctypes.c_int32), ("force_tier", ctypes.c_int32),
+                ("team_vec_min_len", ctypes.c_int32), ("sym_team_max_flop", ctypes.c_int32),
+                ("sym_cta_max_flop", ctypes.c_int32), ("num_team_max_nnz", ctypes.c_int32),
+                ("num_cta_max_nnz", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+# exported symbol -> (restype, argtypes)
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_SIGS = {
+    "kk_spgemm_options_default": (_I32, [ctypes.POINTER(KkOptions)]),
+    "kk_spgemm_handle_create": (_I32, [ctypes.POINTER(_P), ctypes.POINTER(KkOptions), _P]),
+    "kk_spgemm_set_stream": (_I32, [_P, _P]),
+    "kk_spgemm_symbolic": (_I32, [_P, ctypes.POINTER(KkCsr), ctypes.POINTER(KkCsr), _P,
+                                  ctypes.POINTER(ctypes.c_int64)]),
+    "kk_spgemm_numeric": (_I32, [_P, ctypes.POINTER(KkCsr), ctypes.POINTER(KkCsr), _P, _P, _P]),
+    "kk_spgemm_sync": (_I32, [_P]),
+    "kk_spgemm_destroy": (_I32, [_P]),
+    "kk_status_string": (ctypes.c_char_p, [_I32]),
+    "kk_spgemm_last_error": (ctypes.c_char_p, [_P]),
+    "kk_spgemm_last_arith": (_I32, [_P]),
+    "kk_spgemm_kernel_times": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_char_p),
+                                      ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I32), _I32]),
+    "kk_spgemm_stats": (_I32, [_P, ctypes.POINTER(ctypes.c_int64)]),
+}
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libkk_spgemm.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(
+                    f"{_LIB_PATH} is missing: build it with paper_2103_11991_gb300._build.build() "
+                    "(nvcc, sm_103a); there is no CPU fallback")
+            lib = ctypes.CDLL(_LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status: int, handle=None):
+    if status != KK_OK:
+        detail = ""
+        if handle:
+            raw = load_library().kk_spgemm_last_error(handle)
+            detail = raw.decode() if raw else ""
+        raise KKError(status, detail)
+
+
+# ----------------------------------------------------------------------------
+# Same-name wrappers of the C ABI
+# ----------------------------------------------------------------------------
+def kk_spgemm_options_default() -> KkOptions:
+    o = KkOptions()
+    _check(load_library().kk_spgemm_options_default(ctypes.byref(o)))
+    return o
+
+
+def kk_spgemm_handle_create(opt: KkOptions | None = None, stream=None):
+    """Returns an opaque handle (int).  ``stream``: a torch.cuda.Stream, a raw
+    cudaStream_t int, or None for torch's current stream."""
+    import torch
+    h = _P()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(load_library().kk_spgemm_handle_create(ctypes.byref(h),
+                                                  ctypes.byref(opt) if opt is not None else None,
+                                                  ctypes.c_void_p(raw)))
+    return h.value
+
+
+def kk_spgemm_set_stream(h, stream):
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(load_library().kk_spgemm_set_stream(h, ctypes.c_void_p(raw)), h)
+
+
+def kk_spgemm_symbolic(h, A: "DeviceCSR", B: "DeviceCSR", c_rowptr) -> int:
+    nnz = ctypes.c_int64(0)
+    a, b = A.abi(), B.abi()
+    _check(load_library().kk_spgemm_symbolic(h, ctypes.byref(a), ctypes.byref(b),
+                                             ctypes.c_void_p(c_rowptr.data_ptr()),
+                                             ctypes.byref(nnz)), h)
+    return int(nnz.value)
+
+
+def kk_spgemm_numeric(h, A: "DeviceCSR", B: "DeviceCSR", c_rowptr, c_colind, c_vals):
+    a, b = A.abi(), B.abi()
+    _check(load_library().kk_spgemm_numeric(h, ctypes.byref(a), ctypes.byref(b),
+                                            ctypes.c_void_p(c_rowptr.data_ptr()),
+                                            ctypes.c_void_p(c_colind.data_ptr()),
+                                            ctypes.c_void_p(c_vals.data_ptr())), h)
+
+
+def kk_spgemm_sync(h):
+    _check(load_library().kk_spgemm_sync(h), h)
+
+
+def kk_spgemm_destroy(h):
+    _check(load_library().kk_spgemm_destroy(h))
+
+
+def kk_status_string(s: int) -> str:
+    return load_library().kk_status_string(s).decode()
+
+
+def kk_spgemm_last_arith(h) -> int:
+    return int(load_library().kk_spgemm_last_arith(h))
+
+
+def kk_spgemm_kernel_times(h, reset: bool = False) -> dict:
+    lib = load_library()
+    n = 64
+    names = (ctypes.c_char_p * n)()
+    ms = (ctypes.c_double * n)()
+    launches = (ctypes.c_int64 * n)()
+    count = _I32(0)
+    _check(lib.kk_spgemm_kernel_times(h, n, names, ms, launches, ctypes.byref(count), int(reset)), h)
+    return {names[i].decode(): (ms[i], launches[i]) for i in range(min(count.value, n))}
+
+
+def kk_spgemm_stats(h) -> dict:
+    arr = (ctypes.c_int64 * 16)()
+    _check(load_library().kk_spgemm_stats(h, arr), h)
+    keys = ["sym_team_rows", "sym_cta_rows", "sym_dense_rows", "num_team_rows", "num_cta_rows",
+            "num_dense_rows", "flops", "b_sorted", "launches_sym", "launches_num"]
+    return {k: int(arr[i]) for i, k in enumerate(keys)}
+
+
+# ----------------------------------------------------------------------------
+# Device CSR and a small object API on top of the C ABI
+# ----------------------------------------------------------------------------
+class DeviceCSR:
+    """A CSR matrix in device memory (torch tensors).  rowptr int32 (int64 for
+    outputs of the product), colind int32, vals float64."""
+
+    def __init__(self, m, n, rowptr, colind, vals):
+        self.m, self.n = int(m), int(n)
+        self.rowptr, self.colind, self.vals = rowptr, colind, vals
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colind.numel())
+
+    @classmethod
+    def from_host(cls, M, device="cuda", non_blocking=False):
+        import torch
+        rp = torch.from_numpy(np.ascontiguousarray(M.rowptr, dtype=np.int32)).to(device, non_blocking=non_blocking)
+        ci = torch.from_numpy(np.ascontiguousarray(M.colind, dtype=np.int32)).to(device, non_blocking=non_blocking)
+        va = torch.from_numpy(np.ascontiguousarray(M.vals, dtype=np.float64)).to(device, non_blocking=non_blocking)
+        return cls(M.m, M.n, rp, ci, va)
+
+    def abi(self) -> KkCsr:
+        if self.rowptr.dtype.itemsize != 4:
+            raise TypeError("the C ABI takes int32 row pointers for A and B")
+        return KkCsr(self.m, self.n, self.nnz, self.rowptr.data_ptr(),
+                     self.colind.data_ptr() if self.nnz else None,
+                     self.vals.data_ptr() if (self.vals is not None and self.nnz) else None)
+
+    def to_host(self):
+        from paper_2103_11991_gb300.inputs import CSR
+        return CSR(self.m, self.n, self.rowptr.cpu().numpy(), self.colind.cpu().numpy(),
+                   self.vals.cpu().numpy())
+
+
+def make_options(**kw) -> KkOptions:
+    o = kk_spgemm_options_default()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, int(v))
+    return o
+
+
+class SpGEMM:
+    """Owns a handle; ``symbolic`` returns C's int64 row pointers and nnz(C),
+    ``numeric`` fills freshly allocated (or given) colind / vals."""
+
+    def __init__(self, stream=None, **options):
+        self.opt = make_options(**options)
+        self.h = kk_spgemm_handle_create(self.opt, stream)
+
+    def symbolic(self, A: DeviceCSR, B: DeviceCSR):
+        import torch
+        rowptr = torch.empty(A.m + 1, dtype=torch.int64, device=A.rowptr.device)
+        nnz = kk_spgemm_symbolic(self.h, A, B, rowptr)
+        return rowptr, nnz
+
+    def numeric(self, A: DeviceCSR, B: DeviceCSR, rowptr, nnz, colind=None, vals=None):
+        import torch
+        dev = A.rowptr.device
+        if colind is None:
+            colind = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+        if vals is None:
+            vals = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
+        kk_spgemm_numeric(self.h, A, B, rowptr, colind, vals)
+        return colind[:nnz], vals[:nnz]
+
+    def __call__(self, A: DeviceCSR, B: DeviceCSR) -> DeviceCSR:
+        rowptr, nnz = self.symbolic(A, B)
+        colind, vals = self.numeric(A, B, rowptr, nnz)
+        return DeviceCSR(A.m, B.n, rowptr, colind, vals)
+
+    def sync(self):
+        kk_spgemm_sync(self.h)
+
+    def kernel_times(self, reset=False):
+        return kk_spgemm_kernel_times(self.h, reset)
+
+    def stats(self):
+        return kk_spgemm_stats(self.h)
+
+    def last_arith(self):
+        return kk_spgemm_last_arith(self.h)
+
+    def close(self):
+        if self.h:
+            kk_spgemm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spgemm(A: DeviceCSR, B: DeviceCSR, **options) -> DeviceCSR:
+    """C = A*B on the GPU (symbolic, allocate, numeric, sync)."""
+    with SpGEMM(**options) as op:
+        C = op(A, B)
+        op.sync()
+    return C

@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by
+element.  Structure bit-exact; values within 1e-12 * sum|a||b| (exact for
+integer-valued inputs)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_11991_gb300 import inputs as I
+from tests._gpu import check_against_oracle, run_gpu
+from tests._util import assert_structure_equal, assert_values_within
+
+pytestmark = pytest.mark.gpu
+
+ARITHS = [1, 2]  # KK_ARITH_FP64, KK_ARITH_DF32
+TIERS = [-1, 0, 1, 2]
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("tier", TIERS)
+@pytest.mark.parametrize("seed", range(6))
+def test_random_small(seed, tier, arith):
+    u = I.uniform01(seed, "gpu.dims", 3)
+    m, n, k = 1 + int(u[0] * 200), 1 + int(u[1] * 150), 1 + int(u[2] * 300)
+    dens = [0.01, 0.05, 0.15, 0.4][seed % 4]
+    A = I.random_sparse(m, n, dens, seed, duplicates=seed % 3 == 0, unsorted=seed % 2 == 1,
+                        empty_rows=0.1)
+    B = I.random_sparse(n, k, dens, seed + 50, duplicates=seed % 4 == 1, unsorted=seed % 3 == 2)
+    rp, ci, va, _, _ = run_gpu(A, B, arith=arith, force_tier=tier)
+    check_against_oracle(A, B, rp, ci, va)
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("tier", TIERS)
+def test_integer_valued_exact(tier, arith):
+    A = I.random_sparse(150, 120, 0.1, 3, integer=True)
+    B = I.random_sparse(120, 170, 0.1, 4, integer=True)
+    rp, ci, va, _, _ = run_gpu(A, B, arith=arith, force_tier=tier)
+    check_against_oracle(A, B, rp, ci, va, exact=True)
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+def test_stencil2d_64_exact(arith):
+    d = I.config_inputs("stencil2d_64")
+    rp, ci, va, _, st = run_gpu(d["A"], d["B"], arith=arith)
+    ref = check_against_oracle(d["A"], d["B"], rp, ci, va, exact=True)
+    assert ref.nnz == 51972
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+def test_stencil3d27_small_exact(arith):
+    d = I.config_inputs("stencil3d27_100", scale=22)
+    rp, ci, va, _, _ = run_gpu(d["A"], d["B"], arith=arith)
+    check_against_oracle(d["A"], d["B"], rp, ci, va, exact=True)
+
+
+@pytest.mark.parametrize("tier", TIERS)
+def test_rmat_small(tier):
+    A = I.rmat(11, 16, seed=3)
+    rp, ci, va, _, _ = run_gpu(A, A, force_tier=tier)
+    check_against_oracle(A, A, rp, ci, va)
+
+
+def test_rmat_mixed_tiers_auto():
+    # scale 13 has rows in every tier under the default thresholds
+    A = I.rmat(13, 16, seed=5)
+    rp, ci, va, _, st = run_gpu(A, A)
+    check_against_oracle(A, A, rp, ci, va)
+    assert st["sym_team_rows"] > 0 and st["num_team_rows"] > 0
+    assert st["num_cta_rows"] + st["num_dense_rows"] > 0
+
+
+def test_dense_tier_multi_chunk():
+    # k > one dense chunk (16384 columns): chunks swept with sorted B rows
+    A = I.random_rows(60, 50, 20, 40, seed=1)
+    B = I.random_rows(50, 70000, 200, 400, seed=2)
+    rp, ci, va, _, st = run_gpu(A, B, force_tier=2)
+    check_against_oracle(A, B, rp, ci, va)
+    B2 = I.random_sparse(50, 40000, 0.01, 3, unsorted=True)
+    rp, ci, va, _, st = run_gpu(A, B2, force_tier=2)
+    check_against_oracle(A, B2, rp, ci, va)
+
+
+def test_galerkin_with_symbolic_reuse():
+    from paper_2103_11991_gb300 import spgemm as K
+    import torch
+    d = I.config_inputs("amg_galerkin_128", scale=16)
+    A, P, R = d["A"], d["P"], d["R"]
+    dA, dP, dR = (K.DeviceCSR.from_host(X) for X in (A, P, R))
+    op1, op2 = K.SpGEMM(), K.SpGEMM()
+    rp1, nnz1 = op1.symbolic(dA, dP)
+    ci1, va1 = op1.numeric(dA, dP, rp1, nnz1)
+    dAP = K.DeviceCSR(A.m, P.n, rp1.to(torch.int32), ci1, va1)
+    rp2, nnz2 = op2.symbolic(dR, dAP)
+    ci2, va2 = op2.numeric(dR, dAP, rp2, nnz2)
+    L = I.stencil_3d(8, 8, 8, 7, 6.0, -1.0)
+    scales = I.uniform01(11, "refresh", 3) * 1.5 + 0.5
+    for it in range(4):
+        s = 1.0 if it == 0 else float(scales[it - 1])
+        if it > 0:
+            dA.vals.copy_(torch.from_numpy(A.vals * s).cuda())
+            op1.numeric(dA, dP, rp1, nnz1, ci1, va1)
+            op2.numeric(dR, dAP, rp2, nnz2, ci2, va2)
+        op1.sync()
+        op2.sync()
+        assert_structure_equal(rp2.cpu().numpy(), ci2.cpu().numpy(), L.rowptr, L.colind)
+        As = I.CSR(A.m, A.n, A.rowptr, A.colind, A.vals * s)
+        ref = oracle.spgemm(R, I.CSR(A.m, P.n, oracle.spgemm(As, P).rowptr.astype(np.int32),
+                                     oracle.spgemm(As, P).colind, oracle.spgemm(As, P).vals))
+        assert np.array_equal(ci2.cpu().numpy(), ref.colind)
+        assert np.allclose(va2.cpu().numpy(), ref.vals, rtol=1e-13, atol=0)
+        if it == 0:
+            assert np.array_equal(va2.cpu().numpy(), 4.0 * L.vals)
+    op1.close()
+    op2.close()
+
+
+def test_edge_cases():
+    # empty rows everywhere, zero-size dims, single entries
+    cases = [
+        (I.random_sparse(10, 8, 0.0, 1), I.random_sparse(8, 9, 0.5, 2)),
+        (I.random_sparse(10, 8, 0.5, 1), I.random_sparse(8, 9, 0.0, 2)),
+        (I.random_sparse(1, 1, 1.0, 1), I.random_sparse(1, 1, 1.0, 2)),
+        (I.random_sparse(0, 5, 0.5, 1), I.random_sparse(5, 4, 0.5, 2)),
+        (I.random_sparse(6, 0, 0.5, 1), I.random_sparse(0, 4, 0.5, 2)),
+        (I.random_sparse(6, 5, 0.5, 1), I.random_sparse(5, 0, 0.5, 2)),
+    ]
+    for A, B in cases:
+        rp, ci, va, _, _ = run_gpu(A, B)
+        check_against_oracle(A, B, rp, ci, va)
+
+
+def test_cancellation_keeps_structural_zero():
+    A = I.CSR(1, 2, np.array([0, 2], np.int32), np.array([0, 1], np.int32), np.array([1.0, 1.0]))
+    B = I.CSR(2, 1, np.array([0, 1, 2], np.int32), np.array([0, 0], np.int32), np.array([1.0, -1.0]))
+    for arith in ARITHS:
+        rp, ci, va, _, _ = run_gpu(A, B, arith=arith)
+        assert list(rp) == [0, 1] and list(ci) == [0] and va[0] == 0.0
+
+
+def test_df32_window_falls_back_to_fp64():
+    A = I.random_sparse(40, 30, 0.2, 1)
+    B = I.random_sparse(30, 20, 0.2, 2)
+    B.vals[3] = 1e-30  # outside the DF32 window -> every row takes the float64 path
+    rp, ci, va, arith, _ = run_gpu(A, B, arith=0)
+    check_against_oracle(A, B, rp, ci, va)
+    assert arith == 1
+    A.vals[0] = 1e25  # a row of A outside the window
+    B = I.random_sparse(30, 20, 0.2, 2)
+    rp, ci, va, arith, _ = run_gpu(A, B, arith=0)
+    check_against_oracle(A, B, rp, ci, va)
+
+
+def test_determinism_vector_mode():
+    d = I.config_inputs("stencil3d27_100", scale=16)
+    A = d["A"].copy()
+    A.vals = I.uniform01(1, "v", A.nnz) * 2 - 1
+    r1 = run_gpu(A, A)
+    r2 = run_gpu(A, A)
+    assert np.array_equal(r1[2], r2[2])
+    check_against_oracle(A, A, r1[0], r1[1], r1[2])
+
+
+def test_errors_reported():
+    from paper_2103_11991_gb300 import spgemm as K
+    A = I.random_sparse(20, 10, 0.3, 1)
+    B = I.random_sparse(10, 12, 0.3, 2)
+    dA, dB = K.DeviceCSR.from_host(A), K.DeviceCSR.from_host(B)
+    op = K.SpGEMM()
+    import torch
+    rp = torch.zeros(21, dtype=torch.int64, device="cuda")
+    c = torch.zeros(4, dtype=torch.int32, device="cuda")
+    v = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(K.KKError) as e:
+        K.kk_spgemm_numeric(op.h, dA, dB, rp, c, v)
+    assert e.value.status == 7
+    with pytest.raises(K.KKError) as e:
+        K.kk_spgemm_symbolic(op.h, dB, dB, rp)  # 10x12 times 10x12: inner dims differ
+    assert e.value.status == 1
+    bad = A.copy()
+    bad.colind[3] = 10  # column index out of range for B's rows
+    with pytest.raises(K.KKError) as e:
+        op.symbolic(K.DeviceCSR.from_host(bad), dB)
+    assert e.value.status == 8
+    rp, nnz = op.symbolic(dA, dB)
+    A2 = I.random_sparse(20, 10, 0.5, 9)
+    with pytest.raises(K.KKError) as e:
+        op.numeric(K.DeviceCSR.from_host(A2), dB, rp, nnz)
+    assert e.value.status == 4
+    op.close()
