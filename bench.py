@@ -120,7 +120,7 @@ def cpu_oracle_rate(A, B, madds_per_row, budget_s: float):
     block = max(1, m // 64)
     done_rows, done_flops, t_total = 0, 0, 0.0
     r0 = 0
-    while t_total < budget_s and done_rows < m:
+    while t_total < budget_s:
         r1 = min(m, r0 + block)
         t = time.perf_counter()
         oracle.spgemm(A, B, r0, r1)
@@ -247,16 +247,19 @@ def run_ours(args, rank, world, local_rank):
         per_step_bytes = None
     peak, peak_kind = _peaks()
     launches_of_dom_per_step = dom_n / reps
+    dom_ms_per_step = dom_ms / reps
     if per_step_bytes is not None:
-        achieved = (per_step_bytes / launches_of_dom_per_step) / (dom_avg_ms * 1e-3) / 1e9
+        # bytes of all rows this kernel kind processed in one step / its time in one step
+        achieved = per_step_bytes / (dom_ms_per_step * 1e-3) / 1e9
     else:
         achieved = None
     roofline = {
         "bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
         "peak_kind": peak_kind, "unit": "GB/s",
         "frac": (achieved / peak) if achieved else None, "traffic": args.traffic,
-        "algorithmic_bytes_per_launch": (per_step_bytes / launches_of_dom_per_step) if per_step_bytes else None,
-        "avg_launch_ms": dom_avg_ms,
+        "algorithmic_bytes_per_step": per_step_bytes,
+        "launches_per_step": launches_of_dom_per_step,
+        "ms_per_step": dom_ms_per_step,
         "step_frac": (sym_b + num_b) / (ms * 1e-3) / 1e9 / peak,
     }
     kernels = {k: {"ms_per_step": v[0] / reps, "launches_per_step": v[1] / reps} for k, v in kt.items()}

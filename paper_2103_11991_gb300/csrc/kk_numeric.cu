@@ -272,6 +272,299 @@ __global__ void __launch_bounds__(kTeamBlock) k_num_team(NumArgs g) {
 }
 
 // ---------------------------------------------------------------------------
+// Warp-per-row vector kernel (the common case for rows whose referenced B rows
+// are long: stencils, FEM).  One warp per row; the warp's lanes split each B
+// row; A entries are taken in storage order, so the update of an output entry
+// needs no atomic when B's rows have distinct columns.  The lane that inserts
+// a key writes its first product, so the value table needs no clearing.  After
+// accumulation the occupied keys are compacted and sorted in registers
+// (bitonic network, E keys per lane, element e = r*32 + lane), then each sorted
+// key finds its value slot again and the row is written coalesced.
+// ---------------------------------------------------------------------------
+template <int LOG2S>
+struct WarpVecGeom {
+  static constexpr int S = 1 << LOG2S;
+  static constexpr int E = (S / 2) / 32 < 1 ? 1 : (S / 2) / 32;  // keys per lane (P = 32*E >= S/2)
+  static constexpr int WPB = 8;                                   // warps per CTA
+  // per warp: keys int[S] | vals u64[S] | A staging int4[32] | key staging int[32*E]
+  static constexpr size_t kWarpBytes = (size_t)S * 4 + (size_t)S * 8 + 32 * 16 + 32 * E * 4;
+};
+
+__device__ __forceinline__ int probe_find(const int* keys, int32_t key, int log2s) {
+  const uint32_t mask = (1u << log2s) - 1u;
+  uint32_t h = hash_slot(key, log2s);
+  for (uint32_t p = 0; p <= mask; ++p) {
+    const int cur = keys[h];
+    if (cur == key) return (int)h;
+    if (cur == kEmptyKey) return -1;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+// Find-or-insert; *inserted tells whether this call created the key.
+__device__ __forceinline__ int probe_insert(int* keys, int32_t key, int log2s, bool* inserted,
+                                            int* status) {
+  const uint32_t mask = (1u << log2s) - 1u;
+  uint32_t h = hash_slot(key, log2s);
+  for (uint32_t p = 0; p <= mask; ++p) {
+    const int cur = keys[h];
+    if (cur == key) {
+      *inserted = false;
+      return (int)h;
+    }
+    if (cur == kEmptyKey) {
+      const int old = atomicCAS(&keys[h], kEmptyKey, key);
+      if (old == kEmptyKey) {
+        *inserted = true;
+        return (int)h;
+      }
+      if (old == key) {
+        *inserted = false;
+        return (int)h;
+      }
+    }
+    h = (h + 1) & mask;
+  }
+  *inserted = false;
+  set_status(status, KK_ERR_CAPACITY);
+  return -1;
+}
+
+// One product into the warp's map: find-or-insert col; the inserting lane
+// stores the first product, later ones accumulate.  a / b carry DF32 pairs
+// (df) or the two 32-bit halves of a float64.
+template <int LOG2S>
+__device__ __forceinline__ void warp_vec_update(int* keys, u64* vals, int col, int2 a, float2 b,
+                                                bool df, int* status) {
+  bool ins;
+  const int slot = probe_insert(keys, col, LOG2S, &ins, status);
+  if (slot < 0) return;
+  if (df) {
+    DF ad, bd, s;
+    ad.hi = __int_as_float(a.x);
+    ad.lo = __int_as_float(a.y);
+    bd.hi = b.x;
+    bd.lo = b.y;
+    if (ins) {
+      s.hi = 0.f;
+      s.lo = 0.f;
+    } else {
+      s = df_unpack(vals[slot]);
+    }
+    df_fma(s, ad, bd);
+    vals[slot] = df_pack(s);
+  } else {
+    const double av = __longlong_as_double(((long long)a.y << 32) | (unsigned)a.x);
+    const double bvv = __longlong_as_double(((long long)__float_as_int(b.y) << 32) |
+                                            (unsigned)__float_as_int(b.x));
+    double* v = reinterpret_cast<double*>(&vals[slot]);
+    *v = ins ? av * bvv : fma(av, bvv, *v);
+  }
+}
+
+// Bitonic sort of 32*E int keys held in registers, element e = r*32 + lane.
+template <int E>
+__device__ __forceinline__ void warp_bitonic_regs(int (&v)[E], int lane) {
+  constexpr int P = 32 * E;
+  constexpr int LOG2P = (P >= 1024) ? 10 : (P >= 512) ? 9 : (P >= 256) ? 8 : (P >= 128) ? 7 : (P >= 64) ? 6 : 5;
+#pragma unroll
+  for (int lk = 1; lk <= LOG2P; ++lk) {
+    const int k = 1 << lk;
+#pragma unroll
+    for (int lj = lk - 1; lj >= 0; --lj) {
+      const int j = 1 << lj;
+      if (j >= 32) {
+        const int jr = j >> 5;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          if ((r & jr) == 0) {
+            const int r2 = r | jr;
+            const int e = r * 32 + lane;
+            const bool up = (e & k) == 0;
+            const int a = v[r], b = v[r2];
+            const bool sw = (a > b) == up;
+            v[r] = sw ? b : a;
+            v[r2] = sw ? a : b;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const int e = r * 32 + lane;
+          const int o = __shfl_xor_sync(0xffffffffu, v[r], j);
+          const bool keep_min = ((e & j) == 0) == ((e & k) == 0);
+          v[r] = keep_min ? min(v[r], o) : max(v[r], o);
+        }
+      }
+    }
+  }
+}
+
+template <int LOG2S>
+__global__ void __launch_bounds__(256, 3) k_num_warp_vec(NumArgs g) {
+  using G = WarpVecGeom<LOG2S>;
+  constexpr int S = G::S;
+  constexpr int E = G::E;
+  constexpr int P = 32 * E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = smem_raw + (size_t)warp * G::kWarpBytes;
+  u64* vals = reinterpret_cast<u64*>(base);
+  int* keys = reinterpret_cast<int*>(base + (size_t)S * 8);
+  int4* ainfo = reinterpret_cast<int4*>(base + (size_t)S * 12);
+  int* kst = reinterpret_cast<int*>(base + (size_t)S * 12 + 32 * 16);
+  const bool df_all = g.arith == kArithDF32 && *g.b_range_bad == 0;
+  const int32_t* __restrict__ acol = g.A.colind;
+  const double* __restrict__ aval = g.A.vals;
+  const int32_t* __restrict__ brp = g.B.rowptr;
+  const int32_t* __restrict__ bcol = g.B.colind;
+  const double* __restrict__ bval = g.B.vals;
+  const float2* __restrict__ bspl = g.b_split;
+  int* status = g.status;
+  // contiguous share of rows per CTA (neighbouring rows reuse B rows in L1)
+  const int per_cta = (g.nrows + gridDim.x - 1) / gridDim.x;
+  const int r_begin = blockIdx.x * per_cta;
+  const int r_end = min(g.nrows, r_begin + per_cta);
+  for (int r = r_begin + warp; r < r_end; r += G::WPB) {
+    const int i = g.rows[r];
+    const int64_t off = g.c_rowptr[i];
+    const int cnt = (int)(g.c_rowptr[i + 1] - off);
+#pragma unroll
+    for (int s = lane * 4; s < S; s += 128) *reinterpret_cast<int4*>(&keys[s]) = make_int4(-1, -1, -1, -1);
+    __syncwarp();
+    const int pa = g.A.rowptr[i], pe = g.A.rowptr[i + 1];
+    bool df = df_all;
+    if (df_all && pe - pa > 32) {
+      // multi-chunk row: check the whole row against the DF32 window first
+      int bad = 0;
+      for (int p = pa + lane; p < pe; p += 32) {
+        DF t;
+        bad |= df_split(aval[p], t) ? 0 : 1;
+      }
+      df = __any_sync(0xffffffffu, bad) == 0;
+    }
+    for (int p0 = pa; p0 < pe; p0 += 32) {
+      const int p = p0 + lane;
+      int4 info = make_int4(0, 0, 0, 0);
+      double a64 = 0.0;
+      int bad = 0;
+      if (p < pe) {
+        const int j = acol[p];
+        const int bs = brp[j];
+        info.x = bs;
+        info.y = brp[j + 1] - bs;
+        a64 = aval[p];
+        if (df) {
+          DF ad;
+          bad = df_split(a64, ad) ? 0 : 1;
+          info.z = __float_as_int(ad.hi);
+          info.w = __float_as_int(ad.lo);
+        }
+      }
+      if (df && __any_sync(0xffffffffu, bad)) df = false;  // single-chunk row outside the window
+      if (!df) {
+        const long long ab = __double_as_longlong(a64);
+        info.z = (int)(ab & 0xffffffffll);
+        info.w = (int)(ab >> 32);
+      }
+      ainfo[lane] = info;
+      __syncwarp();
+      const int nch = min(32, pe - p0);
+      const unsigned maxlen = __reduce_max_sync(0xffffffffu, (unsigned)info.y);
+      if (maxlen <= 32u) {
+        // every referenced B row fits one pass of the warp: issue the loads of
+        // kBatch A entries before their updates (memory-level parallelism)
+        constexpr int kBatch = 8;
+        for (int t0 = 0; t0 < nch; t0 += kBatch) {
+          int cols[kBatch];
+          float2 bv[kBatch];
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            cols[u] = -1;
+            bv[u] = make_float2(0.f, 0.f);
+            const int t = t0 + u;
+            if (t < nch) {
+              const int2 in = *reinterpret_cast<const int2*>(&ainfo[t]);
+              if (lane < in.y) {
+                const int q = in.x + lane;
+                cols[u] = bcol[q];
+                if (df) {
+                  bv[u] = bspl[q];
+                } else {
+                  const long long bb = __double_as_longlong(bval[q]);
+                  bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)), __int_as_float((int)(bb >> 32)));
+                }
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            if (t0 + u < nch) {
+              if (cols[u] >= 0) {
+                const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
+                warp_vec_update<LOG2S>(keys, vals, cols[u], az, bv[u], df, status);
+              }
+              __syncwarp();  // this A entry's updates are visible before the next one's
+            }
+          }
+        }
+      } else {
+        for (int t = 0; t < nch; ++t) {
+          const int4 in = ainfo[t];
+          for (int q0 = 0; q0 < in.y; q0 += 32) {
+            const int q = in.x + q0 + lane;
+            if (q0 + lane < in.y) {
+              float2 b2;
+              if (df) {
+                b2 = bspl[q];
+              } else {
+                const long long bb = __double_as_longlong(bval[q]);
+                b2 = make_float2(__int_as_float((int)(bb & 0xffffffffll)), __int_as_float((int)(bb >> 32)));
+              }
+              warp_vec_update<LOG2S>(keys, vals, bcol[q], make_int2(in.z, in.w), b2, df, status);
+            }
+          }
+          __syncwarp();  // this A entry's updates are visible before the next one's
+        }
+      }
+      __syncwarp();
+    }
+    // compaction of occupied keys
+    int n = 0;
+#pragma unroll 4
+    for (int s0 = 0; s0 < S; s0 += 32) {
+      const int key = keys[s0 + lane];
+      const bool occ = key != kEmptyKey;
+      const unsigned bal = __ballot_sync(0xffffffffu, occ);
+      const int pos = n + __popc(bal & ((1u << lane) - 1u));
+      if (occ && pos < P) kst[pos] = key;
+      n += __popc(bal);
+    }
+    if (n != cnt && lane == 0) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    const int nn = max(0, min(min(n, cnt), P));
+    __syncwarp();
+    int v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int e = r * 32 + lane;
+      v[r] = e < nn ? kst[e] : 0x7fffffff;
+    }
+    warp_bitonic_regs<E>(v, lane);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int e = r * 32 + lane;
+      if (e < nn) {
+        const int slot = probe_find(keys, v[r], LOG2S);
+        g.c_colind[off + e] = v[r];
+        g.c_vals[off + e] = slot >= 0 ? out_value(vals[slot], df) : 0.0;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // CTA tier: warps of the CTA share one hash map; flattened traversal, atomics.
 // ---------------------------------------------------------------------------
 template <int LOG2S>
@@ -464,6 +757,21 @@ cudaError_t dispatch_team(const LaunchCtx& ctx, int log2s, const NumArgs& g) {
 }
 
 template <int LOG2S>
+cudaError_t launch_warp_vec(const LaunchCtx& ctx, const NumArgs& g) {
+  using G = WarpVecGeom<LOG2S>;
+  const size_t smem = (size_t)G::WPB * G::kWarpBytes;
+  auto kern = k_num_warp_vec<LOG2S>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  long long blocks = (g.nrows + G::WPB * 4 - 1) / (G::WPB * 4);
+  const long long cap = (long long)ctx.num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  kern<<<(unsigned)blocks, G::WPB * 32, smem, ctx.stream>>>(g);
+  return cudaGetLastError();
+}
+
+template <int LOG2S>
 cudaError_t launch_cta(const LaunchCtx& ctx, const NumArgs& g) {
   const size_t smem = (size_t)(1u << LOG2S) * (8 + 4 + 4);
   auto kern = k_num_cta<LOG2S>;
@@ -498,6 +806,18 @@ cudaError_t launch_numeric_bin(const LaunchCtx& ctx, const BinSpec& bin, const C
   while ((1 << log2s) < bin.slots) ++log2s;
   cudaError_t e = cudaErrorInvalidValue;
   if (bin.tier == kTierTeam) {
+    if (!bin.flat && bin.team == 32 && b_sorted && log2s >= 5 && log2s <= 9) {
+      timer_begin(ctx.timer, ctx.stream, "num_warp_vec");
+      switch (log2s) {
+        case 5: e = launch_warp_vec<5>(ctx, g); break;
+        case 6: e = launch_warp_vec<6>(ctx, g); break;
+        case 7: e = launch_warp_vec<7>(ctx, g); break;
+        case 8: e = launch_warp_vec<8>(ctx, g); break;
+        case 9: e = launch_warp_vec<9>(ctx, g); break;
+      }
+      timer_end(ctx.timer, ctx.stream);
+      return e;
+    }
     timer_begin(ctx.timer, ctx.stream, bin.flat ? "num_team_flat" : "num_team_vec");
     if (bin.flat) {
       if (bin.team == 8) e = dispatch_team<8, true>(ctx, log2s, g);

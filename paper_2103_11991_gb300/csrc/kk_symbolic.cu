@@ -69,6 +69,76 @@ k_sym_team(CsrView A, CsrView B, const int32_t* __restrict__ rows, int32_t nrows
   }
 }
 
+// Warp-per-row vector kernel: one warp per row, lanes split each B row, the
+// row's A entries staged once in shared memory (bs, len) and read back as
+// broadcasts.  Rows are split into contiguous shares per CTA so neighbouring
+// rows reuse B rows through L1.
+template <int LOG2S>
+__global__ void __launch_bounds__(256)
+k_sym_warp_vec(CsrView A, CsrView B, const int32_t* __restrict__ rows, int32_t nrows,
+               int32_t* __restrict__ cnt, int* status) {
+  constexpr int S = 1 << LOG2S;
+  constexpr int WPB = 8;
+  extern __shared__ __align__(16) int smem_w[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int* tab = smem_w + warp * (S + 64);
+  int2* ainfo = reinterpret_cast<int2*>(tab + S);
+  const int32_t* __restrict__ acol = A.colind;
+  const int32_t* __restrict__ brp = B.rowptr;
+  const int32_t* __restrict__ bcol = B.colind;
+  const int per_cta = (nrows + gridDim.x - 1) / gridDim.x;
+  const int r_begin = blockIdx.x * per_cta;
+  const int r_end = min(nrows, r_begin + per_cta);
+  for (int r = r_begin + warp; r < r_end; r += WPB) {
+    const int i = rows[r];
+#pragma unroll
+    for (int s = lane * 4; s < S; s += 128) *reinterpret_cast<int4*>(&tab[s]) = make_int4(-1, -1, -1, -1);
+    __syncwarp();
+    const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
+    int mine = 0;
+    for (int p0 = pa; p0 < pe; p0 += 32) {
+      const int p = p0 + lane;
+      int2 info = make_int2(0, 0);
+      if (p < pe) {
+        const int j = acol[p];
+        info.x = brp[j];
+        info.y = brp[j + 1] - info.x;
+      }
+      ainfo[lane] = info;
+      __syncwarp();
+      const int nch = min(32, pe - p0);
+      const unsigned maxlen = __reduce_max_sync(0xffffffffu, (unsigned)info.y);
+      if (maxlen <= 32u) {
+        // issue the loads of kBatch A entries' B rows before inserting them
+        constexpr int kBatch = 8;
+        for (int t0 = 0; t0 < nch; t0 += kBatch) {
+          int cols[kBatch];
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            cols[u] = -1;
+            if (t0 + u < nch) {
+              const int2 in = ainfo[t0 + u];
+              if (lane < in.y) cols[u] = bcol[in.x + lane];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u)
+            if (cols[u] >= 0) mine += set_insert(tab, cols[u], LOG2S, status);
+        }
+      } else {
+        for (int t = 0; t < nch; ++t) {
+          const int2 in = ainfo[t];
+          for (int q0 = lane; q0 < in.y; q0 += 32) mine += set_insert(tab, bcol[in.x + q0], LOG2S, status);
+        }
+      }
+      __syncwarp();
+    }
+    mine = team_sum<32>(mine, 0xffffffffu);
+    if (lane == 0) cnt[i] = mine;
+    __syncwarp();
+  }
+}
+
 template <int LOG2S>
 __global__ void __launch_bounds__(kCtaBlock)
 k_sym_cta(CsrView A, CsrView B, const int32_t* __restrict__ rows, int32_t nrows,
@@ -191,6 +261,21 @@ cudaError_t dispatch_team_slots(const LaunchCtx& ctx, int log2s, const CsrView& 
 }
 
 template <int LOG2S>
+cudaError_t launch_warp_vec(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                            const int32_t* rows, int32_t nrows, int32_t* cnt) {
+  const size_t smem = (size_t)8 * ((1u << LOG2S) + 64) * sizeof(int);
+  auto kern = k_sym_warp_vec<LOG2S>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  long long blocks = (nrows + 31) / 32;
+  const long long cap = (long long)ctx.num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  kern<<<(unsigned)blocks, 256, smem, ctx.stream>>>(A, B, rows, nrows, cnt, ctx.status);
+  return cudaGetLastError();
+}
+
+template <int LOG2S>
 cudaError_t launch_cta(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
                        const int32_t* rows, int32_t nrows, int32_t* cnt) {
   const size_t smem = (size_t)(1u << LOG2S) * sizeof(int);
@@ -220,6 +305,22 @@ cudaError_t launch_symbolic_bin(const LaunchCtx& ctx, const BinSpec& bin, const 
   if (nrows <= 0) return cudaSuccess;
   int log2s = 0;
   while ((1 << log2s) < bin.slots) ++log2s;
+  if (bin.tier == kTierTeam && !bin.flat && bin.team == 32 && log2s >= 5 && log2s <= 12) {
+    timer_begin(ctx.timer, ctx.stream, "sym_warp_vec");
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (log2s) {
+      case 5: e = launch_warp_vec<5>(ctx, A, B, rows, nrows, cnt); break;
+      case 6: e = launch_warp_vec<6>(ctx, A, B, rows, nrows, cnt); break;
+      case 7: e = launch_warp_vec<7>(ctx, A, B, rows, nrows, cnt); break;
+      case 8: e = launch_warp_vec<8>(ctx, A, B, rows, nrows, cnt); break;
+      case 9: e = launch_warp_vec<9>(ctx, A, B, rows, nrows, cnt); break;
+      case 10: e = launch_warp_vec<10>(ctx, A, B, rows, nrows, cnt); break;
+      case 11: e = launch_warp_vec<11>(ctx, A, B, rows, nrows, cnt); break;
+      case 12: e = launch_warp_vec<12>(ctx, A, B, rows, nrows, cnt); break;
+    }
+    timer_end(ctx.timer, ctx.stream);
+    return e;
+  }
   if (bin.tier == kTierTeam) {
     timer_begin(ctx.timer, ctx.stream, bin.flat ? "sym_team_flat" : "sym_team_vec");
     cudaError_t e = cudaErrorInvalidValue;

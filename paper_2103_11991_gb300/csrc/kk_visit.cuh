@@ -71,6 +71,7 @@ __device__ __forceinline__ void visit_products(int pa, int pe, int first_chunk, 
         const int l = __shfl_sync(mask, bl, t, TEAM);
         const Payload pt = shfl_payload(mask, pay, t, TEAM);
         for (int q = tl; q < l; q += TEAM) visit(pt, p0 + t, s + q);
+        __syncwarp(mask);  // updates of this A entry are visible to the next one
       }
     }
   }
