@@ -77,13 +77,16 @@ typedef struct {
   int32_t arith;          /* kk_arith */
   int32_t debug_checks;   /* 1: extra device-side consistency checks in numeric */
   int32_t timing;         /* 1: record CUDA events around every kernel (see kk_spgemm_kernel_times) */
-  int32_t force_tier;     /* testing: -1 = automatic; 0 = team hash, 1 = CTA hash, 2 = dense chunks */
+  int32_t force_tier;     /* testing: -1 = automatic; 0 = team hash, 1 = CTA hash, 2 = dense chunks,
+                             3 = window wherever a row qualifies (team hash elsewhere) */
   int32_t team_vec_min_len; /* mean B-row length from which a team walks B rows lane-parallel (else flattened) */
   int32_t sym_team_max_flop;  /* rows up to this flop bound use a team hash in the symbolic phase */
   int32_t sym_cta_max_flop;   /* rows up to this flop bound use a CTA hash; above it dense chunks */
   int32_t num_team_max_nnz;   /* rows up to this nnz(C(i,:)) use a team hash in the numeric phase */
   int32_t num_cta_max_nnz;    /* rows up to this nnz use a CTA hash; above it dense chunks */
-  int32_t reserved[7];
+  int32_t use_window;         /* 1: rows whose column span fits a shared-memory window use the
+                                 dense window accumulator (needs B rows sorted) */
+  int32_t reserved[6];
 } kk_spgemm_options;
 
 typedef struct kk_spgemm_handle_s* kk_spgemm_handle;
@@ -147,7 +150,8 @@ kk_status kk_spgemm_kernel_times(kk_spgemm_handle h, int32_t max_kernels, const 
  * (stats[0..2] symbolic team/CTA/dense, stats[3..5] numeric team/CTA/dense),
  * stats[6] = total flops (multiply-adds), stats[7] = 1 if B's rows were
  * strictly ascending, stats[8] / stats[9] = kernels launched by the last
- * symbolic / numeric call, stats[10..15] reserved (0). */
+ * symbolic / numeric call, stats[10] / stats[11] = rows in the window tier of
+ * the symbolic / numeric phase, stats[12..15] reserved (0). */
 kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[16]);
 
 #ifdef __cplusplus

@@ -126,14 +126,27 @@ constexpr uint8_t kSkipBin = 0xFF;
 
 // Device-side classifier: first bin whose hi bound covers q and whose mode
 // (0 = vector only, 1 = flattened only, 2 = either) admits the row's mode.
+// Window bins (window tier) are tried first: a row qualifies for window class
+// w when B's rows are sorted, its span fits kWindowBits[w], the window is not
+// too wide for its flop count, and (numeric) its nnz fits the dense value slots.
 struct BinTable {
   int32_t nb;
   long long hi[kMaxBins];
   int32_t mode[kMaxBins];
+  int32_t nwin;
+  int32_t win_bits[kNumWindowClasses];
+  int32_t win_bin[kNumWindowClasses];
+  long long win_max_q;
 };
 
-__device__ __forceinline__ uint8_t classify(const BinTable& t, long long q, int flat) {
+__device__ __forceinline__ uint8_t classify(const BinTable& t, long long q, int flat, int span,
+                                            long long flop, int sorted) {
   if (q <= 0) return kSkipBin;
+  if (sorted && span > 0 && q <= t.win_max_q) {
+    for (int w = 0; w < t.nwin; ++w)
+      if (span <= t.win_bits[w] && (long long)t.win_bits[w] <= (long long)kWindowFlopRatio * flop)
+        return (uint8_t)t.win_bin[w];
+  }
   for (int b = 0; b < t.nb; ++b)
     if (q <= t.hi[b] && (t.mode[b] == 2 || t.mode[b] == flat)) return (uint8_t)b;
   return (uint8_t)(t.nb - 1);
@@ -174,10 +187,14 @@ __global__ void k_analyze_b(CsrView B, int32_t* sorted_flag, int* status) {
 }
 
 // A rows: flop bound, column range, symbolic bin id; optional total flops.
-__global__ void k_analyze_a(CsrView A, const int32_t* __restrict__ brp, int32_t nb_rows,
-                            BinTable tab, int32_t vec_min_len, long long* __restrict__ flop,
-                            uint8_t* __restrict__ bin, unsigned long long* total_flop,
+__global__ void k_analyze_a(CsrView A, const int32_t* __restrict__ brp,
+                            const int32_t* __restrict__ bcol, int32_t nb_rows,
+                            const int32_t* __restrict__ b_sorted, BinTable tab,
+                            int32_t vec_min_len, long long* __restrict__ flop,
+                            uint8_t* __restrict__ bin, int32_t* __restrict__ row_lo,
+                            int32_t* __restrict__ row_span, unsigned long long* total_flop,
                             int* status) {
+  const int sorted = *b_sorted;
   const int tl = threadIdx.x % kAnaTeam;
   const unsigned mask = team_mask<kAnaTeam>();
   const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kAnaTeam;
@@ -189,6 +206,7 @@ __global__ void k_analyze_a(CsrView A, const int32_t* __restrict__ brp, int32_t 
     long long f = 0;
     int bad = 0;
     int pa = 0, pe = 0;
+    int lo = 0x7fffffff, hi = -1;
     if (r < A.m) {
       pa = A.rowptr[r];
       pe = A.rowptr[r + 1];
@@ -202,16 +220,29 @@ __global__ void k_analyze_a(CsrView A, const int32_t* __restrict__ brp, int32_t 
           bad = 1;
           continue;
         }
-        f += brp[j + 1] - brp[j];
+        const int bs = brp[j], be = brp[j + 1];
+        f += be - bs;
+        if (sorted && be > bs) {
+          lo = min(lo, bcol[bs]);
+          hi = max(hi, bcol[be - 1]);
+        }
       }
     }
 #pragma unroll
-    for (int o = kAnaTeam / 2; o > 0; o >>= 1) f += __shfl_xor_sync(mask, f, o, kAnaTeam);
+    for (int o = kAnaTeam / 2; o > 0; o >>= 1) {
+      f += __shfl_xor_sync(mask, f, o, kAnaTeam);
+      lo = min(lo, __shfl_xor_sync(mask, lo, o, kAnaTeam));
+      hi = max(hi, __shfl_xor_sync(mask, hi, o, kAnaTeam));
+    }
     if (bad) set_status(status, KK_ERR_BAD_INDEX);
     if (r < A.m && tl == 0) {
       flop[r] = f;
+      const long long span = hi >= lo ? (long long)hi - lo + 1 : 0;
+      const int sp = span > 0x7fffffff ? 0x7fffffff : (int)span;
+      row_lo[r] = hi >= lo ? lo : 0;
+      row_span[r] = sp;
       const int flat = (f < (long long)vec_min_len * (pe - pa)) ? 1 : 0;
-      bin[r] = classify(tab, f, flat);
+      bin[r] = classify(tab, f, flat, sp, f, sorted);
       acc += (unsigned long long)f;
     }
   }
@@ -385,8 +416,10 @@ k_scan_top(int32_t nblk, long long* __restrict__ blk_sum, long long* __restrict_
 __global__ void __launch_bounds__(kScanBlock)
 k_scan_final(int32_t m, const int32_t* __restrict__ cnt, const long long* __restrict__ blk_off,
              const long long* __restrict__ flop, const int32_t* __restrict__ arp,
+             const int32_t* __restrict__ row_span, const int32_t* __restrict__ b_sorted,
              int32_t vec_min_len, BinTable ntab, int64_t* __restrict__ rowptr,
              uint8_t* __restrict__ nbin) {
+  const int sorted = *b_sorted;
   __shared__ long long scratch[33];
   const long long base = (long long)blockIdx.x * kScanRows + (long long)threadIdx.x * kScanPer;
   int v[kScanPer];
@@ -403,7 +436,7 @@ k_scan_final(int32_t m, const int32_t* __restrict__ cnt, const long long* __rest
       rowptr[r] = run;
       const int nza = arp[r + 1] - arp[r];
       const int flat = (flop[r] < (long long)vec_min_len * nza) ? 1 : 0;
-      nbin[r] = classify(ntab, v[t], flat);
+      nbin[r] = classify(ntab, v[t], flat, row_span[r], flop[r], sorted);
       if (r == m - 1) rowptr[m] = run + v[t];
     }
     run += v[t];
@@ -450,6 +483,8 @@ struct kk_spgemm_handle_s {
   DevBuf d_srows;      // int32[m]
   DevBuf d_nrows;      // int32[m]
   DevBuf d_cnt;        // int32[m]
+  DevBuf d_rowlo;      // int32[m]  first column of each row's span
+  DevBuf d_span;       // int32[m]  span width (0 for rows without products)
   DevBuf d_blk;        // int32[kMaxBins * nblk]
   DevBuf d_binstart;   // int32[2 * (kMaxBins + 1)]
   DevBuf d_scan;       // long long[nblk]
@@ -557,12 +592,30 @@ void build_bins(const kk_spgemm_options& o, bool numeric, std::vector<BinSpec>& 
     out.push_back(BinSpec{kTierDense, 512, 16384, 1, 0, (long long)9e18});
   }
   for (size_t b = 0; b < out.size(); ++b) out[b].lo = b == 0 ? 1 : out[b - 1].hi + 1;
+  // window bins last (looked up through the table's window classes)
+  if (o.use_window && (force == -1 || force == 3)) {
+    for (int w = 0; w < kNumWindowClasses; ++w)
+      out.push_back(BinSpec{kTierWindow, 128, kWindowBits[w], 0, 0,
+                            numeric ? kWindowMaxNnz : (long long)9e18});
+  }
 }
 
 BinTable to_table(const std::vector<BinSpec>& bins) {
   BinTable t{};
-  t.nb = (int32_t)bins.size();
+  t.nb = 0;
+  t.nwin = 0;
+  t.win_max_q = 0;
   for (size_t b = 0; b < bins.size(); ++b) {
+    if (bins[b].tier == kTierWindow) {
+      t.win_bits[t.nwin] = bins[b].slots;
+      t.win_bin[t.nwin] = (int32_t)b;
+      t.win_max_q = bins[b].hi;
+      ++t.nwin;
+    } else {
+      t.nb = (int32_t)b + 1;
+    }
+  }
+  for (int b = 0; b < t.nb; ++b) {
     t.hi[b] = bins[b].hi;
     t.mode[b] = bins[b].tier == kTierTeam ? bins[b].flat : 2;
   }
@@ -570,7 +623,8 @@ BinTable to_table(const std::vector<BinSpec>& bins) {
 }
 
 LaunchCtx ctx_of(kk_spgemm_handle h) {
-  return LaunchCtx{h->stream, h->timer, &h->d_misc.as<Misc>()->status, h->num_sms, h->max_smem};
+  return LaunchCtx{h->stream, h->timer, &h->d_misc.as<Misc>()->status, h->num_sms, h->max_smem,
+                   h->d_rowlo.as<int32_t>()};
 }
 
 int grid_for(long long work, int per_block, int cap) {
@@ -644,6 +698,7 @@ kk_status kk_spgemm_options_default(kk_spgemm_options* opt) {
   opt->sym_cta_max_flop = 24576;
   opt->num_team_max_nnz = 1024;
   opt->num_cta_max_nnz = 4096;
+  opt->use_window = 1;
   return KK_OK;
 }
 
@@ -654,7 +709,7 @@ kk_status kk_spgemm_handle_create(kk_spgemm_handle* out, const kk_spgemm_options
   kk_spgemm_handle h = new (std::nothrow) kk_spgemm_handle_s();
   if (!h) return KK_ERR_OOM;
   if (opt) h->opt = *opt; else kk_spgemm_options_default(&h->opt);
-  if (h->opt.arith < 0 || h->opt.arith > 2 || h->opt.force_tier < -1 || h->opt.force_tier > 2 ||
+  if (h->opt.arith < 0 || h->opt.arith > 2 || h->opt.force_tier < -1 || h->opt.force_tier > 3 ||
       h->opt.team_vec_min_len < 0) {
     delete h;
     return KK_ERR_INVALID_ARG;
@@ -722,6 +777,8 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   KK_CUDA(h, h->d_srows.ensure(sizeof(int32_t) * (size_t)(m > 0 ? m : 1)), "alloc rows");
   KK_CUDA(h, h->d_nrows.ensure(sizeof(int32_t) * (size_t)(m > 0 ? m : 1)), "alloc rows");
   KK_CUDA(h, h->d_cnt.ensure(sizeof(int32_t) * (size_t)(m > 0 ? m : 1)), "alloc counts");
+  KK_CUDA(h, h->d_rowlo.ensure(sizeof(int32_t) * (size_t)(m > 0 ? m : 1)), "alloc spans");
+  KK_CUDA(h, h->d_span.ensure(sizeof(int32_t) * (size_t)(m > 0 ? m : 1)), "alloc spans");
   const int nblk_scan = (int)((m + kScanRows - 1) / kScanRows);
   KK_CUDA(h, h->d_scan.ensure(sizeof(long long) * (size_t)(nblk_scan > 0 ? nblk_scan : 1)), "alloc scan");
 
@@ -739,8 +796,9 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
       k_analyze_b<<<grid_for((long long)bv.m * kAnaTeam, 256, h->num_sms * 8), 256, 0, s>>>(
           bv, &dm->sorted, &dm->status);
     k_analyze_a<<<grid_for((long long)m * kAnaTeam, 256, h->num_sms * 8), 256, 0, s>>>(
-        av, bv.rowptr, bv.m, to_table(h->sym_bins), h->opt.team_vec_min_len,
-        h->d_flop.as<long long>(), h->d_sbin.as<uint8_t>(), &dm->total_flop, &dm->status);
+        av, bv.rowptr, bv.colind, bv.m, &dm->sorted, to_table(h->sym_bins), h->opt.team_vec_min_len,
+        h->d_flop.as<long long>(), h->d_sbin.as<uint8_t>(), h->d_rowlo.as<int32_t>(),
+        h->d_span.as<int32_t>(), &dm->total_flop, &dm->status);
     timer_end(h->timer, s);
     KK_CUDA(h, cudaGetLastError(), "analyze launch");
     if ((st = run_binning(h, m, h->d_sbin.as<uint8_t>(), nbs, h->d_srows.as<int32_t>(), sym_start)) != KK_OK)
@@ -761,17 +819,21 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   if (m > 0) {
     KK_CUDA(h, cudaMemsetAsync(h->d_cnt.p, 0, sizeof(int32_t) * (size_t)m, s), "memset counts");
     LaunchCtx ctx = ctx_of(h);
-    int64_t tier_rows[3] = {0, 0, 0};
+    int64_t tier_rows[4] = {0, 0, 0, 0};
     for (int b = 0; b < nbs; ++b) {
       const int cnt = h_start[b + 1] - h_start[b];
       if (cnt <= 0) continue;
       tier_rows[h->sym_bins[b].tier] += cnt;
-      cudaError_t e = launch_symbolic_bin(ctx, h->sym_bins[b], av, bv, h->b_sorted,
-                                          h->d_srows.as<int32_t>() + h_start[b], cnt,
-                                          h->d_cnt.as<int32_t>());
+      const int32_t* rows = h->d_srows.as<int32_t>() + h_start[b];
+      cudaError_t e = h->sym_bins[b].tier == kTierWindow
+                          ? launch_symbolic_window(ctx, h->sym_bins[b], av, bv, rows, cnt,
+                                                   h->d_cnt.as<int32_t>())
+                          : launch_symbolic_bin(ctx, h->sym_bins[b], av, bv, h->b_sorted, rows, cnt,
+                                                h->d_cnt.as<int32_t>());
       if (e != cudaSuccess) return cuda_fail(h, e, "symbolic launch");
     }
     for (int t = 0; t < 3; ++t) h->stats[t] = tier_rows[t];
+    h->stats[10] = tier_rows[kTierWindow];
     int64_t nb_launched = 0;
     for (int b = 0; b < nbs; ++b) nb_launched += (h_start[b + 1] - h_start[b]) > 0 ? 1 : 0;
     // analyze (2) + binning (3) + symbolic bins + scan (3) + numeric binning (3)
@@ -782,7 +844,8 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
     k_scan_top<<<1, 1024, 0, s>>>(nblk_scan, h->d_scan.as<long long>(), &dm->grand);
     k_scan_final<<<nblk_scan, kScanBlock, 0, s>>>(
         m, h->d_cnt.as<int32_t>(), h->d_scan.as<long long>(), h->d_flop.as<long long>(), av.rowptr,
-        h->opt.team_vec_min_len, to_table(h->num_bins), c_rowptr, h->d_nbin.as<uint8_t>());
+        h->d_span.as<int32_t>(), &dm->sorted, h->opt.team_vec_min_len, to_table(h->num_bins),
+        c_rowptr, h->d_nbin.as<uint8_t>());
     timer_end(h->timer, s);
     KK_CUDA(h, cudaGetLastError(), "scan launch");
     if ((st = run_binning(h, m, h->d_nbin.as<uint8_t>(), nbn, h->d_nrows.as<int32_t>(), num_start)) != KK_OK)
@@ -798,9 +861,10 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
   h->nnz_c = m > 0 ? hm->grand : 0;
   h->num_start.assign(h_start, h_start + nbn + 1);
-  int64_t ntier[3] = {0, 0, 0};
+  int64_t ntier[4] = {0, 0, 0, 0};
   for (int b = 0; b < nbn; ++b) ntier[h->num_bins[b].tier] += h_start[b + 1] - h_start[b];
   for (int t = 0; t < 3; ++t) h->stats[3 + t] = ntier[t];
+  h->stats[11] = ntier[kTierWindow];
   h->am = m;
   h->an = A->n;
   h->bn = B->n;
@@ -848,10 +912,13 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
     const int cnt = h->num_start[b + 1] - h->num_start[b];
     if (cnt <= 0) continue;
     h->stats[9] += 1;
-    cudaError_t e = launch_numeric_bin(ctx, h->num_bins[b], av, bv, h->b_sorted, bsplit,
-                                       &dm->range_bad, arith, c_rowptr,
-                                       h->d_nrows.as<int32_t>() + h->num_start[b], cnt, c_colind,
-                                       c_vals, h->opt.debug_checks);
+    const int32_t* rows = h->d_nrows.as<int32_t>() + h->num_start[b];
+    cudaError_t e = h->num_bins[b].tier == kTierWindow
+                        ? launch_numeric_window(ctx, h->num_bins[b], av, bv, bsplit, &dm->range_bad,
+                                                arith, c_rowptr, rows, cnt, c_colind, c_vals)
+                        : launch_numeric_bin(ctx, h->num_bins[b], av, bv, h->b_sorted, bsplit,
+                                             &dm->range_bad, arith, c_rowptr, rows, cnt, c_colind,
+                                             c_vals, h->opt.debug_checks);
     if (e != cudaSuccess) return cuda_fail(h, e, "numeric launch");
   }
   return KK_OK;
@@ -905,6 +972,8 @@ kk_status kk_spgemm_destroy(kk_spgemm_handle h) {
   h->d_srows.release();
   h->d_nrows.release();
   h->d_cnt.release();
+  h->d_rowlo.release();
+  h->d_span.release();
   h->d_blk.release();
   h->d_binstart.release();
   h->d_scan.release();

@@ -19,6 +19,7 @@ struct LaunchCtx {
   int* status;         // device status word
   int num_sms;
   int max_smem_optin;
+  const int32_t* row_lo;  // first column of each row's span window (window tier)
 };
 
 struct CsrView {
@@ -29,7 +30,14 @@ struct CsrView {
 };
 
 // Accumulator tiers.
-enum Tier : int32_t { kTierTeam = 0, kTierCta = 1, kTierDense = 2 };
+enum Tier : int32_t { kTierTeam = 0, kTierCta = 1, kTierDense = 2, kTierWindow = 3 };
+
+// Window tier: a row whose columns of C all lie in [row_lo, row_lo + W) gets a
+// dense bit vector of W bits (plus per-word ranks in the numeric phase).
+constexpr int kNumWindowClasses = 4;
+constexpr int32_t kWindowBits[kNumWindowClasses] = {4096, 16384, 49152, 65536};
+constexpr int32_t kWindowMaxNnz = 256;   // numeric window rows: nnz(C(i,:)) <= this
+constexpr int32_t kWindowFlopRatio = 128;  // window used only when W <= ratio * flop
 
 // One bin of rows: its tier and the accumulator geometry.
 struct BinSpec {
@@ -55,6 +63,16 @@ cudaError_t launch_numeric_bin(const LaunchCtx& ctx, const BinSpec& bin, const C
                                const int32_t* b_range_bad, int32_t arith,
                                const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
                                int32_t* c_colind, double* c_vals, int32_t debug_checks);
+
+// Window-tier launches (kk_window.cu).
+cudaError_t launch_symbolic_window(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,
+                                   const CsrView& B, const int32_t* rows, int32_t nrows,
+                                   int32_t* cnt);
+cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,
+                                  const CsrView& B, const float2* b_split,
+                                  const int32_t* b_range_bad, int32_t arith,
+                                  const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
+                                  int32_t* c_colind, double* c_vals);
 
 // Shared-memory bytes a bin's kernel needs per CTA (0 if it does not fit).
 size_t symbolic_smem_bytes(const BinSpec& bin);

@@ -48,7 +48,8 @@ class KkOptions(ctypes.Structure):
                 ("timing", ctypes.c_int32), ("force_tier", ctypes.c_int32),
                 ("team_vec_min_len", ctypes.c_int32), ("sym_team_max_flop", ctypes.c_int32),
                 ("sym_cta_max_flop", ctypes.c_int32), ("num_team_max_nnz", ctypes.c_int32),
-                ("num_cta_max_nnz", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("num_cta_max_nnz", ctypes.c_int32), ("use_window", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -184,7 +185,8 @@ def kk_spgemm_stats(h) -> dict:
     arr = (ctypes.c_int64 * 16)()
     _check(load_library().kk_spgemm_stats(h, arr), h)
     keys = ["sym_team_rows", "sym_cta_rows", "sym_dense_rows", "num_team_rows", "num_cta_rows",
-            "num_dense_rows", "flops", "b_sorted", "launches_sym", "launches_num"]
+            "num_dense_rows", "flops", "b_sorted", "launches_sym", "launches_num",
+            "sym_window_rows", "num_window_rows"]
     return {k: int(arr[i]) for i, k in enumerate(keys)}
 
 

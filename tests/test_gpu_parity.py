@@ -12,7 +12,7 @@ from tests._util import assert_structure_equal, assert_values_within
 pytestmark = pytest.mark.gpu
 
 ARITHS = [1, 2]  # KK_ARITH_FP64, KK_ARITH_DF32
-TIERS = [-1, 0, 1, 2]
+TIERS = [-1, 0, 1, 2, 3]
 
 
 @pytest.mark.parametrize("arith", ARITHS)
@@ -46,11 +46,29 @@ def test_stencil2d_64_exact(arith):
     assert ref.nnz == 51972
 
 
+@pytest.mark.parametrize("window", [0, 1])
 @pytest.mark.parametrize("arith", ARITHS)
-def test_stencil3d27_small_exact(arith):
+def test_stencil3d27_small_exact(arith, window):
     d = I.config_inputs("stencil3d27_100", scale=22)
-    rp, ci, va, _, _ = run_gpu(d["A"], d["B"], arith=arith)
+    rp, ci, va, _, st = run_gpu(d["A"], d["B"], arith=arith, use_window=window)
     check_against_oracle(d["A"], d["B"], rp, ci, va, exact=True)
+    if window:
+        assert st["sym_window_rows"] == d["A"].m and st["num_window_rows"] == d["A"].m
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+def test_window_tier_random_values(arith):
+    # stencil structure with random values, and random rows with a narrow span
+    d = I.config_inputs("stencil3d27_100", scale=14)
+    A = d["A"].copy()
+    A.vals = I.uniform01(3, "w", A.nnz) * 2 - 1
+    rp, ci, va, _, st = run_gpu(A, A, arith=arith, force_tier=3)
+    check_against_oracle(A, A, rp, ci, va)
+    assert st["num_window_rows"] > 0
+    B = I.random_rows(3000, 3000, 20, 40, seed=4)
+    A2 = I.random_rows(400, 3000, 5, 30, seed=5)
+    rp, ci, va, _, st = run_gpu(A2, B, arith=arith, force_tier=3)
+    check_against_oracle(A2, B, rp, ci, va)
 
 
 @pytest.mark.parametrize("tier", TIERS)
@@ -65,7 +83,8 @@ def test_rmat_mixed_tiers_auto():
     A = I.rmat(13, 16, seed=5)
     rp, ci, va, _, st = run_gpu(A, A)
     check_against_oracle(A, A, rp, ci, va)
-    assert st["sym_team_rows"] > 0 and st["num_team_rows"] > 0
+    assert st["sym_team_rows"] + st["sym_window_rows"] > 0
+    assert st["num_team_rows"] + st["num_window_rows"] > 0
     assert st["num_cta_rows"] + st["num_dense_rows"] > 0
 
 
