@@ -86,7 +86,9 @@ typedef struct {
   int32_t num_cta_max_nnz;    /* rows up to this nnz use a CTA hash; above it dense chunks */
   int32_t use_window;         /* 1: rows whose column span fits a shared-memory window use the
                                  dense window accumulator (needs B rows sorted) */
-  int32_t reserved[6];
+  int32_t batched_graph;      /* 1: batched phases are captured into CUDA graphs and replayed
+                                 (needs a non-default stream) */
+  int32_t reserved[5];
 } kk_spgemm_options;
 
 typedef struct kk_spgemm_handle_s* kk_spgemm_handle;
@@ -151,7 +153,10 @@ kk_status kk_spgemm_kernel_times(kk_spgemm_handle h, int32_t max_kernels, const 
  * stats[6] = total flops (multiply-adds), stats[7] = 1 if B's rows were
  * strictly ascending, stats[8] / stats[9] = kernels launched by the last
  * symbolic / numeric call, stats[10] / stats[11] = rows in the window tier of
- * the symbolic / numeric phase, stats[12..15] reserved (0). */
+ * the symbolic / numeric phase; after a learned symbolic call (kk_learned.h)
+ * stats[12] = rows sent to the speculative one-pass, stats[13] = of those, rows
+ * that overflowed and were re-run, stats[14] = rows predicted heavy (plain
+ * path), stats[15] = staging entries. */
 kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[16]);
 
 #ifdef __cplusplus

@@ -10,7 +10,8 @@ For row i of A (C = A*B) with referenced B rows R_i = {j : j in A(i,:)}:
   span   = max_j maxcol(B(j,:)) - min_j mincol(B(j,:)) + 1 over non-empty B rows
            (0 if there is none): every column of C(i,:) lies in that window
 Features, in this order (F = 8), each log2(1 + value):
-  nnzA, flop, maxlen, mean, maxlen - minlen, span, min(flop, span), k
+  nnzA, flop, maxlen, mean, maxlen - minlen, span, min(flop, span),
+  min(flop, span, k)
 Label: the capacity class of c = nnz(C(i,:)): class 0 holds c <= 16, class t
 holds 16*2^(t-1) < c <= 16*2^t, capped at NUM_CLASSES - 1.  Capacity of class
 t is 16*2^t entries.
@@ -44,7 +45,7 @@ def row_features(A, B) -> np.ndarray:
         mean = flop / nnza if nnza else 0.0
         ne = js[lens > 0]
         span = int(bmax[ne].max() - bmin[ne].min() + 1) if len(ne) else 0
-        vals = [nnza, flop, mx, mean, mx - mn, span, min(flop, span), B.n]
+        vals = [nnza, flop, mx, mean, mx - mn, span, min(flop, span), min(flop, span, B.n)]
         out[i] = np.log2(1.0 + np.asarray(vals, dtype=np.float64))
     return out
 

@@ -20,6 +20,8 @@
 
 #include "kk_internal.h"
 #include "kk_device.cuh"
+#include "kk_batched.h"
+#include "kk_learned.h"
 
 namespace kk {
 
@@ -434,12 +436,30 @@ k_scan_final(int32_t m, const int32_t* __restrict__ cnt, const long long* __rest
     const long long r = base + t;
     if (r < m) {
       rowptr[r] = run;
-      const int nza = arp[r + 1] - arp[r];
-      const int flat = (flop[r] < (long long)vec_min_len * nza) ? 1 : 0;
-      nbin[r] = classify(ntab, v[t], flat, row_span[r], flop[r], sorted);
+      if (nbin) {
+        const int nza = arp[r + 1] - arp[r];
+        const int flat = (flop[r] < (long long)vec_min_len * nza) ? 1 : 0;
+        nbin[r] = classify(ntab, v[t], flat, row_span[r], flop[r], sorted);
+      }
       if (r == m - 1) rowptr[m] = run + v[t];
     }
     run += v[t];
+  }
+}
+
+// Symbolic bin of every row from its flop bound and span (learned form: the
+// rows left to the plain path are picked from these afterwards).
+__global__ void k_sym_classify(int32_t m, const long long* __restrict__ flop,
+                               const int32_t* __restrict__ arp, const int32_t* __restrict__ row_span,
+                               const int32_t* __restrict__ b_sorted, BinTable tab,
+                               int32_t vec_min_len, uint8_t* __restrict__ bin) {
+  const int sorted = *b_sorted;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < m;
+       r += (long long)gridDim.x * blockDim.x) {
+    const long long f = flop[r];
+    const int nza = arp[r + 1] - arp[r];
+    const int flat = (f < (long long)vec_min_len * nza) ? 1 : 0;
+    bin[r] = classify(tab, f, flat, row_span[r], f, sorted);
   }
 }
 
@@ -489,6 +509,36 @@ struct kk_spgemm_handle_s {
   DevBuf d_binstart;   // int32[2 * (kMaxBins + 1)]
   DevBuf d_scan;       // long long[nblk]
   DevBuf d_bsplit;     // float2[nnzB]
+  // learned form
+  DevBuf d_params;     // float[KK_MLP_NUM_PARAMS]
+  bool have_pred = false;
+  float quantile = 0.95f;
+  DevBuf d_lbin;       // uint8[m]  learned bin (one-pass class / heavy / none)
+  DevBuf d_plain;      // uint8[m]  1 = row takes the plain path
+  DevBuf d_cap;        // int32[m]  staging capacity
+  DevBuf d_soff;       // int64[m+1] staging offsets
+  DevBuf d_scol;       // int32[staging]
+  DevBuf d_sval;       // double[staging]
+  DevBuf d_sball;      // uint8[m]  symbolic bins of all rows
+  DevBuf d_nbin2;      // uint8[m]  numeric bins of plain-path rows
+  DevBuf d_lrows;      // int32[m]  learned bins' row lists
+  DevBuf d_lrows2;     // int32[m]  plain-path numeric bins' row lists
+  DevBuf d_mm;         // int2[n]   B row min/max columns (features)
+  bool learned_valid = false;
+  std::vector<int32_t> lnum_start;
+  // batched form
+  DevBuf d_bdesc, d_rowpair, d_bflop, d_bsbin, d_bnbin, d_bsrows, d_bnrows, d_bcnt, d_btiles, d_bstart,
+      d_bqueue, d_bsplit2, d_boff;
+  void* h_bdesc = nullptr;   // pinned PairDesc[count] (symbolic upload)
+  void* h_bdesc2 = nullptr;  // pinned PairDesc[count] (numeric upload, device flags included)
+  void* h_boff = nullptr;    // pinned int64[count + 1]
+  size_t h_bcap = 0;         // pairs the pinned buffers hold
+  int32_t b_count = 0;
+  long long b_R = 0, b_total = 0, b_nnzb = 0;
+  bool b_valid = false;
+  BBinTable b_sym{}, b_num{};
+  cudaGraphExec_t g_sym = nullptr, g_num = nullptr;
+  unsigned long long g_sym_key = 0, g_num_key = 0;
   void* h_pinned = nullptr;  // host staging for readbacks
   // symbolic state
   bool have_symbolic = false;
@@ -510,6 +560,7 @@ struct Misc {
   int32_t pad;
   unsigned long long total_flop;
   long long grand;
+  long long grand2;
 };
 
 kk_status fail(kk_spgemm_handle h, kk_status s, const std::string& msg) {
@@ -699,6 +750,7 @@ kk_status kk_spgemm_options_default(kk_spgemm_options* opt) {
   opt->num_team_max_nnz = 1024;
   opt->num_cta_max_nnz = 4096;
   opt->use_window = 1;
+  opt->batched_graph = 1;
   return KK_OK;
 }
 
@@ -924,6 +976,506 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
   return KK_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Learned form (kk_learned.h)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+// Exclusive scan of int32 counts into int64 offsets out[0..m] (out[m] = total,
+// also written to *grand); nbin (nullable) receives numeric bin ids.
+kk_status run_scan(kk_spgemm_handle h, int32_t m, const int32_t* cnt, int64_t* out, long long* grand,
+                   const CsrView& av, uint8_t* nbin) {
+  cudaStream_t s = h->stream;
+  const int nblk = (int)((m + kScanRows - 1) / kScanRows);
+  if (m == 0) return KK_OK;
+  KK_CUDA(h, h->d_scan.ensure(sizeof(long long) * (size_t)nblk), "alloc scan");
+  Misc* dm = h->d_misc.as<Misc>();
+  k_scan_partial<<<nblk, kScanBlock, 0, s>>>(m, cnt, h->d_scan.as<long long>());
+  k_scan_top<<<1, 1024, 0, s>>>(nblk, h->d_scan.as<long long>(), grand);
+  k_scan_final<<<nblk, kScanBlock, 0, s>>>(m, cnt, h->d_scan.as<long long>(), h->d_flop.as<long long>(),
+                                           av.rowptr, h->d_span.as<int32_t>(), &dm->sorted,
+                                           h->opt.team_vec_min_len, to_table(h->num_bins), out, nbin);
+  KK_CUDA(h, cudaGetLastError(), "scan launch");
+  return KK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kk_status kk_spgemm_row_features(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B, float* features) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  kk_status st;
+  if ((st = check_csr(h, A, "A", false)) != KK_OK) return st;
+  if ((st = check_csr(h, B, "B", false)) != KK_OK) return st;
+  if (A->n != B->m) return fail(h, KK_ERR_INVALID_ARG, "A.n != B.m");
+  if (A->m > 0 && !features) return fail(h, KK_ERR_INVALID_ARG, "features is NULL");
+  KK_CUDA(h, h->d_mm.ensure(sizeof(int2) * (size_t)(B->m > 0 ? B->m : 1)), "alloc minmax");
+  cudaError_t e = launch_row_features(h->stream, view(A), view(B), h->d_mm.as<int2>(), features,
+                                      h->num_sms);
+  if (e != cudaSuccess) return cuda_fail(h, e, "features launch");
+  return KK_OK;
+}
+
+kk_status kk_spgemm_set_predictor(kk_spgemm_handle h, const float* params_host, float quantile) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  if (!params_host) {
+    h->have_pred = false;
+    return KK_OK;
+  }
+  if (!(quantile <= 1.0f)) return fail(h, KK_ERR_INVALID_ARG, "quantile must be <= 1");
+  KK_CUDA(h, h->d_params.ensure(sizeof(float) * KK_MLP_NUM_PARAMS), "alloc params");
+  KK_CUDA(h, cudaMemcpyAsync(h->d_params.p, params_host, sizeof(float) * KK_MLP_NUM_PARAMS,
+                             cudaMemcpyHostToDevice, h->stream), "copy params");
+  KK_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+  h->have_pred = true;
+  h->quantile = quantile;
+  return KK_OK;
+}
+
+kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B,
+                                     int64_t* c_rowptr, int64_t* nnz_c) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  kk_status st;
+  if ((st = check_csr(h, A, "A", true)) != KK_OK) return st;
+  if ((st = check_csr(h, B, "B", true)) != KK_OK) return st;
+  if (A->n != B->m) return fail(h, KK_ERR_INVALID_ARG, "A.n != B.m");
+  if (!c_rowptr || !nnz_c) return fail(h, KK_ERR_INVALID_ARG, "c_rowptr / nnz_c is NULL");
+  h->have_symbolic = false;
+  h->learned_valid = false;
+  const int32_t m = A->m;
+  const size_t mm1 = (size_t)(m > 0 ? m : 1);
+  const CsrView av = view(A), bv = view(B);
+  cudaStream_t s = h->stream;
+  Misc* dm = h->d_misc.as<Misc>();
+  Misc* hm = static_cast<Misc*>(h->h_pinned);
+  int32_t* h_start = reinterpret_cast<int32_t*>(static_cast<char*>(h->h_pinned) + 256);
+  int32_t* h_start2 = h_start + 2 * (kMaxBins + 1);
+
+  build_bins(h->opt, false, h->sym_bins);
+  build_bins(h->opt, true, h->num_bins);
+  const int nbs = (int)h->sym_bins.size(), nbn = (int)h->num_bins.size();
+  const int nbl = kLearnedHeavy + 1;
+  for (DevBuf* b : {&h->d_sbin, &h->d_nbin, &h->d_lbin, &h->d_plain, &h->d_sball, &h->d_nbin2})
+    KK_CUDA(h, b->ensure(mm1), "alloc bins");
+  for (DevBuf* b : {&h->d_srows, &h->d_nrows, &h->d_cnt, &h->d_rowlo, &h->d_span, &h->d_cap,
+                    &h->d_lrows, &h->d_lrows2})
+    KK_CUDA(h, b->ensure(sizeof(int32_t) * mm1), "alloc rows");
+  KK_CUDA(h, h->d_flop.ensure(sizeof(long long) * mm1), "alloc flop");
+  KK_CUDA(h, h->d_soff.ensure(sizeof(int64_t) * (mm1 + 1)), "alloc staging offsets");
+  KK_CUDA(h, h->d_binstart.ensure(sizeof(int32_t) * 4 * (kMaxBins + 1)), "alloc bins");
+  int32_t* sym_start = h->d_binstart.as<int32_t>();
+  int32_t* num_start = sym_start + (kMaxBins + 1);
+  int32_t* l_start = sym_start + 2 * (kMaxBins + 1);
+  int32_t* ln_start = sym_start + 3 * (kMaxBins + 1);
+
+  Misc init{};
+  init.sorted = 1;
+  KK_CUDA(h, cudaMemcpyAsync(dm, &init, sizeof(Misc), cudaMemcpyHostToDevice, s), "init");
+  LaunchCtx ctx = ctx_of(h);
+  if (m > 0) {
+    if (bv.m > 0)
+      k_analyze_b<<<grid_for((long long)bv.m * kAnaTeam, 256, h->num_sms * 8), 256, 0, s>>>(
+          bv, &dm->sorted, &dm->status);
+    KK_CUDA(h, cudaGetLastError(), "analyze launch");
+    cudaError_t e = launch_learned_analyze(
+        ctx, av, bv, &dm->sorted, h->have_pred ? h->d_params.as<float>() : nullptr, h->quantile,
+        h->have_pred ? 1 : 0, h->d_flop.as<long long>(), h->d_rowlo.as<int32_t>(),
+        h->d_span.as<int32_t>(), h->d_lbin.as<uint8_t>(), h->d_cap.as<int32_t>(), &dm->total_flop);
+    if (e != cudaSuccess) return cuda_fail(h, e, "learned analyze");
+    timer_begin(h->timer, s, "learned_plan");
+    if ((st = run_scan(h, m, h->d_cap.as<int32_t>(), h->d_soff.as<int64_t>(), &dm->grand2, av, nullptr)) != KK_OK)
+      return st;
+    timer_end(h->timer, s);
+    if ((st = run_binning(h, m, h->d_lbin.as<uint8_t>(), nbl, h->d_lrows.as<int32_t>(), l_start)) != KK_OK)
+      return st;
+  } else {
+    KK_CUDA(h, cudaMemsetAsync(l_start, 0, sizeof(int32_t) * (nbl + 1), s), "memset");
+  }
+  KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
+  KK_CUDA(h, cudaMemcpyAsync(h_start, l_start, sizeof(int32_t) * (nbl + 1), cudaMemcpyDeviceToHost, s),
+          "readback");
+  KK_CUDA(h, cudaStreamSynchronize(s), "sync");
+  if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
+  h->b_sorted = hm->sorted;
+  h->stats[6] = (int64_t)hm->total_flop;
+  h->stats[7] = hm->sorted;
+  const long long staging = m > 0 ? hm->grand2 : 0;
+  std::vector<int32_t> lstart(h_start, h_start + nbl + 1);
+  KK_CUDA(h, h->d_scol.ensure(sizeof(int32_t) * (size_t)(staging > 0 ? staging : 1)), "alloc staging");
+  KK_CUDA(h, h->d_sval.ensure(sizeof(double) * (size_t)(staging > 0 ? staging : 1)), "alloc staging");
+  const int32_t arith = h->opt.arith == KK_ARITH_FP64 ? kArithF64 : kArithDF32;
+  h->last_arith = arith;
+  if (arith == kArithDF32 && bv.nnz > 0) {
+    KK_CUDA(h, h->d_bsplit.ensure(sizeof(float2) * (size_t)bv.nnz), "alloc split");
+    KK_CUDA(h, cudaMemsetAsync(&dm->range_bad, 0, sizeof(int32_t), s), "memset");
+    timer_begin(h->timer, s, "split_b");
+    k_split_values<<<grid_for(bv.nnz, 256, h->num_sms * 16), 256, 0, s>>>(
+        bv.nnz, bv.vals, h->d_bsplit.as<float2>(), &dm->range_bad);
+    timer_end(h->timer, s);
+  }
+  int64_t light = 0, heavy = 0;
+  if (m > 0) {
+    KK_CUDA(h, cudaMemsetAsync(h->d_cnt.p, 0, sizeof(int32_t) * (size_t)m, s), "memset counts");
+    for (int c = 0; c < kLearnedHeavy; ++c) {
+      const int n = lstart[c + 1] - lstart[c];
+      if (n <= 0) continue;
+      light += n;
+      const int32_t* lrows = h->d_lrows.as<int32_t>() + lstart[c];
+      cudaError_t e =
+          c < kOnepassClasses
+              ? launch_onepass(ctx, 5 + c, av, bv, h->d_bsplit.as<float2>(), &dm->range_bad, arith,
+                               h->d_soff.as<int64_t>(), lrows, n, h->d_scol.as<int32_t>(),
+                               h->d_sval.as<double>(), h->d_cnt.as<int32_t>())
+              : launch_onepass_window(ctx, c - kOnepassClasses, av, bv, h->d_bsplit.as<float2>(),
+                                      &dm->range_bad, arith, h->d_soff.as<int64_t>(), h->d_cap.as<int32_t>(),
+                                      lrows, n, h->d_scol.as<int32_t>(), h->d_sval.as<double>(),
+                                      h->d_cnt.as<int32_t>());
+      if (e != cudaSuccess) return cuda_fail(h, e, "one-pass launch");
+    }
+    heavy = lstart[kLearnedHeavy + 1] - lstart[kLearnedHeavy];
+    // rows left to the plain two-phase path: heavy rows and overflowed rows
+    k_sym_classify<<<grid_for(m, 256, h->num_sms * 8), 256, 0, s>>>(
+        m, h->d_flop.as<long long>(), av.rowptr, h->d_span.as<int32_t>(), &dm->sorted,
+        to_table(h->sym_bins), h->opt.team_vec_min_len, h->d_sball.as<uint8_t>());
+    cudaError_t e = launch_learned_leftover(ctx, m, h->d_lbin.as<uint8_t>(), h->d_cnt.as<int32_t>(),
+                                            h->d_plain.as<uint8_t>(), h->d_sball.as<uint8_t>(),
+                                            h->d_sbin.as<uint8_t>());
+    if (e != cudaSuccess) return cuda_fail(h, e, "leftover launch");
+    if ((st = run_binning(h, m, h->d_sbin.as<uint8_t>(), nbs, h->d_srows.as<int32_t>(), sym_start)) != KK_OK)
+      return st;
+    KK_CUDA(h, cudaMemcpyAsync(h_start, sym_start, sizeof(int32_t) * (nbs + 1), cudaMemcpyDeviceToHost, s),
+            "readback");
+    KK_CUDA(h, cudaStreamSynchronize(s), "sync");
+    int64_t plain_rows = 0;
+    for (int b = 0; b < nbs; ++b) {
+      const int cnt = h_start[b + 1] - h_start[b];
+      if (cnt <= 0) continue;
+      plain_rows += cnt;
+      const int32_t* rows = h->d_srows.as<int32_t>() + h_start[b];
+      cudaError_t e2 = h->sym_bins[b].tier == kTierWindow
+                           ? launch_symbolic_window(ctx, h->sym_bins[b], av, bv, rows, cnt, h->d_cnt.as<int32_t>())
+                           : launch_symbolic_bin(ctx, h->sym_bins[b], av, bv, h->b_sorted, rows, cnt,
+                                                 h->d_cnt.as<int32_t>());
+      if (e2 != cudaSuccess) return cuda_fail(h, e2, "symbolic launch");
+    }
+    h->stats[12] = light;
+    h->stats[13] = plain_rows - heavy;  // overflowed one-pass rows
+    h->stats[14] = heavy;
+    h->stats[15] = staging;
+    timer_begin(h->timer, s, "scan");
+    if ((st = run_scan(h, m, h->d_cnt.as<int32_t>(), c_rowptr, &dm->grand, av, h->d_nbin.as<uint8_t>())) != KK_OK)
+      return st;
+    timer_end(h->timer, s);
+    if ((st = run_binning(h, m, h->d_nbin.as<uint8_t>(), nbn, h->d_nrows.as<int32_t>(), num_start)) != KK_OK)
+      return st;
+    e = launch_mask_bins(ctx, m, h->d_plain.as<uint8_t>(), h->d_nbin.as<uint8_t>(), h->d_nbin2.as<uint8_t>());
+    if (e != cudaSuccess) return cuda_fail(h, e, "mask launch");
+    if ((st = run_binning(h, m, h->d_nbin2.as<uint8_t>(), nbn, h->d_lrows2.as<int32_t>(), ln_start)) != KK_OK)
+      return st;
+  } else {
+    KK_CUDA(h, cudaMemsetAsync(c_rowptr, 0, sizeof(int64_t), s), "memset rowptr");
+    KK_CUDA(h, cudaMemsetAsync(num_start, 0, sizeof(int32_t) * (nbn + 1), s), "memset");
+    KK_CUDA(h, cudaMemsetAsync(ln_start, 0, sizeof(int32_t) * (nbn + 1), s), "memset");
+  }
+  KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
+  KK_CUDA(h, cudaMemcpyAsync(h_start, num_start, sizeof(int32_t) * (nbn + 1), cudaMemcpyDeviceToHost, s),
+          "readback");
+  KK_CUDA(h, cudaMemcpyAsync(h_start2, ln_start, sizeof(int32_t) * (nbn + 1), cudaMemcpyDeviceToHost, s),
+          "readback");
+  KK_CUDA(h, cudaStreamSynchronize(s), "sync");
+  if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
+  h->nnz_c = m > 0 ? hm->grand : 0;
+  h->num_start.assign(h_start, h_start + nbn + 1);
+  h->lnum_start.assign(h_start2, h_start2 + nbn + 1);
+  h->am = m;
+  h->an = A->n;
+  h->bn = B->n;
+  h->annz = A->nnz;
+  h->bnnz = B->nnz;
+  h->have_symbolic = true;
+  h->learned_valid = true;
+  *nnz_c = h->nnz_c;
+  return KK_OK;
+}
+
+kk_status kk_spgemm_learned_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B,
+                                    const int64_t* c_rowptr, int32_t* c_colind, double* c_vals) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  if (!h->learned_valid) return fail(h, KK_ERR_NOT_SYMBOLIC, "learned numeric before learned symbolic");
+  kk_status st;
+  if ((st = check_csr(h, A, "A", true)) != KK_OK) return st;
+  if ((st = check_csr(h, B, "B", true)) != KK_OK) return st;
+  if (A->m != h->am || A->n != h->an || B->n != h->bn || A->nnz != h->annz || B->nnz != h->bnnz)
+    return fail(h, KK_ERR_STRUCTURE_MISMATCH, "A/B dims or nnz differ from the learned symbolic call");
+  if (!c_rowptr) return fail(h, KK_ERR_INVALID_ARG, "c_rowptr is NULL");
+  if (h->nnz_c > 0 && (!c_colind || !c_vals)) return fail(h, KK_ERR_INVALID_ARG, "C arrays are NULL");
+  if (h->am == 0 || h->nnz_c == 0) return KK_OK;
+  const CsrView av = view(A), bv = view(B);
+  Misc* dm = h->d_misc.as<Misc>();
+  LaunchCtx ctx = ctx_of(h);
+  cudaError_t e = launch_copy_staged(ctx, h->am, h->d_lbin.as<uint8_t>(), h->d_plain.as<uint8_t>(),
+                                     h->d_soff.as<int64_t>(), c_rowptr, h->d_scol.as<int32_t>(),
+                                     h->d_sval.as<double>(), c_colind, c_vals);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy launch");
+  const int32_t arith = h->last_arith;
+  const float2* bsplit = arith == kArithDF32 ? h->d_bsplit.as<float2>() : nullptr;
+  const int nbn = (int)h->num_bins.size();
+  for (int b = 0; b < nbn; ++b) {
+    const int cnt = h->lnum_start[b + 1] - h->lnum_start[b];
+    if (cnt <= 0) continue;
+    const int32_t* rows = h->d_lrows2.as<int32_t>() + h->lnum_start[b];
+    e = h->num_bins[b].tier == kTierWindow
+            ? launch_numeric_window(ctx, h->num_bins[b], av, bv, bsplit, &dm->range_bad, arith, c_rowptr,
+                                    rows, cnt, c_colind, c_vals)
+            : launch_numeric_bin(ctx, h->num_bins[b], av, bv, h->b_sorted, bsplit, &dm->range_bad, arith,
+                                 c_rowptr, rows, cnt, c_colind, c_vals, h->opt.debug_checks);
+    if (e != cudaSuccess) return cuda_fail(h, e, "numeric launch");
+  }
+  return KK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched form (kk_batched.h)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+unsigned long long fnv1a(const void* p, size_t n, unsigned long long h = 1469598103934665603ull) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+  return h;
+}
+
+kk_status ensure_pinned(kk_spgemm_handle h, int32_t count) {
+  if ((size_t)count + 1 <= h->h_bcap) return KK_OK;
+  for (void** p : {&h->h_bdesc, &h->h_bdesc2, &h->h_boff})
+    if (*p) {
+      cudaFreeHost(*p);
+      *p = nullptr;
+    }
+  const size_t cap = (size_t)count + 1 + (size_t)count / 4;
+  KK_CUDA(h, cudaMallocHost(&h->h_bdesc, sizeof(PairDesc) * cap), "pinned descriptors");
+  KK_CUDA(h, cudaMallocHost(&h->h_bdesc2, sizeof(PairDesc) * cap), "pinned descriptors");
+  KK_CUDA(h, cudaMallocHost(&h->h_boff, sizeof(int64_t) * cap), "pinned offsets");
+  h->h_bcap = cap;
+  return KK_OK;
+}
+
+// Runs `enqueue` directly, or through a CUDA graph captured on the first call
+// with `key` and replayed afterwards (non-default streams only).
+template <class F>
+kk_status run_maybe_graph(kk_spgemm_handle h, bool use_graph, cudaGraphExec_t* exec,
+                          unsigned long long* exec_key, unsigned long long key, F enqueue) {
+  if (!use_graph) return enqueue();
+  if (*exec && *exec_key == key) {
+    KK_CUDA(h, cudaGraphLaunch(*exec, h->stream), "graph launch");
+    return KK_OK;
+  }
+  if (*exec) {
+    cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+  }
+  KernelTimer* saved = h->timer;
+  h->timer = nullptr;  // no event records inside a captured graph
+  KK_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed), "begin capture");
+  kk_status st = enqueue();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  h->timer = saved;
+  if (st != KK_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    *exec = nullptr;
+    return cuda_fail(h, e, "graph instantiate");
+  }
+  *exec_key = key;
+  KK_CUDA(h, cudaGraphLaunch(*exec, h->stream), "graph launch");
+  return KK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kk_status kk_spgemm_batched_symbolic(kk_spgemm_handle h, int32_t count, const kk_csr* A,
+                                     const kk_csr* B, int64_t* c_rowptr, int64_t* c_offsets,
+                                     int64_t* total_nnz) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  if (count < 0 || (count > 0 && (!A || !B)) || !total_nnz)
+    return fail(h, KK_ERR_INVALID_ARG, "bad batch arguments");
+  h->b_valid = false;
+  h->have_symbolic = false;
+  h->learned_valid = false;
+  kk_status st;
+  long long R = 0, nnzb = 0;
+  for (int k = 0; k < count; ++k) {
+    if ((st = check_csr(h, &A[k], "A[k]", false)) != KK_OK) return st;
+    if ((st = check_csr(h, &B[k], "B[k]", false)) != KK_OK) return st;
+    if (A[k].n != B[k].m) return fail(h, KK_ERR_INVALID_ARG, "A[k].n != B[k].m at k=" + std::to_string(k));
+    R += A[k].m;
+    nnzb += B[k].nnz;
+  }
+  if (R > 0x7fffffffll) return fail(h, KK_ERR_INVALID_ARG, "batch has more than 2^31-1 rows");
+  if (R > 0 && !c_rowptr) return fail(h, KK_ERR_INVALID_ARG, "c_rowptr is NULL");
+  if ((st = ensure_pinned(h, count)) != KK_OK) return st;
+  PairDesc* hd = static_cast<PairDesc*>(h->h_bdesc);
+  long long rb = 0, sb = 0;
+  for (int k = 0; k < count; ++k) {
+    hd[k] = PairDesc{view(&A[k]), view(&B[k]), rb, sb, 1, 0};
+    rb += A[k].m;
+    sb += B[k].nnz;
+  }
+  batched_bin_tables(h->b_sym, h->b_num);
+  const size_t R1 = (size_t)(R > 0 ? R : 1);
+  const int nblk = (int)((R + kBinRows - 1) / kBinRows);
+  const int nblk_scan = (int)((R + kScanRows - 1) / kScanRows);
+  const int nbmax = h->b_sym.nb > h->b_num.nb ? h->b_sym.nb : h->b_num.nb;
+  KK_CUDA(h, h->d_bdesc.ensure(sizeof(PairDesc) * (size_t)(count > 0 ? count : 1)), "alloc batch");
+  for (DevBuf* b : {&h->d_rowpair, &h->d_bsrows, &h->d_bnrows, &h->d_bcnt})
+    KK_CUDA(h, b->ensure(sizeof(int32_t) * R1), "alloc batch");
+  KK_CUDA(h, h->d_bflop.ensure(sizeof(long long) * R1), "alloc batch");
+  KK_CUDA(h, h->d_bsbin.ensure(R1), "alloc batch");
+  KK_CUDA(h, h->d_bnbin.ensure(R1), "alloc batch");
+  KK_CUDA(h, h->d_btiles.ensure(sizeof(int32_t) * 2 * (kMaxBBins + 1)), "alloc batch");
+  KK_CUDA(h, h->d_bstart.ensure(sizeof(int32_t) * 2 * (kMaxBBins + 1)), "alloc batch");
+  KK_CUDA(h, h->d_bqueue.ensure(sizeof(int) * 2), "alloc batch");
+  KK_CUDA(h, h->d_boff.ensure(sizeof(int64_t) * ((size_t)count + 1)), "alloc batch");
+  KK_CUDA(h, h->d_blk.ensure(sizeof(int32_t) * (size_t)nbmax * (size_t)(nblk > 0 ? nblk : 1)), "alloc bins");
+  KK_CUDA(h, h->d_scan.ensure(sizeof(long long) * (size_t)(nblk_scan > 0 ? nblk_scan : 1)), "alloc scan");
+  if (h->d_span.bytes == 0) KK_CUDA(h, h->d_span.ensure(4), "alloc");
+  if (h->d_flop.bytes == 0) KK_CUDA(h, h->d_flop.ensure(8), "alloc");
+  cudaStream_t s = h->stream;
+  Misc* dm = h->d_misc.as<Misc>();
+  Misc* hm = static_cast<Misc*>(h->h_pinned);
+  int32_t* sym_start = h->d_bstart.as<int32_t>();
+  int32_t* num_start = sym_start + (kMaxBBins + 1);
+  PairDesc* dd = h->d_bdesc.as<PairDesc>();
+  const CsrView none{0, 0, 0, nullptr, nullptr, nullptr};
+  auto enqueue = [&]() -> kk_status {
+    LaunchCtx ctx = ctx_of(h);
+    kk_status st2;
+    if (count > 0)
+      KK_CUDA(h, cudaMemcpyAsync(dd, hd, sizeof(PairDesc) * count, cudaMemcpyHostToDevice, s), "upload");
+    KK_CUDA(h, cudaMemsetAsync(dm, 0, sizeof(Misc), s), "memset");
+    KK_CUDA(h, cudaMemsetAsync(&dm->sorted, 0xFF, sizeof(int32_t), s), "memset");
+    if (R > 0) {
+      KK_CUDA(h, launch_b_prepare(s, h->num_sms, count, dd, R, h->d_rowpair.as<int32_t>(), &dm->status), "prepare");
+      KK_CUDA(h, launch_b_analyze_a(s, h->num_sms, R, dd, h->d_rowpair.as<int32_t>(), h->b_sym,
+                                    h->opt.team_vec_min_len, h->d_bflop.as<long long>(), h->d_bsbin.as<uint8_t>(),
+                                    &dm->total_flop, &dm->status), "analyze");
+      if ((st2 = run_binning(h, (int32_t)R, h->d_bsbin.as<uint8_t>(), h->b_sym.nb, h->d_bsrows.as<int32_t>(),
+                             sym_start)) != KK_OK)
+        return st2;
+      KK_CUDA(h, cudaMemsetAsync(h->d_bcnt.p, 0, sizeof(int32_t) * (size_t)R, s), "memset");
+      KK_CUDA(h, launch_b_symbolic(ctx, dd, h->d_rowpair.as<int32_t>(), h->d_bsrows.as<int32_t>(), sym_start,
+                                   h->d_btiles.as<int32_t>(), h->b_sym, h->d_bqueue.as<int>(),
+                                   h->d_bcnt.as<int32_t>()), "batched symbolic");
+      if ((st2 = run_scan(h, (int32_t)R, h->d_bcnt.as<int32_t>(), c_rowptr, &dm->grand, none, nullptr)) != KK_OK)
+        return st2;
+      KK_CUDA(h, launch_b_nclassify(s, h->num_sms, R, dd, h->d_rowpair.as<int32_t>(), c_rowptr,
+                                    h->d_bflop.as<long long>(), h->b_num, h->opt.team_vec_min_len,
+                                    h->d_bnbin.as<uint8_t>(), &dm->status), "classify");
+      if ((st2 = run_binning(h, (int32_t)R, h->d_bnbin.as<uint8_t>(), h->b_num.nb, h->d_bnrows.as<int32_t>(),
+                             num_start)) != KK_OK)
+        return st2;
+      KK_CUDA(h, launch_b_offsets(s, count, dd, R, c_rowptr, h->d_boff.as<int64_t>()), "offsets");
+    } else {
+      KK_CUDA(h, cudaMemsetAsync(h->d_boff.p, 0, sizeof(int64_t) * ((size_t)count + 1), s), "memset");
+      if (c_rowptr) KK_CUDA(h, cudaMemsetAsync(c_rowptr, 0, sizeof(int64_t), s), "memset");
+    }
+    KK_CUDA(h, cudaMemcpyAsync(h->h_boff, h->d_boff.p, sizeof(int64_t) * ((size_t)count + 1),
+                               cudaMemcpyDeviceToHost, s), "readback");
+    if (count > 0)
+      KK_CUDA(h, cudaMemcpyAsync(h->h_bdesc2, dd, sizeof(PairDesc) * count, cudaMemcpyDeviceToHost, s),
+              "readback");
+    KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
+    return KK_OK;
+  };
+  const bool use_graph = h->opt.batched_graph && s != nullptr && s != cudaStreamLegacy &&
+                         s != cudaStreamPerThread;
+  unsigned long long key = fnv1a(hd, sizeof(PairDesc) * (size_t)count);
+  key = fnv1a(&c_rowptr, sizeof(c_rowptr), key);
+  key = fnv1a(&count, sizeof(count), key);
+  if ((st = run_maybe_graph(h, use_graph, &h->g_sym, &h->g_sym_key, key, enqueue)) != KK_OK) return st;
+  KK_CUDA(h, cudaStreamSynchronize(s), "sync");
+  if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
+  const int64_t* off = static_cast<const int64_t*>(h->h_boff);
+  h->b_total = off[count];
+  if (c_offsets)
+    for (int k = 0; k <= count; ++k) c_offsets[k] = off[k];
+  h->b_count = count;
+  h->b_R = R;
+  h->b_nnzb = nnzb;
+  h->stats[6] = (int64_t)hm->total_flop;
+  h->b_valid = true;
+  *total_nnz = h->b_total;
+  return KK_OK;
+}
+
+kk_status kk_spgemm_batched_numeric(kk_spgemm_handle h, int32_t count, const kk_csr* A,
+                                    const kk_csr* B, const int64_t* c_rowptr, int32_t* c_colind,
+                                    double* c_vals) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  if (!h->b_valid) return fail(h, KK_ERR_NOT_SYMBOLIC, "batched numeric before batched symbolic");
+  if (count != h->b_count || (count > 0 && (!A || !B)))
+    return fail(h, KK_ERR_STRUCTURE_MISMATCH, "batch size differs from the batched symbolic call");
+  if (h->b_total > 0 && (!c_rowptr || !c_colind || !c_vals))
+    return fail(h, KK_ERR_INVALID_ARG, "C arrays are NULL");
+  kk_status st;
+  PairDesc* hd2 = static_cast<PairDesc*>(h->h_bdesc2);
+  bool changed = false;
+  for (int k = 0; k < count; ++k) {
+    if ((st = check_csr(h, &A[k], "A[k]", true)) != KK_OK) return st;
+    if ((st = check_csr(h, &B[k], "B[k]", true)) != KK_OK) return st;
+    const PairDesc& d = hd2[k];
+    if (A[k].m != d.A.m || A[k].n != d.A.n || A[k].nnz != d.A.nnz || B[k].n != d.B.n || B[k].nnz != d.B.nnz)
+      return fail(h, KK_ERR_STRUCTURE_MISMATCH, "pair " + std::to_string(k) + " differs from the symbolic call");
+    const CsrView a = view(&A[k]), b = view(&B[k]);
+    if (a.rowptr != d.A.rowptr || a.colind != d.A.colind || a.vals != d.A.vals || b.rowptr != d.B.rowptr ||
+        b.colind != d.B.colind || b.vals != d.B.vals)
+      changed = true;
+  }
+  if (changed) {
+    KK_CUDA(h, cudaStreamSynchronize(h->stream), "sync");  // pending uploads read the pinned copy
+    for (int k = 0; k < count; ++k) {
+      hd2[k].A = view(&A[k]);
+      hd2[k].B = view(&B[k]);
+    }
+  }
+  if (h->b_R == 0 || h->b_total == 0) return KK_OK;
+  const int32_t arith = h->opt.arith == KK_ARITH_FP64 ? kArithF64 : kArithDF32;
+  h->last_arith = arith;
+  KK_CUDA(h, h->d_bsplit2.ensure(sizeof(float2) * (size_t)(h->b_nnzb > 0 ? h->b_nnzb : 1)), "alloc split");
+  cudaStream_t s = h->stream;
+  PairDesc* dd = h->d_bdesc.as<PairDesc>();
+  int32_t* num_start = h->d_bstart.as<int32_t>() + (kMaxBBins + 1);
+  auto enqueue = [&]() -> kk_status {
+    LaunchCtx ctx = ctx_of(h);
+    KK_CUDA(h, cudaMemcpyAsync(dd, hd2, sizeof(PairDesc) * count, cudaMemcpyHostToDevice, s), "upload");
+    KK_CUDA(h, launch_b_numeric(ctx, count, dd, h->d_rowpair.as<int32_t>(), h->d_bnrows.as<int32_t>(), num_start,
+                                h->d_btiles.as<int32_t>() + (kMaxBBins + 1), h->b_num, h->d_bqueue.as<int>() + 1,
+                                arith, h->d_bsplit2.as<float2>(), c_rowptr, c_colind, c_vals),
+            "batched numeric");
+    return KK_OK;
+  };
+  const bool use_graph = h->opt.batched_graph && s != nullptr && s != cudaStreamLegacy &&
+                         s != cudaStreamPerThread;
+  unsigned long long key = fnv1a(hd2, sizeof(PairDesc) * (size_t)count);
+  const void* ptrs[3] = {c_rowptr, c_colind, c_vals};
+  key = fnv1a(ptrs, sizeof(ptrs), key);
+  key = fnv1a(&arith, sizeof(arith), key);
+  return run_maybe_graph(h, use_graph, &h->g_num, &h->g_num_key, key, enqueue);
+}
+
 kk_status kk_spgemm_sync(kk_spgemm_handle h) {
   if (!h) return KK_ERR_INVALID_ARG;
   Misc* hm = static_cast<Misc*>(h->h_pinned);
@@ -978,6 +1530,16 @@ kk_status kk_spgemm_destroy(kk_spgemm_handle h) {
   h->d_binstart.release();
   h->d_scan.release();
   h->d_bsplit.release();
+  for (DevBuf* b : {&h->d_params, &h->d_lbin, &h->d_plain, &h->d_cap, &h->d_soff, &h->d_scol,
+                    &h->d_sval, &h->d_sball, &h->d_nbin2, &h->d_lrows, &h->d_lrows2, &h->d_mm,
+                    &h->d_bdesc, &h->d_rowpair, &h->d_bflop, &h->d_bsbin, &h->d_bnbin, &h->d_bsrows,
+                    &h->d_bnrows, &h->d_bcnt, &h->d_btiles, &h->d_bstart, &h->d_bqueue, &h->d_bsplit2,
+                    &h->d_boff})
+    b->release();
+  for (void* p : {h->h_bdesc, h->h_bdesc2, h->h_boff})
+    if (p) cudaFreeHost(p);
+  if (h->g_sym) cudaGraphExecDestroy(h->g_sym);
+  if (h->g_num) cudaGraphExecDestroy(h->g_num);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   delete h;
   return KK_OK;

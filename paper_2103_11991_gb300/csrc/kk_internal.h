@@ -36,6 +36,9 @@ enum Tier : int32_t { kTierTeam = 0, kTierCta = 1, kTierDense = 2, kTierWindow =
 // dense bit vector of W bits (plus per-word ranks in the numeric phase).
 constexpr int kNumWindowClasses = 4;
 constexpr int32_t kWindowBits[kNumWindowClasses] = {4096, 16384, 49152, 65536};
+__host__ __device__ constexpr int32_t window_bits(int w) {
+  return w == 0 ? 4096 : w == 1 ? 16384 : w == 2 ? 49152 : 65536;
+}
 constexpr int32_t kWindowMaxNnz = 256;   // numeric window rows: nnz(C(i,:)) <= this
 constexpr int32_t kWindowFlopRatio = 128;  // window used only when W <= ratio * flop
 
@@ -73,6 +76,79 @@ cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, cons
                                   const int32_t* b_range_bad, int32_t arith,
                                   const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
                                   int32_t* c_colind, double* c_vals);
+
+// Speculative one-pass (learned form) over rows whose predicted table is
+// 2^log2s slots (log2s in 5..9); see k_num_warp_vec<LOG2S, true>.
+cudaError_t launch_onepass(const LaunchCtx& ctx, int32_t log2s, const CsrView& A, const CsrView& B,
+                           const float2* b_split, const int32_t* b_range_bad, int32_t arith,
+                           const int64_t* soff, const int32_t* rows, int32_t nrows, int32_t* scol,
+                           double* sval, int32_t* cnt_out);
+
+// Learned form (kk_learned.cu).  Rows predicted to need at most
+// 16 << (kOnepassClasses - 1) entries take the speculative one-pass.
+constexpr int kOnepassClasses = 5;
+// Learned bins: [0, kOnepassClasses) hash one-pass by capacity class,
+// [kOnepassClasses, kLearnedHeavy) window one-pass by window class,
+// kLearnedHeavy = plain path.
+constexpr int kLearnedHeavy = kOnepassClasses + kNumWindowClasses;
+cudaError_t launch_onepass_window(const LaunchCtx& ctx, int32_t wclass, const CsrView& A,
+                                  const CsrView& B, const float2* b_split,
+                                  const int32_t* b_range_bad, int32_t arith, const int64_t* soff,
+                                  const int32_t* cap, const int32_t* rows, int32_t nrows,
+                                  int32_t* scol, double* sval, int32_t* cnt_out);
+cudaError_t launch_learned_analyze(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                                   const int32_t* b_sorted, const float* params, float quantile,
+                                   int32_t use_pred, long long* flop, int32_t* row_lo,
+                                   int32_t* row_span, uint8_t* lbin, int32_t* cap,
+                                   unsigned long long* total_flop);
+cudaError_t launch_learned_leftover(const LaunchCtx& ctx, int32_t m, const uint8_t* lbin,
+                                    const int32_t* cnt, uint8_t* plain, const uint8_t* sbin_all,
+                                    uint8_t* sbin);
+cudaError_t launch_mask_bins(const LaunchCtx& ctx, int32_t m, const uint8_t* plain,
+                             const uint8_t* nbin, uint8_t* out);
+cudaError_t launch_copy_staged(const LaunchCtx& ctx, int32_t m, const uint8_t* lbin,
+                               const uint8_t* plain, const int64_t* soff, const int64_t* rowptr,
+                               const int32_t* scol, const double* sval, int32_t* ccol,
+                               double* cval);
+
+// Batched form (kk_batched.cu).
+struct PairDesc {
+  CsrView A, B;
+  long long row_base;    // first global row of this pair
+  long long split_base;  // first DF32 pair of B's values in the split buffer
+  int32_t b_sorted;      // set on the device
+  int32_t range_bad;     // set on the device (values outside the DF32 window)
+};
+constexpr int kMaxBBins = 24;
+struct BBinTable {
+  int32_t nb;
+  int32_t kind[kMaxBBins];   // 0 warp, 1 CTA
+  int32_t log2s[kMaxBBins];
+  int32_t flat[kMaxBBins];
+  long long hi[kMaxBBins];
+};
+void batched_bin_tables(BBinTable& sym, BBinTable& num);
+cudaError_t launch_b_prepare(cudaStream_t s, int num_sms, int32_t count, PairDesc* d, long long R,
+                             int32_t* row_pair, int* status);
+cudaError_t launch_b_analyze_a(cudaStream_t s, int num_sms, long long R, const PairDesc* d,
+                               const int32_t* row_pair, const BBinTable& tab, int32_t vec_min_len,
+                               long long* flop, uint8_t* bin, unsigned long long* total_flop, int* status);
+cudaError_t launch_b_nclassify(cudaStream_t s, int num_sms, long long R, const PairDesc* d,
+                               const int32_t* row_pair, const int64_t* rowptr, const long long* flop,
+                               const BBinTable& tab, int32_t vec_min_len, uint8_t* bin, int* status);
+cudaError_t launch_b_symbolic(const LaunchCtx& ctx, const PairDesc* d, const int32_t* row_pair,
+                              const int32_t* rows, const int32_t* bin_start, int32_t* tile_prefix,
+                              const BBinTable& tab, int* queue, int32_t* cnt);
+cudaError_t launch_b_numeric(const LaunchCtx& ctx, int32_t count, PairDesc* d, const int32_t* row_pair,
+                             const int32_t* rows, const int32_t* bin_start, int32_t* tile_prefix,
+                             const BBinTable& tab, int* queue, int32_t arith, float2* split,
+                             const int64_t* rowptr, int32_t* ccol, double* cval);
+cudaError_t launch_b_offsets(cudaStream_t s, int32_t count, const PairDesc* d, long long R,
+                             const int64_t* rowptr, int64_t* off);
+
+// Row features (kk_mlp.cu); mm is scratch int2[B.m].
+cudaError_t launch_row_features(cudaStream_t s, const CsrView& A, const CsrView& B, int2* mm,
+                                float* feat, int num_sms);
 
 // Shared-memory bytes a bin's kernel needs per CTA (0 if it does not fit).
 size_t symbolic_smem_bytes(const BinSpec& bin);

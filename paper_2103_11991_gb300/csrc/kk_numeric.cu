@@ -18,6 +18,7 @@
 // otherwise.  In vector mode with distinct columns per B row the updates of one
 // output entry happen in A-row storage order without atomics.
 #include "kk_internal.h"
+#include "kk_rowops.cuh"
 #include "kk_visit.cuh"
 
 namespace kk {
@@ -27,7 +28,7 @@ constexpr int kTeamBlock = 256;
 constexpr int kCtaBlock = 512;
 constexpr int kDenseBlock = 512;
 
-using u64 = unsigned long long;
+
 
 struct NumArgs {
   CsrView A, B;
@@ -43,147 +44,12 @@ struct NumArgs {
   int* status;
   int32_t k;
   int32_t W;  // dense chunk width
+  // speculative one-pass (learned form): staging offsets / arrays, row counts
+  const int64_t* soff;
+  int32_t* scol;
+  double* sval;
+  int32_t* cnt_out;
 };
-
-struct FullRange {
-  const int32_t* acol;
-  const int32_t* brp;
-  __device__ __forceinline__ void operator()(int p, int& bs, int& bl) const {
-    const int j = acol[p];
-    bs = brp[j];
-    bl = brp[j + 1] - bs;
-  }
-};
-
-struct PrepF64 {
-  const double* av;
-  __device__ __forceinline__ double operator()(int p) const { return av[p]; }
-};
-struct PrepDF {
-  const double* av;
-  __device__ __forceinline__ DF operator()(int p) const {
-    DF t;
-    df_split(av[p], t);
-    return t;
-  }
-};
-
-__device__ __forceinline__ DF load_b(const float2* bs, int q) {
-  const float2 v = bs[q];
-  DF d;
-  d.hi = v.x;
-  d.lo = v.y;
-  return d;
-}
-
-// Accumulate one product into slot `slot` of a u64 value array.
-__device__ __forceinline__ void upd_df(u64* vals, int slot, DF a, DF b, bool atomic, int* status) {
-  if (atomic) {
-    df_atomic_fma(&vals[slot], a, b, status);
-  } else {
-    DF s = df_unpack(vals[slot]);
-    df_fma(s, a, b);
-    vals[slot] = df_pack(s);
-  }
-}
-__device__ __forceinline__ void upd_f64(u64* vals, int slot, double a, double b, bool atomic) {
-  double* v = reinterpret_cast<double*>(&vals[slot]);
-  if (atomic) atomicAdd(v, a * b);
-  else *v = fma(a, b, *v);
-}
-
-// True if every A value of the row lies in the DF32 window (team vote).
-template <int TEAM>
-__device__ __forceinline__ bool row_df_ok(const double* av, int pa, int pe, int tl, unsigned mask) {
-  int bad = 0;
-  for (int p = pa + tl; p < pe; p += TEAM) {
-    DF t;
-    bad |= df_split(av[p], t) ? 0 : 1;
-  }
-  return __any_sync(mask, bad) == 0;
-}
-
-__device__ __forceinline__ bool block_df_ok(const double* av, int pa, int pe, int* flag) {
-  if (threadIdx.x == 0) *flag = 0;
-  __syncthreads();
-  for (int p = pa + threadIdx.x; p < pe; p += blockDim.x) {
-    DF t;
-    if (!df_split(av[p], t)) *flag = 1;
-  }
-  __syncthreads();
-  const bool ok = *flag == 0;
-  __syncthreads();
-  return ok;
-}
-
-__device__ __forceinline__ double out_value(u64 v, bool df) {
-  return df ? df_to_double(df_unpack(v)) : __longlong_as_double((long long)v);
-}
-
-// Bitonic sort of P (a power of two) u64 items in shared memory by a team.
-template <int TEAM>
-__device__ __forceinline__ void team_bitonic(u64* buf, int P, int tl, unsigned mask) {
-  for (int kk = 2; kk <= P; kk <<= 1) {
-    for (int j = kk >> 1; j > 0; j >>= 1) {
-      for (int t = tl; t < (P >> 1); t += TEAM) {
-        const int lo = ((t & ~(j - 1)) << 1) | (t & (j - 1));
-        const int hi = lo + j;
-        const bool up = (lo & kk) == 0;
-        const u64 x = buf[lo], y = buf[hi];
-        if ((x > y) == up) {
-          buf[lo] = y;
-          buf[hi] = x;
-        }
-      }
-      __syncwarp(mask);
-    }
-  }
-}
-
-__device__ __forceinline__ void block_bitonic(u64* buf, int P) {
-  for (int kk = 2; kk <= P; kk <<= 1) {
-    for (int j = kk >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
-        const int lo = ((t & ~(j - 1)) << 1) | (t & (j - 1));
-        const int hi = lo + j;
-        const bool up = (lo & kk) == 0;
-        const u64 x = buf[lo], y = buf[hi];
-        if ((x > y) == up) {
-          buf[lo] = y;
-          buf[hi] = x;
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// Exclusive scan of v over the block (blockDim.x a multiple of 32, <= 1024);
-// returns this thread's prefix and the block total in *total.
-__device__ __forceinline__ int block_exclusive_scan(int v, int* scratch, int* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  int incl = team_inclusive_scan<32>(v, lane, 0xffffffffu);
-  if (lane == 31) scratch[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    int w = lane < nw ? scratch[lane] : 0;
-    int wi = team_inclusive_scan<32>(w, lane, 0xffffffffu);
-    if (lane < nw) scratch[lane] = wi - w;
-    if (lane == 31) scratch[32] = wi;
-  }
-  __syncthreads();
-  const int r = scratch[warp] + incl - v;
-  *total = scratch[32];
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ int pow2ceil(int n) {
-  int p = 1;
-  while (p < n) p <<= 1;
-  return p;
-}
 
 // ---------------------------------------------------------------------------
 // Team tier
@@ -334,12 +200,14 @@ __device__ __forceinline__ int probe_insert(int* keys, int32_t key, int log2s, b
 // One product into the warp's map: find-or-insert col; the inserting lane
 // stores the first product, later ones accumulate.  a / b carry DF32 pairs
 // (df) or the two 32-bit halves of a float64.
+// Returns 1 if this product inserted its column, 0 if the column was present,
+// -1 if the table was full (the product is then dropped).
 template <int LOG2S>
-__device__ __forceinline__ void warp_vec_update(int* keys, u64* vals, int col, int2 a, float2 b,
-                                                bool df, int* status) {
+__device__ __forceinline__ int warp_vec_update(int* keys, u64* vals, int col, int2 a, float2 b,
+                                               bool df, int* status) {
   bool ins;
   const int slot = probe_insert(keys, col, LOG2S, &ins, status);
-  if (slot < 0) return;
+  if (slot < 0) return -1;
   if (df) {
     DF ad, bd, s;
     ad.hi = __int_as_float(a.x);
@@ -361,6 +229,7 @@ __device__ __forceinline__ void warp_vec_update(int* keys, u64* vals, int col, i
     double* v = reinterpret_cast<double*>(&vals[slot]);
     *v = ins ? av * bvv : fma(av, bvv, *v);
   }
+  return ins ? 1 : 0;
 }
 
 // Bitonic sort of 32*E int keys held in registers, element e = r*32 + lane.
@@ -401,7 +270,13 @@ __device__ __forceinline__ void warp_bitonic_regs(int (&v)[E], int lane) {
   }
 }
 
-template <int LOG2S>
+// SPEC = true: speculative one-pass of the learned form.  The row's count is
+// not known; the table holds S slots and the staging area S/2 entries at
+// g.soff[i].  A row whose distinct columns exceed S/2 (or fill the table)
+// overflows: it is abandoned and marked with g.cnt_out[i] = -1 for the plain
+// two-phase re-run.  Otherwise its sorted columns and values go to the staging
+// area and g.cnt_out[i] receives its count.
+template <int LOG2S, bool SPEC>
 __global__ void __launch_bounds__(256, 3) k_num_warp_vec(NumArgs g) {
   using G = WarpVecGeom<LOG2S>;
   constexpr int S = G::S;
@@ -422,14 +297,19 @@ __global__ void __launch_bounds__(256, 3) k_num_warp_vec(NumArgs g) {
   const double* __restrict__ bval = g.B.vals;
   const float2* __restrict__ bspl = g.b_split;
   int* status = g.status;
+  int* pstatus = SPEC ? nullptr : status;  // a full table is an overflow, not an error
+  int32_t* out_col = SPEC ? g.scol : g.c_colind;
+  double* out_val = SPEC ? g.sval : g.c_vals;
   // contiguous share of rows per CTA (neighbouring rows reuse B rows in L1)
   const int per_cta = (g.nrows + gridDim.x - 1) / gridDim.x;
   const int r_begin = blockIdx.x * per_cta;
   const int r_end = min(g.nrows, r_begin + per_cta);
   for (int r = r_begin + warp; r < r_end; r += G::WPB) {
     const int i = g.rows[r];
-    const int64_t off = g.c_rowptr[i];
-    const int cnt = (int)(g.c_rowptr[i + 1] - off);
+    const int64_t off = SPEC ? g.soff[i] : g.c_rowptr[i];
+    const int cnt = SPEC ? S / 2 : (int)(g.c_rowptr[i + 1] - off);
+    int n_ins = 0;
+    bool ovf = false;
 #pragma unroll
     for (int s = lane * 4; s < S; s += 128) *reinterpret_cast<int4*>(&keys[s]) = make_int4(-1, -1, -1, -1);
     __syncwarp();
@@ -444,7 +324,7 @@ __global__ void __launch_bounds__(256, 3) k_num_warp_vec(NumArgs g) {
       }
       df = __any_sync(0xffffffffu, bad) == 0;
     }
-    for (int p0 = pa; p0 < pe; p0 += 32) {
+    for (int p0 = pa; p0 < pe && !ovf; p0 += 32) {
       const int p = p0 + lane;
       int4 info = make_int4(0, 0, 0, 0);
       double a64 = 0.0;
@@ -476,7 +356,7 @@ __global__ void __launch_bounds__(256, 3) k_num_warp_vec(NumArgs g) {
         // every referenced B row fits one pass of the warp: issue the loads of
         // kBatch A entries before their updates (memory-level parallelism)
         constexpr int kBatch = 8;
-        for (int t0 = 0; t0 < nch; t0 += kBatch) {
+        for (int t0 = 0; t0 < nch && !ovf; t0 += kBatch) {
           int cols[kBatch];
           float2 bv[kBatch];
 #pragma unroll
@@ -501,19 +381,25 @@ __global__ void __launch_bounds__(256, 3) k_num_warp_vec(NumArgs g) {
 #pragma unroll
           for (int u = 0; u < kBatch; ++u) {
             if (t0 + u < nch) {
+              int res = 0;
               if (cols[u] >= 0) {
                 const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
-                warp_vec_update<LOG2S>(keys, vals, cols[u], az, bv[u], df, status);
+                res = warp_vec_update<LOG2S>(keys, vals, cols[u], az, bv[u], df, pstatus);
+              }
+              if (SPEC) {
+                n_ins += __popc(__ballot_sync(0xffffffffu, res == 1));
+                if (__any_sync(0xffffffffu, res < 0) || n_ins > S / 2) ovf = true;
               }
               __syncwarp();  // this A entry's updates are visible before the next one's
             }
           }
         }
       } else {
-        for (int t = 0; t < nch; ++t) {
+        for (int t = 0; t < nch && !ovf; ++t) {
           const int4 in = ainfo[t];
-          for (int q0 = 0; q0 < in.y; q0 += 32) {
+          for (int q0 = 0; q0 < in.y && !ovf; q0 += 32) {
             const int q = in.x + q0 + lane;
+            int res = 0;
             if (q0 + lane < in.y) {
               float2 b2;
               if (df) {
@@ -522,13 +408,22 @@ __global__ void __launch_bounds__(256, 3) k_num_warp_vec(NumArgs g) {
                 const long long bb = __double_as_longlong(bval[q]);
                 b2 = make_float2(__int_as_float((int)(bb & 0xffffffffll)), __int_as_float((int)(bb >> 32)));
               }
-              warp_vec_update<LOG2S>(keys, vals, bcol[q], make_int2(in.z, in.w), b2, df, status);
+              res = warp_vec_update<LOG2S>(keys, vals, bcol[q], make_int2(in.z, in.w), b2, df, pstatus);
+            }
+            if (SPEC) {
+              n_ins += __popc(__ballot_sync(0xffffffffu, res == 1));
+              if (__any_sync(0xffffffffu, res < 0) || n_ins > S / 2) ovf = true;
             }
           }
           __syncwarp();  // this A entry's updates are visible before the next one's
         }
       }
       __syncwarp();
+    }
+    if (SPEC && ovf) {
+      if (lane == 0) g.cnt_out[i] = -1;
+      __syncwarp();
+      continue;
     }
     // compaction of occupied keys
     int n = 0;
@@ -541,7 +436,8 @@ __global__ void __launch_bounds__(256, 3) k_num_warp_vec(NumArgs g) {
       if (occ && pos < P) kst[pos] = key;
       n += __popc(bal);
     }
-    if (n != cnt && lane == 0) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    if (!SPEC && n != cnt && lane == 0) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    if (SPEC && lane == 0) g.cnt_out[i] = n;
     const int nn = max(0, min(min(n, cnt), P));
     __syncwarp();
     int v[E];
@@ -556,8 +452,8 @@ __global__ void __launch_bounds__(256, 3) k_num_warp_vec(NumArgs g) {
       const int e = r * 32 + lane;
       if (e < nn) {
         const int slot = probe_find(keys, v[r], LOG2S);
-        g.c_colind[off + e] = v[r];
-        g.c_vals[off + e] = slot >= 0 ? out_value(vals[slot], df) : 0.0;
+        out_col[off + e] = v[r];
+        out_val[off + e] = slot >= 0 ? out_value(vals[slot], df) : 0.0;
       }
     }
     __syncwarp();
@@ -756,11 +652,11 @@ cudaError_t dispatch_team(const LaunchCtx& ctx, int log2s, const NumArgs& g) {
   }
 }
 
-template <int LOG2S>
+template <int LOG2S, bool SPEC = false>
 cudaError_t launch_warp_vec(const LaunchCtx& ctx, const NumArgs& g) {
   using G = WarpVecGeom<LOG2S>;
   const size_t smem = (size_t)G::WPB * G::kWarpBytes;
-  auto kern = k_num_warp_vec<LOG2S>;
+  auto kern = k_num_warp_vec<LOG2S, SPEC>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   long long blocks = (g.nrows + G::WPB * 4 - 1) / (G::WPB * 4);
@@ -801,7 +697,7 @@ cudaError_t launch_numeric_bin(const LaunchCtx& ctx, const BinSpec& bin, const C
                                int32_t* c_colind, double* c_vals, int32_t) {
   if (nrows <= 0) return cudaSuccess;
   NumArgs g{A, B, b_sorted, b_split, b_range_bad, arith, c_rowptr, rows, nrows,
-            c_colind, c_vals, ctx.status, B.n, bin.slots};
+            c_colind, c_vals, ctx.status, B.n, bin.slots, nullptr, nullptr, nullptr, nullptr};
   int log2s = 0;
   while ((1 << log2s) < bin.slots) ++log2s;
   cudaError_t e = cudaErrorInvalidValue;
@@ -846,6 +742,26 @@ cudaError_t launch_numeric_bin(const LaunchCtx& ctx, const BinSpec& bin, const C
     long long blocks = nrows < ctx.num_sms ? nrows : ctx.num_sms;
     k_num_dense<<<(unsigned)blocks, kDenseBlock, smem, ctx.stream>>>(g);
     e = cudaGetLastError();
+  }
+  timer_end(ctx.timer, ctx.stream);
+  return e;
+}
+
+cudaError_t launch_onepass(const LaunchCtx& ctx, int32_t log2s, const CsrView& A, const CsrView& B,
+                           const float2* b_split, const int32_t* b_range_bad, int32_t arith,
+                           const int64_t* soff, const int32_t* rows, int32_t nrows, int32_t* scol,
+                           double* sval, int32_t* cnt_out) {
+  if (nrows <= 0) return cudaSuccess;
+  NumArgs g{A, B, 1, b_split, b_range_bad, arith, nullptr, rows, nrows, nullptr, nullptr,
+            ctx.status, B.n, 0, soff, scol, sval, cnt_out};
+  timer_begin(ctx.timer, ctx.stream, "onepass_warp");
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (log2s) {
+    case 5: e = launch_warp_vec<5, true>(ctx, g); break;
+    case 6: e = launch_warp_vec<6, true>(ctx, g); break;
+    case 7: e = launch_warp_vec<7, true>(ctx, g); break;
+    case 8: e = launch_warp_vec<8, true>(ctx, g); break;
+    case 9: e = launch_warp_vec<9, true>(ctx, g); break;
   }
   timer_end(ctx.timer, ctx.stream);
   return e;

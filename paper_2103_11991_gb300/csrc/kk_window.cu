@@ -217,12 +217,17 @@ k_sym_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo,
   }
 }
 
-template <int W>
+// SPEC = true: speculative one-pass of the learned form.  c_rowptr then holds
+// staging offsets, c_colind / c_vals the staging arrays, cap[i] the row's
+// predicted capacity; a row with more columns than its capacity overflows
+// (cnt_out[i] = -1, re-run by the plain path), otherwise cnt_out[i] = nnz.
+template <int W, bool SPEC>
 __global__ void __launch_bounds__(kWinWarps * 32, 4)
 k_num_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo, const float2* __restrict__ bspl,
              const int32_t* __restrict__ b_range_bad, int32_t arith,
              const int64_t* __restrict__ c_rowptr, const int32_t* __restrict__ rows, int32_t nrows,
-             int32_t* __restrict__ c_colind, double* __restrict__ c_vals, int* status) {
+             int32_t* __restrict__ c_colind, double* __restrict__ c_vals, int* status,
+             const int32_t* __restrict__ cap, int32_t* __restrict__ cnt_out) {
   using G = NumWinGeom<W>;
   constexpr int WORDS = G::WORDS;
   constexpr int SUMS = G::SUMS;
@@ -253,7 +258,7 @@ k_num_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo, const flo
     const int i = rows[r];
     const int lo = row_lo[i];
     const int64_t off = c_rowptr[i];
-    const int cnt = (int)(c_rowptr[i + 1] - off);
+    const int cnt = SPEC ? min(cap[i], kWindowMaxNnz) : (int)(c_rowptr[i + 1] - off);
     const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
     for (int e = lane; e < kWindowMaxNnz; e += 32) vacc[e] = 0ull;
     // Compact rows (at most 32 A entries, every B row at most 32 long): each
@@ -354,7 +359,21 @@ k_num_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo, const flo
         }
       }
     }
-    if (run != cnt && lane == 0) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    if (!SPEC && run != cnt && lane == 0) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    if (SPEC) {
+      if (run > cnt) {  // overflow: abandon the row, clear what it set
+        if (lane == 0) cnt_out[i] = -1;
+        if (carry > kWindowMaxNnz) {
+          for (int w = lane * 4; w < WORDS; w += 128)
+            *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+          for (int e = lane; e < L; e += 32) bits[list[e]] = 0u;
+        }
+        __syncwarp();
+        continue;
+      }
+      if (lane == 0) cnt_out[i] = run;
+    }
     __syncwarp();
     // arithmetic of this row: DF32 unless a value of the row is outside its window
     bool df = df_all;
@@ -495,7 +514,7 @@ k_num_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo, const flo
       }
       __syncwarp();
     }
-    const int n = min(cnt, kWindowMaxNnz);
+    const int n = min(SPEC ? run : cnt, kWindowMaxNnz);
     for (int e = lane; e < n; e += 32) {
       const u64 v = vacc[e];
       c_vals[off + e] = df ? df_to_double(df_unpack(v)) : __longlong_as_double((long long)v);
@@ -531,18 +550,19 @@ cudaError_t sym_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
   return cudaGetLastError();
 }
 
-template <int W>
+template <int W, bool SPEC = false>
 cudaError_t num_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
                        const float2* b_split, const int32_t* b_range_bad, int32_t arith,
                        const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
-                       int32_t* c_colind, double* c_vals) {
+                       int32_t* c_colind, double* c_vals, const int32_t* cap = nullptr,
+                       int32_t* cnt_out = nullptr) {
   const size_t smem = (size_t)kWinWarps * NumWinGeom<W>::kWarpBytes;
-  auto kern = k_num_window<W>;
+  auto kern = k_num_window<W, SPEC>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid_for_rows(ctx, nrows), kWinWarps * 32, smem, ctx.stream>>>(
       A, B, ctx.row_lo, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals,
-      ctx.status);
+      ctx.status, cap, cnt_out);
   return cudaGetLastError();
 }
 
@@ -577,6 +597,28 @@ cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, cons
     case 16384: e = num_window<16384>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
     case 49152: e = num_window<49152>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
     case 65536: e = num_window<65536>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
+  }
+  timer_end(ctx.timer, ctx.stream);
+  return e;
+}
+
+}  // namespace kk
+
+namespace kk {
+
+cudaError_t launch_onepass_window(const LaunchCtx& ctx, int32_t wclass, const CsrView& A,
+                                  const CsrView& B, const float2* b_split,
+                                  const int32_t* b_range_bad, int32_t arith, const int64_t* soff,
+                                  const int32_t* cap, const int32_t* rows, int32_t nrows,
+                                  int32_t* scol, double* sval, int32_t* cnt_out) {
+  if (nrows <= 0) return cudaSuccess;
+  timer_begin(ctx.timer, ctx.stream, "onepass_window");
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (kWindowBits[wclass]) {
+    case 4096: e = num_window<4096, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
+    case 16384: e = num_window<16384, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
+    case 49152: e = num_window<49152, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
+    case 65536: e = num_window<65536, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
   }
   timer_end(ctx.timer, ctx.stream);
   return e;

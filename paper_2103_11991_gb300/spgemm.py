@@ -49,7 +49,7 @@ class KkOptions(ctypes.Structure):
                 ("team_vec_min_len", ctypes.c_int32), ("sym_team_max_flop", ctypes.c_int32),
                 ("sym_cta_max_flop", ctypes.c_int32), ("num_team_max_nnz", ctypes.c_int32),
                 ("num_cta_max_nnz", ctypes.c_int32), ("use_window", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("batched_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -71,7 +71,23 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I32), _I32]),
     "kk_spgemm_stats": (_I32, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    # learned form (include/kk_learned.h)
+    "kk_spgemm_row_features": (_I32, [_P, ctypes.POINTER(KkCsr), ctypes.POINTER(KkCsr), _P]),
+    "kk_capacity_classes": (_I32, [_P, _I32, _P, _P]),
+    "kk_mlp_init": (_I32, [_P, _P, ctypes.c_uint64]),
+    "kk_mlp_loss_grad": (_I32, [_P, _I32, _P, _P, _P, _P, _P]),
+    "kk_mlp_adam": (_I32, [_P, _P, _P, _P, _P, _I32, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_float, ctypes.c_float]),
+    "kk_mlp_train": (_I32, [_P, _I32, _P, _P, _P, _I32, _I32, ctypes.c_float, ctypes.c_uint64,
+                            ctypes.POINTER(ctypes.c_float)]),
+    "kk_mlp_predict": (_I32, [_P, _I32, _P, _P, ctypes.c_float, _P]),
+    "kk_spgemm_set_predictor": (_I32, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_float]),
+    "kk_spgemm_learned_symbolic": (_I32, [_P, ctypes.POINTER(KkCsr), ctypes.POINTER(KkCsr), _P,
+                                          ctypes.POINTER(ctypes.c_int64)]),
+    "kk_spgemm_learned_numeric": (_I32, [_P, ctypes.POINTER(KkCsr), ctypes.POINTER(KkCsr), _P, _P,
+                                         _P]),
 }
+MLP_FEATURES, MLP_CLASSES, MLP_NUM_PARAMS = 8, 16, 1872
 
 
 def library_path() -> str:
@@ -186,8 +202,90 @@ def kk_spgemm_stats(h) -> dict:
     _check(load_library().kk_spgemm_stats(h, arr), h)
     keys = ["sym_team_rows", "sym_cta_rows", "sym_dense_rows", "num_team_rows", "num_cta_rows",
             "num_dense_rows", "flops", "b_sorted", "launches_sym", "launches_num",
-            "sym_window_rows", "num_window_rows"]
+            "sym_window_rows", "num_window_rows", "onepass_rows", "overflow_rows", "heavy_rows",
+            "staging_entries"]
     return {k: int(arr[i]) for i, k in enumerate(keys)}
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def kk_spgemm_row_features(h, A: "DeviceCSR", B: "DeviceCSR", features):
+    a, b = A.abi(), B.abi()
+    _check(load_library().kk_spgemm_row_features(h, ctypes.byref(a), ctypes.byref(b),
+                                                 ctypes.c_void_p(features.data_ptr())), h)
+
+
+def kk_capacity_classes(m: int, c_rowptr, cls, stream=None):
+    _check(load_library().kk_capacity_classes(_stream_ptr(stream), int(m),
+                                              ctypes.c_void_p(c_rowptr.data_ptr()),
+                                              ctypes.c_void_p(cls.data_ptr())))
+
+
+def kk_mlp_init(params, seed: int, stream=None):
+    _check(load_library().kk_mlp_init(_stream_ptr(stream), ctypes.c_void_p(params.data_ptr()),
+                                      ctypes.c_uint64(seed)))
+
+
+def kk_mlp_loss_grad(X, y, params, grad, loss, stream=None):
+    _check(load_library().kk_mlp_loss_grad(_stream_ptr(stream), int(X.shape[0]),
+                                           ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                           ctypes.c_void_p(params.data_ptr()),
+                                           ctypes.c_void_p(grad.data_ptr()),
+                                           ctypes.c_void_p(loss.data_ptr())))
+
+
+def kk_mlp_adam(grad, params, m1, m2, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load_library().kk_mlp_adam(_stream_ptr(stream), ctypes.c_void_p(grad.data_ptr()),
+                                      ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(m1.data_ptr()),
+                                      ctypes.c_void_p(m2.data_ptr()), int(step), lr, beta1, beta2, eps))
+
+
+def kk_mlp_train(X, y, params, epochs=20, batch=4096, lr=3e-3, seed=0, stream=None) -> float:
+    out = ctypes.c_float(0.0)
+    _check(load_library().kk_mlp_train(_stream_ptr(stream), int(X.shape[0]), ctypes.c_void_p(X.data_ptr()),
+                                       ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(params.data_ptr()),
+                                       int(epochs), int(batch), float(lr), ctypes.c_uint64(seed),
+                                       ctypes.byref(out)))
+    return float(out.value)
+
+
+def kk_mlp_predict(X, params, cls, quantile=0.0, stream=None):
+    _check(load_library().kk_mlp_predict(_stream_ptr(stream), int(X.shape[0]), ctypes.c_void_p(X.data_ptr()),
+                                         ctypes.c_void_p(params.data_ptr()), float(quantile),
+                                         ctypes.c_void_p(cls.data_ptr())))
+
+
+def kk_spgemm_set_predictor(h, params_host, quantile: float = 0.95):
+    if params_host is None:
+        _check(load_library().kk_spgemm_set_predictor(h, None, float(quantile)), h)
+        return
+    arr = np.ascontiguousarray(params_host, dtype=np.float32)
+    if arr.size != MLP_NUM_PARAMS:
+        raise ValueError("predictor needs %d parameters" % MLP_NUM_PARAMS)
+    _check(load_library().kk_spgemm_set_predictor(h, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                  float(quantile)), h)
+
+
+def kk_spgemm_learned_symbolic(h, A: "DeviceCSR", B: "DeviceCSR", c_rowptr) -> int:
+    nnz = ctypes.c_int64(0)
+    a, b = A.abi(), B.abi()
+    _check(load_library().kk_spgemm_learned_symbolic(h, ctypes.byref(a), ctypes.byref(b),
+                                                     ctypes.c_void_p(c_rowptr.data_ptr()),
+                                                     ctypes.byref(nnz)), h)
+    return int(nnz.value)
+
+
+def kk_spgemm_learned_numeric(h, A: "DeviceCSR", B: "DeviceCSR", c_rowptr, c_colind, c_vals):
+    a, b = A.abi(), B.abi()
+    _check(load_library().kk_spgemm_learned_numeric(h, ctypes.byref(a), ctypes.byref(b),
+                                                    ctypes.c_void_p(c_rowptr.data_ptr()),
+                                                    ctypes.c_void_p(c_colind.data_ptr()),
+                                                    ctypes.c_void_p(c_vals.data_ptr())), h)
 
 
 # ----------------------------------------------------------------------------
@@ -264,6 +362,25 @@ class SpGEMM:
         colind, vals = self.numeric(A, B, rowptr, nnz)
         return DeviceCSR(A.m, B.n, rowptr, colind, vals)
 
+    def set_predictor(self, params, quantile: float = 0.95):
+        kk_spgemm_set_predictor(self.h, params, quantile)
+
+    def learned_symbolic(self, A: DeviceCSR, B: DeviceCSR):
+        import torch
+        rowptr = torch.empty(A.m + 1, dtype=torch.int64, device=A.rowptr.device)
+        nnz = kk_spgemm_learned_symbolic(self.h, A, B, rowptr)
+        return rowptr, nnz
+
+    def learned_numeric(self, A: DeviceCSR, B: DeviceCSR, rowptr, nnz, colind=None, vals=None):
+        import torch
+        dev = A.rowptr.device
+        if colind is None:
+            colind = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+        if vals is None:
+            vals = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
+        kk_spgemm_learned_numeric(self.h, A, B, rowptr, colind, vals)
+        return colind[:nnz], vals[:nnz]
+
     def sync(self):
         kk_spgemm_sync(self.h)
 
@@ -300,3 +417,96 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, **options) -> DeviceCSR:
         C = op(A, B)
         op.sync()
     return C
+
+
+# ----------------------------------------------------------------------------
+# Batched form (include/kk_batched.h)
+# ----------------------------------------------------------------------------
+_SIGS.update({
+    "kk_spgemm_batched_symbolic": (_I32, [_P, _I32, ctypes.POINTER(KkCsr), ctypes.POINTER(KkCsr), _P,
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "kk_spgemm_batched_numeric": (_I32, [_P, _I32, ctypes.POINTER(KkCsr), ctypes.POINTER(KkCsr), _P, _P, _P]),
+})
+
+
+def _csr_array(mats):
+    arr = (KkCsr * max(1, len(mats)))()
+    for k, M in enumerate(mats):
+        arr[k] = M.abi()
+    return arr
+
+
+def kk_spgemm_batched_symbolic(h, As, Bs, c_rowptr):
+    """Returns (offsets as a numpy int64[count + 1], total nnz)."""
+    lib = load_library()
+    count = len(As)
+    a, b = _csr_array(As), _csr_array(Bs)
+    off = np.zeros(count + 1, dtype=np.int64)
+    total = ctypes.c_int64(0)
+    _check(lib.kk_spgemm_batched_symbolic(h, count, a, b,
+                                          ctypes.c_void_p(c_rowptr.data_ptr()) if c_rowptr is not None else None,
+                                          off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                          ctypes.byref(total)), h)
+    return off, int(total.value)
+
+
+def kk_spgemm_batched_numeric(h, As, Bs, c_rowptr, c_colind, c_vals):
+    lib = load_library()
+    a, b = _csr_array(As), _csr_array(Bs)
+    _check(lib.kk_spgemm_batched_numeric(h, len(As), a, b, ctypes.c_void_p(c_rowptr.data_ptr()),
+                                         ctypes.c_void_p(c_colind.data_ptr()),
+                                         ctypes.c_void_p(c_vals.data_ptr())), h)
+
+
+class BatchedSpGEMM:
+    """Batched products C_k = A_k * B_k on one handle (stream: a non-default
+    torch.cuda.Stream enables CUDA-graph capture and replay)."""
+
+    def __init__(self, stream=None, **options):
+        self.opt = make_options(**options)
+        self.stream = stream
+        self.h = kk_spgemm_handle_create(self.opt, stream)
+
+    def symbolic(self, As, Bs):
+        import torch
+        R = sum(A.m for A in As)
+        dev = As[0].rowptr.device if As else "cuda"
+        rowptr = torch.empty(R + 1, dtype=torch.int64, device=dev)
+        off, total = kk_spgemm_batched_symbolic(self.h, As, Bs, rowptr)
+        return rowptr, off, total
+
+    def numeric(self, As, Bs, rowptr, total, colind=None, vals=None):
+        import torch
+        dev = rowptr.device
+        if colind is None:
+            colind = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+        if vals is None:
+            vals = torch.empty(max(total, 1), dtype=torch.float64, device=dev)
+        kk_spgemm_batched_numeric(self.h, As, Bs, rowptr, colind, vals)
+        return colind, vals
+
+    def sync(self):
+        kk_spgemm_sync(self.h)
+
+    def stats(self):
+        return kk_spgemm_stats(self.h)
+
+    def kernel_times(self, reset=False):
+        return kk_spgemm_kernel_times(self.h, reset)
+
+    def close(self):
+        if self.h:
+            kk_spgemm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
