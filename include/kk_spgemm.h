@@ -88,7 +88,11 @@ typedef struct {
                                  dense window accumulator (needs B rows sorted) */
   int32_t batched_graph;      /* 1: batched phases are captured into CUDA graphs and replayed
                                  (needs a non-default stream) */
-  int32_t reserved[5];
+  int32_t sym_load_pct;       /* hash tables of the symbolic phase are sized so the flop bound
+                                 fills at most this percentage (10..100, default 75) */
+  int32_t num_load_pct;       /* numeric maps are sized so nnz(C(i,:)) fills at most this
+                                 percentage (10..50, default 50; the sort buffer holds half) */
+  int32_t reserved[3];
 } kk_spgemm_options;
 
 typedef struct kk_spgemm_handle_s* kk_spgemm_handle;

@@ -607,7 +607,7 @@ void build_bins(const kk_spgemm_options& o, bool numeric, std::vector<BinSpec>& 
     if (force < 1) {
       for (int ls = 5; ls <= 12; ++ls) {
         const long long S = 1ll << ls;
-        const long long hi = (S * 3) / 4;
+        const long long hi = (S * o.sym_load_pct) / 100;
         if (hi > o.sym_team_max_flop && ls > 5) break;
         out.push_back(BinSpec{kTierTeam, 32, (int)S, 0, 0, hi});
         out.push_back(BinSpec{kTierTeam, S <= 64 ? 8 : 32, (int)S, 1, 0, hi});
@@ -616,7 +616,7 @@ void build_bins(const kk_spgemm_options& o, bool numeric, std::vector<BinSpec>& 
     if (force < 2) {
       for (int ls = 13; ls <= 15; ++ls) {
         const long long S = 1ll << ls;
-        const long long hi = (S * 3) / 4;
+        const long long hi = (S * o.sym_load_pct) / 100;
         if (hi > o.sym_cta_max_flop && ls > 13) break;
         out.push_back(BinSpec{kTierCta, 512, (int)S, 1, 0, hi});
       }
@@ -626,7 +626,7 @@ void build_bins(const kk_spgemm_options& o, bool numeric, std::vector<BinSpec>& 
     if (force < 1) {
       for (int ls = 5; ls <= 11; ++ls) {
         const long long S = 1ll << ls;
-        const long long hi = S / 2;
+        const long long hi = (S * o.num_load_pct) / 100;
         if (hi > o.num_team_max_nnz && ls > 5) break;
         out.push_back(BinSpec{kTierTeam, 32, (int)S, 0, 0, hi});
         out.push_back(BinSpec{kTierTeam, S <= 64 ? 8 : 32, (int)S, 1, 0, hi});
@@ -635,7 +635,7 @@ void build_bins(const kk_spgemm_options& o, bool numeric, std::vector<BinSpec>& 
     if (force < 2) {
       for (int ls = 12; ls <= 13; ++ls) {
         const long long S = 1ll << ls;
-        const long long hi = S / 2;
+        const long long hi = (S * o.num_load_pct) / 100;
         if (hi > o.num_cta_max_nnz && ls > 12) break;
         out.push_back(BinSpec{kTierCta, 512, (int)S, 1, 0, hi});
       }
@@ -751,6 +751,8 @@ kk_status kk_spgemm_options_default(kk_spgemm_options* opt) {
   opt->num_cta_max_nnz = 4096;
   opt->use_window = 1;
   opt->batched_graph = 1;
+  opt->sym_load_pct = 75;
+  opt->num_load_pct = 50;
   return KK_OK;
 }
 
@@ -762,6 +764,8 @@ kk_status kk_spgemm_handle_create(kk_spgemm_handle* out, const kk_spgemm_options
   if (!h) return KK_ERR_OOM;
   if (opt) h->opt = *opt; else kk_spgemm_options_default(&h->opt);
   if (h->opt.arith < 0 || h->opt.arith > 2 || h->opt.force_tier < -1 || h->opt.force_tier > 3 ||
+      h->opt.sym_load_pct < 10 || h->opt.sym_load_pct > 100 || h->opt.num_load_pct < 10 ||
+      h->opt.num_load_pct > 50 ||
       h->opt.team_vec_min_len < 0) {
     delete h;
     return KK_ERR_INVALID_ARG;
@@ -1334,7 +1338,7 @@ kk_status kk_spgemm_batched_symbolic(kk_spgemm_handle h, int32_t count, const kk
     rb += A[k].m;
     sb += B[k].nnz;
   }
-  batched_bin_tables(h->b_sym, h->b_num);
+  batched_bin_tables(h->b_sym, h->b_num, h->opt.sym_load_pct, h->opt.num_load_pct);
   const size_t R1 = (size_t)(R > 0 ? R : 1);
   const int nblk = (int)((R + kBinRows - 1) / kBinRows);
   const int nblk_scan = (int)((R + kScanRows - 1) / kScanRows);

@@ -442,16 +442,17 @@ int persist_grid(int num_sms) {
 
 }  // namespace
 
-void batched_bin_tables(BBinTable& sym, BBinTable& num) {
+void batched_bin_tables(BBinTable& sym, BBinTable& num, int sym_load_pct, int num_load_pct) {
   sym = BBinTable{};
   num = BBinTable{};
-  // symbolic, keyed by flop bound: warp tables of 2^5..2^11 keys (load <= 3/4), vector and flattened
+  // symbolic, keyed by flop bound: warp tables of 2^5..2^11 keys (load <= sym_load_pct), vector
+  // and flattened; numeric rows fill at most num_load_pct (<= 50) of their map
   for (int ls = 5; ls <= 11; ++ls) {
     for (int fl = 0; fl < 2; ++fl) {
       sym.kind[sym.nb] = 0;
       sym.log2s[sym.nb] = ls;
       sym.flat[sym.nb] = fl;
-      sym.hi[sym.nb] = (3ll << ls) / 4;
+      sym.hi[sym.nb] = ((1ll << ls) * sym_load_pct) / 100;
       ++sym.nb;
     }
   }
@@ -459,7 +460,7 @@ void batched_bin_tables(BBinTable& sym, BBinTable& num) {
     sym.kind[sym.nb] = 1;
     sym.log2s[sym.nb] = ls;
     sym.flat[sym.nb] = 1;
-    sym.hi[sym.nb] = (3ll << ls) / 4;
+    sym.hi[sym.nb] = ((1ll << ls) * sym_load_pct) / 100;
     ++sym.nb;
   }
   // numeric, keyed by nnz(C(i,:)): warp maps 2^5..2^9 slots (16 B per slot), CTA 2^10..2^12
@@ -468,7 +469,7 @@ void batched_bin_tables(BBinTable& sym, BBinTable& num) {
       num.kind[num.nb] = 0;
       num.log2s[num.nb] = ls;
       num.flat[num.nb] = fl;
-      num.hi[num.nb] = (1ll << ls) / 2;
+      num.hi[num.nb] = ((1ll << ls) * num_load_pct) / 100;
       ++num.nb;
     }
   }
@@ -476,7 +477,7 @@ void batched_bin_tables(BBinTable& sym, BBinTable& num) {
     num.kind[num.nb] = 1;
     num.log2s[num.nb] = ls;
     num.flat[num.nb] = 1;
-    num.hi[num.nb] = (1ll << ls) / 2;
+    num.hi[num.nb] = ((1ll << ls) * num_load_pct) / 100;
     ++num.nb;
   }
 }

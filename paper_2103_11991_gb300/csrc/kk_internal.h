@@ -127,7 +127,7 @@ struct BBinTable {
   int32_t flat[kMaxBBins];
   long long hi[kMaxBBins];
 };
-void batched_bin_tables(BBinTable& sym, BBinTable& num);
+void batched_bin_tables(BBinTable& sym, BBinTable& num, int sym_load_pct, int num_load_pct);
 cudaError_t launch_b_prepare(cudaStream_t s, int num_sms, int32_t count, PairDesc* d, long long R,
                              int32_t* row_pair, int* status);
 cudaError_t launch_b_analyze_a(cudaStream_t s, int num_sms, long long R, const PairDesc* d,

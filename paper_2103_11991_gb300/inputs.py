@@ -117,7 +117,9 @@ def _from_sorted_coo(m: int, n: int, rows: np.ndarray, cols: np.ndarray, vals: n
 def _coo_to_csr_merge(m: int, n: int, rows: np.ndarray, cols: np.ndarray) -> tuple:
     """Sort (row, col) pairs and drop duplicates; returns (rowptr, colind)."""
     key = rows.astype(np.int64) * np.int64(n) + cols.astype(np.int64)
-    key = np.unique(key)
+    key = np.sort(key)
+    if len(key):
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     r = (key // n).astype(np.int64)
     c = (key % n).astype(np.int32)
     counts = np.bincount(r, minlength=m).astype(np.int64)
@@ -246,7 +248,10 @@ def random_rows(m: int, n: int, nnz_lo: int, nnz_hi: int, seed: int, purpose: st
     k = 2 * cnt + 8
     r = np.repeat(np.arange(m, dtype=np.int64), k)
     draws = _uniform_int(seed, purpose + ".col", int(k.sum()), 0, n - 1)
-    _, first = np.unique(r * np.int64(n) + draws, return_index=True)
+    key = r * np.int64(n) + draws
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    first = order[np.concatenate(([True], ks[1:] != ks[:-1]))] if len(ks) else order
     first.sort()
     r1, c1 = r[first], draws[first]
     rowstart = np.searchsorted(r1, np.arange(m, dtype=np.int64))

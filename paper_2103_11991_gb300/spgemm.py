@@ -49,7 +49,8 @@ class KkOptions(ctypes.Structure):
                 ("team_vec_min_len", ctypes.c_int32), ("sym_team_max_flop", ctypes.c_int32),
                 ("sym_cta_max_flop", ctypes.c_int32), ("num_team_max_nnz", ctypes.c_int32),
                 ("num_cta_max_nnz", ctypes.c_int32), ("use_window", ctypes.c_int32),
-                ("batched_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("batched_graph", ctypes.c_int32), ("sym_load_pct", ctypes.c_int32),
+                ("num_load_pct", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 # exported symbol -> (restype, argtypes)
