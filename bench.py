@@ -169,6 +169,118 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def _events_ms(fn, steps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def bench_learned(args, dA, dB, madds, plain_ms, ci, va):
+    """Learned form on the same workload: predictor trained on the GPU from the
+    training families (disjoint from this workload), then learned symbolic +
+    learned numeric per step, timed like the plain step."""
+    import torch
+    from paper_2103_11991_gb300 import learned as L
+    from paper_2103_11991_gb300 import spgemm as K
+    t0 = time.perf_counter()
+    X, y = L.make_training_set(L.training_pairs(small=False))
+    params, loss = L.train_predictor(X, y, epochs=30)
+    train_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    out = {"predictor": {"samples": int(X.shape[0]), "final_loss": loss, "train_s": train_s}}
+    del X, y
+    for label, p in (("with_network", params), ("without_network", None)):
+        op = K.SpGEMM()
+        if p is not None:
+            op.set_predictor(p, 0.95)
+
+        def step():
+            rp, nnz = op.learned_symbolic(dA, dB)
+            op.learned_numeric(dA, dB, rp, nnz, ci, va)
+
+        ms = _events_ms(step, max(3, args.steps // 2), stream)
+        op.sync()
+        st = op.stats()
+        out[label] = {"ms_per_step": ms, "value": 2.0 * madds / (ms * 1e-3) / 1e9,
+                      "speedup_vs_plain": plain_ms / ms, "onepass_rows": st["onepass_rows"],
+                      "overflow_rows": st["overflow_rows"], "heavy_rows": st["heavy_rows"],
+                      "staging_entries": st["staging_entries"]}
+        op.close()
+    out["unit"] = "GFLOP/s"
+    out["workload"] = WORKLOAD
+    return out
+
+
+def bench_batched(args):
+    """Batched form on the first `--batch-count` pairs of the 2000-pair
+    workload (seeds 5000..): one persistent launch per phase, CUDA-graph
+    replayed, against the same products as looped plain calls on one stream."""
+    import torch
+    from paper_2103_11991_gb300 import inputs as I
+    from paper_2103_11991_gb300 import spgemm as K
+    t0 = time.perf_counter()
+    pairs = I.batch_pairs(args.batch_count)
+    gen_s = time.perf_counter() - t0
+    dAs = [K.DeviceCSR.from_host(A) for A, _ in pairs]
+    dBs = [K.DeviceCSR.from_host(B) for _, B in pairs]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        op = K.BatchedSpGEMM(stream=stream)
+        rp, off, total = op.symbolic(dAs, dBs)
+        ci, va = op.numeric(dAs, dBs, rp, total)
+        op.sync()
+        madds = op.stats()["flops"]
+
+        def step():
+            r, o, t = op.symbolic(dAs, dBs)
+            op.numeric(dAs, dBs, r, t, ci, va)
+
+        ms = _events_ms(step, 3, stream)
+        op.close()
+        plain = K.SpGEMM(stream=stream)
+        outs = []
+        for a, b in zip(dAs, dBs):
+            r, n = plain.symbolic(a, b)
+            c, v = plain.numeric(a, b, r, n)
+            outs.append((c, v))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for (a, b), (c, v) in zip(zip(dAs, dBs), outs):
+            r, n = plain.symbolic(a, b)
+            plain.numeric(a, b, r, n, c, v)
+        torch.cuda.synchronize()
+        loop_ms = (time.perf_counter() - t1) * 1e3
+        plain.close()
+    return {"pairs": len(pairs), "rows": int(sum(A.m for A, _ in pairs)), "nnz_c": int(total),
+            "madds": int(madds), "ms_per_step": ms, "value": 2.0 * madds / (ms * 1e-3) / 1e9,
+            "looped_plain_ms": loop_ms, "looped_plain_value": 2.0 * madds / (loop_ms * 1e-3) / 1e9,
+            "speedup_vs_looped": loop_ms / ms, "unit": "GFLOP/s", "graph": True,
+            "generation_s": gen_s}
+
+
+def _ncu_traffic():
+    """DRAM bytes per step of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f)
+        src = os.path.join(ROOT, "paper_2103_11991_gb300", "csrc", rec["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if sha != rec["source_sha256"]:
+            return None, rec["kernel"]
+        return float(rec["dram_bytes_per_step"]), rec["kernel"]
+    except Exception:
+        return None, None
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2103_11991_gb300 import inputs as I
@@ -253,10 +365,15 @@ def run_ours(args, rank, world, local_rank):
         achieved = per_step_bytes / (dom_ms_per_step * 1e-3) / 1e9
     else:
         achieved = None
+    traffic = args.traffic
+    if traffic is None:
+        t_bytes, t_kernel = _ncu_traffic()
+        traffic = t_bytes if t_kernel == dom_name else None
     roofline = {
         "bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
         "peak_kind": peak_kind, "unit": "GB/s",
-        "frac": (achieved / peak) if achieved else None, "traffic": args.traffic,
+        "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+        "traffic_unit": "bytes per step (all launches of the kernel)",
         "algorithmic_bytes_per_step": per_step_bytes,
         "launches_per_step": launches_of_dom_per_step,
         "ms_per_step": dom_ms_per_step,
@@ -297,6 +414,12 @@ def run_ours(args, rank, world, local_rank):
         e2e_ms = float(t.item())
     e2e_value = 2.0 * madds * world / (e2e_ms * 1e-3) / 1e9
 
+    forms = {}
+    if rank == 0 and args.forms in ("all", "learned"):
+        forms["learned"] = bench_learned(args, dA, dB, madds, ms, ci, va)
+    if rank == 0 and args.forms in ("all", "batched"):
+        forms["batched"] = bench_batched(args)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         flops_row = None
@@ -324,6 +447,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk,
             "kernels": kernels,
             "hbm_gbs_step": (sym_b + num_b) / (ms * 1e-3) / 1e9,
+            "forms": forms,
         }
         print(json.dumps(out), flush=True)
     op.close()
@@ -338,7 +462,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--traffic", type=float, default=None,
-                    help="ncu DRAM bytes per launch of the dominant kernel, if captured")
+                    help="ncu DRAM bytes per step of the dominant kernel (default: profiles/ncu_traffic.json)")
+    ap.add_argument("--forms", default="all", choices=["all", "learned", "batched", "none"],
+                    help="also measure the learned and batched forms")
+    ap.add_argument("--batch-count", type=int, default=400,
+                    help="pairs of the 2000-pair batched workload to measure")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

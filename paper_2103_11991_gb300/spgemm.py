@@ -511,3 +511,4 @@ class BatchedSpGEMM:
             self.close()
         except Exception:
             pass
+
