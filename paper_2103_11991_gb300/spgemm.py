@@ -512,3 +512,24 @@ class BatchedSpGEMM:
         except Exception:
             pass
 
+
+# ----------------------------------------------------------------------------
+# Symbolic phase without allocation (include/kk_noalloc.h)
+# ----------------------------------------------------------------------------
+_SIGS.update({
+    "kk_spgemm_symbolic_noalloc": (_I32, [ctypes.POINTER(KkCsr), ctypes.POINTER(KkCsr), _P,
+                                          ctypes.POINTER(ctypes.c_int64), _P]),
+})
+NOALLOC_MAX_ROWS = 1 << 20
+
+
+def kk_spgemm_symbolic_noalloc(A: "DeviceCSR", B: "DeviceCSR", c_rowptr, stream=None) -> int:
+    """Row pointers of C = A*B into c_rowptr (int64[A.m + 1]) using only the
+    library's fixed device scratch; returns nnz(C)."""
+    lib = load_library()
+    nnz = ctypes.c_int64(0)
+    a, b = A.abi(), B.abi()
+    _check(lib.kk_spgemm_symbolic_noalloc(ctypes.byref(a), ctypes.byref(b),
+                                          ctypes.c_void_p(c_rowptr.data_ptr()), ctypes.byref(nnz),
+                                          _stream_ptr(stream)))
+    return int(nnz.value)
