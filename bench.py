@@ -291,7 +291,12 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         import torch.distributed as tdist
 
-    d = I.config_inputs(WORKLOAD)
+    if args.scale != 100:
+        # smaller grid of the same stencil: only for profiler captures
+        global WORKLOAD, WORKLOAD_DESC
+        WORKLOAD = f"stencil3d27_{args.scale}"
+        WORKLOAD_DESC = f"C=A*A, A = 3D 27-point stencil on {args.scale}^3 (profiling size)"
+    d = I.config_inputs("stencil3d27_100", scale=args.scale)
     A, B = d["A"], d["B"]
     dA, dB = K.DeviceCSR.from_host(A), K.DeviceCSR.from_host(B)
     op = K.SpGEMM()
@@ -340,20 +345,25 @@ def run_ours(args, rank, world, local_rank):
         trp, tnnz = top.symbolic(dA, dB)
         top.numeric(dA, dB, trp, tnnz, tci, tva)
     kt = top.kernel_times()
-    launches_per_step = top.stats()["launches_sym"] + top.stats()["launches_num"]
+    tst = top.stats()
+    launches_per_step = tst["launches_sym"] + tst["launches_num"]
     top.close()
     del tci, tva, trp
 
     sym_b, num_b = algorithmic_bytes(A.m, B.m, A.nnz, B.nnz, nnz)
     dom_name, (dom_ms, dom_n) = max(kt.items(), key=lambda kv: kv[1][0])
     dom_avg_ms = dom_ms / dom_n
-    num_kernels = {k: v for k, v in kt.items() if k.startswith("num_")}
-    sym_kernels = {k: v for k, v in kt.items() if k.startswith("sym_")}
-    # For this workload every numeric row falls in the dominant numeric kind, so
-    # its algorithmic bytes per step are the numeric phase's; likewise symbolic.
-    if dom_name.startswith("num_") and len(num_kernels) == 1:
-        per_step_bytes = num_b
-    elif dom_name.startswith("sym_") and len(sym_kernels) == 1:
+    # Algorithmic bytes of the rows the dominant kernel processed: their A rows
+    # (structure + values) and C rows (row pointers read, columns + values
+    # written), plus all of B (structure + values), which those rows reference.
+    tier_of = {"num_window": "window", "num_warp_vec": "team", "num_team_vec": "team",
+               "num_team_flat": "team", "num_cta": "cta", "num_dense": "dense"}
+    if dom_name in tier_of:
+        t = tier_of[dom_name]
+        rows_t = tst[f"num_{t}_rows"] if t != "window" else tst["num_window_rows"]
+        per_step_bytes = (12 * tst[f"num_{t}_a"] + 12 * (rows_t + 1) + 12 * tst[f"num_{t}_c"]
+                          + 12 * B.nnz + 4 * (B.m + 1))
+    elif dom_name.startswith("sym_"):
         per_step_bytes = sym_b
     else:
         per_step_bytes = None
@@ -467,6 +477,9 @@ def main():
                     help="also measure the learned and batched forms")
     ap.add_argument("--batch-count", type=int, default=400,
                     help="pairs of the 2000-pair batched workload to measure")
+    ap.add_argument("--scale", type=int, default=100,
+                    help="grid edge of the 27-point workload (100 = the benchmark; smaller only "
+                         "to keep profiler captures small)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -160,8 +160,10 @@ kk_status kk_spgemm_kernel_times(kk_spgemm_handle h, int32_t max_kernels, const 
  * the symbolic / numeric phase; after a learned symbolic call (kk_learned.h)
  * stats[12] = rows sent to the speculative one-pass, stats[13] = of those, rows
  * that overflowed and were re-run, stats[14] = rows predicted heavy (plain
- * path), stats[15] = staging entries. */
-kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[16]);
+ * path), stats[15] = staging entries; after a plain symbolic call
+ * stats[16..19] = C entries and stats[20..23] = A entries of the rows in each
+ * numeric tier (team, CTA, dense, window), for per-kernel byte accounting. */
+kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[24]);
 
 #ifdef __cplusplus
 }

@@ -463,6 +463,46 @@ __global__ void k_sym_classify(int32_t m, const long long* __restrict__ flop,
   }
 }
 
+// Per numeric tier: C entries and A entries of the rows binned to it (for the
+// per-kernel roofline accounting).
+struct TierOfBin {
+  int32_t nb;
+  int8_t tier[kMaxBins];
+};
+
+__global__ void k_tier_sums(int32_t m, const uint8_t* __restrict__ nbin, const int64_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ arp, TierOfBin tb, unsigned long long* tier_c,
+                            unsigned long long* tier_a) {
+  unsigned long long c[4] = {0, 0, 0, 0}, a[4] = {0, 0, 0, 0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint8_t b = nbin[i];
+    if (b == kSkipBin || b >= tb.nb) continue;
+    const int t = tb.tier[b];
+    c[t] += (unsigned long long)(rowptr[i + 1] - rowptr[i]);
+    a[t] += (unsigned long long)(arp[i + 1] - arp[i]);
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      c[t] += __shfl_xor_sync(0xffffffffu, c[t], o);
+      a[t] += __shfl_xor_sync(0xffffffffu, a[t], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (c[t]) atomicAdd(&tier_c[t], c[t]);
+      if (a[t]) atomicAdd(&tier_a[t], a[t]);
+    }
+  }
+}
+
+TierOfBin tier_of_bins(const std::vector<BinSpec>& bins) {
+  TierOfBin t{};
+  t.nb = (int32_t)bins.size();
+  for (size_t b = 0; b < bins.size() && b < (size_t)kMaxBins; ++b) t.tier[b] = (int8_t)bins[b].tier;
+  return t;
+}
+
 // ---------------------------------------------------------------------------
 // DF32 split of B's values, with the window check.
 // ---------------------------------------------------------------------------
@@ -547,7 +587,7 @@ struct kk_spgemm_handle_s {
   int32_t b_sorted = 1;
   std::vector<BinSpec> sym_bins, num_bins;
   std::vector<int32_t> num_start;  // nb + 1
-  int64_t stats[16] = {0};
+  int64_t stats[24] = {0};
   int32_t last_arith = kArithDF32;
 };
 
@@ -561,6 +601,8 @@ struct Misc {
   unsigned long long total_flop;
   long long grand;
   long long grand2;
+  unsigned long long tier_c[4];  // numeric tiers: C entries of their rows
+  unsigned long long tier_a[4];  // numeric tiers: A entries of their rows
 };
 
 kk_status fail(kk_spgemm_handle h, kk_status s, const std::string& msg) {
@@ -801,9 +843,9 @@ const char* kk_spgemm_last_error(kk_spgemm_handle h) { return h ? h->last_error.
 
 int32_t kk_spgemm_last_arith(kk_spgemm_handle h) { return h ? h->last_arith : 0; }
 
-kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[16]) {
+kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[24]) {
   if (!h || !stats) return KK_ERR_INVALID_ARG;
-  for (int i = 0; i < 16; ++i) stats[i] = h->stats[i];
+  for (int i = 0; i < 24; ++i) stats[i] = h->stats[i];
   return KK_OK;
 }
 
@@ -906,6 +948,8 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
     KK_CUDA(h, cudaGetLastError(), "scan launch");
     if ((st = run_binning(h, m, h->d_nbin.as<uint8_t>(), nbn, h->d_nrows.as<int32_t>(), num_start)) != KK_OK)
       return st;
+    k_tier_sums<<<grid_for(m, 256, h->num_sms * 8), 256, 0, s>>>(
+        m, h->d_nbin.as<uint8_t>(), c_rowptr, av.rowptr, tier_of_bins(h->num_bins), dm->tier_c, dm->tier_a);
   } else {
     KK_CUDA(h, cudaMemsetAsync(c_rowptr, 0, sizeof(int64_t), s), "memset rowptr");
     KK_CUDA(h, cudaMemsetAsync(num_start, 0, sizeof(int32_t) * (nbn + 1), s), "memset");
@@ -921,6 +965,10 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   for (int b = 0; b < nbn; ++b) ntier[h->num_bins[b].tier] += h_start[b + 1] - h_start[b];
   for (int t = 0; t < 3; ++t) h->stats[3 + t] = ntier[t];
   h->stats[11] = ntier[kTierWindow];
+  for (int t = 0; t < 4; ++t) {
+    h->stats[16 + t] = (int64_t)hm->tier_c[t];
+    h->stats[20 + t] = (int64_t)hm->tier_a[t];
+  }
   h->am = m;
   h->an = A->n;
   h->bn = B->n;

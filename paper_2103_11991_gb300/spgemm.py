@@ -199,12 +199,13 @@ def kk_spgemm_kernel_times(h, reset: bool = False) -> dict:
 
 
 def kk_spgemm_stats(h) -> dict:
-    arr = (ctypes.c_int64 * 16)()
+    arr = (ctypes.c_int64 * 24)()
     _check(load_library().kk_spgemm_stats(h, arr), h)
     keys = ["sym_team_rows", "sym_cta_rows", "sym_dense_rows", "num_team_rows", "num_cta_rows",
             "num_dense_rows", "flops", "b_sorted", "launches_sym", "launches_num",
             "sym_window_rows", "num_window_rows", "onepass_rows", "overflow_rows", "heavy_rows",
-            "staging_entries"]
+            "staging_entries", "num_team_c", "num_cta_c", "num_dense_c", "num_window_c",
+            "num_team_a", "num_cta_a", "num_dense_a", "num_window_a"]
     return {k: int(arr[i]) for i, k in enumerate(keys)}
 
 
