@@ -34,10 +34,10 @@ enum Tier : int32_t { kTierTeam = 0, kTierCta = 1, kTierDense = 2, kTierWindow =
 
 // Window tier: a row whose columns of C all lie in [row_lo, row_lo + W) gets a
 // dense bit vector of W bits (plus per-word ranks in the numeric phase).
-constexpr int kNumWindowClasses = 4;
-constexpr int32_t kWindowBits[kNumWindowClasses] = {4096, 16384, 49152, 65536};
+constexpr int kNumWindowClasses = 5;
+constexpr int32_t kWindowBits[kNumWindowClasses] = {4096, 12288, 24576, 40960, 65536};
 __host__ __device__ constexpr int32_t window_bits(int w) {
-  return w == 0 ? 4096 : w == 1 ? 16384 : w == 2 ? 49152 : 65536;
+  return w == 0 ? 4096 : w == 1 ? 12288 : w == 2 ? 24576 : w == 3 ? 40960 : 65536;
 }
 constexpr int32_t kWindowMaxNnz = 256;   // numeric window rows: nnz(C(i,:)) <= this
 constexpr int32_t kWindowFlopRatio = 128;  // window used only when W <= ratio * flop

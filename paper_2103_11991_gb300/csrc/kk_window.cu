@@ -576,8 +576,9 @@ cudaError_t launch_symbolic_window(const LaunchCtx& ctx, const BinSpec& bin, con
   cudaError_t e = cudaErrorInvalidValue;
   switch (bin.slots) {
     case 4096: e = sym_window<4096>(ctx, A, B, rows, nrows, cnt); break;
-    case 16384: e = sym_window<16384>(ctx, A, B, rows, nrows, cnt); break;
-    case 49152: e = sym_window<49152>(ctx, A, B, rows, nrows, cnt); break;
+    case 12288: e = sym_window<12288>(ctx, A, B, rows, nrows, cnt); break;
+    case 24576: e = sym_window<24576>(ctx, A, B, rows, nrows, cnt); break;
+    case 40960: e = sym_window<40960>(ctx, A, B, rows, nrows, cnt); break;
     case 65536: e = sym_window<65536>(ctx, A, B, rows, nrows, cnt); break;
   }
   timer_end(ctx.timer, ctx.stream);
@@ -594,8 +595,9 @@ cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, cons
   cudaError_t e = cudaErrorInvalidValue;
   switch (bin.slots) {
     case 4096: e = num_window<4096>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
-    case 16384: e = num_window<16384>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
-    case 49152: e = num_window<49152>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
+    case 12288: e = num_window<12288>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
+    case 24576: e = num_window<24576>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
+    case 40960: e = num_window<40960>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
     case 65536: e = num_window<65536>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
   }
   timer_end(ctx.timer, ctx.stream);
@@ -616,8 +618,9 @@ cudaError_t launch_onepass_window(const LaunchCtx& ctx, int32_t wclass, const Cs
   cudaError_t e = cudaErrorInvalidValue;
   switch (kWindowBits[wclass]) {
     case 4096: e = num_window<4096, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
-    case 16384: e = num_window<16384, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
-    case 49152: e = num_window<49152, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
+    case 12288: e = num_window<12288, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
+    case 24576: e = num_window<24576, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
+    case 40960: e = num_window<40960, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
     case 65536: e = num_window<65536, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
   }
   timer_end(ctx.timer, ctx.stream);
