@@ -92,7 +92,11 @@ typedef struct {
                                  fills at most this percentage (10..100, default 75) */
   int32_t num_load_pct;       /* numeric maps are sized so nnz(C(i,:)) fills at most this
                                  percentage (10..50, default 50; the sort buffer holds half) */
-  int32_t reserved[3];
+  int32_t structure_cache;    /* 1: the symbolic phase keeps the structure of every window row
+                                 (its non-empty 32-column words, at most 64 per row, 6 bytes
+                                 each) so that the numeric phase of the same A and B arrays
+                                 writes C's columns without re-deriving them (default 1) */
+  int32_t reserved[2];
 } kk_spgemm_options;
 
 typedef struct kk_spgemm_handle_s* kk_spgemm_handle;
@@ -162,8 +166,11 @@ kk_status kk_spgemm_kernel_times(kk_spgemm_handle h, int32_t max_kernels, const 
  * that overflowed and were re-run, stats[14] = rows predicted heavy (plain
  * path), stats[15] = staging entries; after a plain symbolic call
  * stats[16..19] = C entries and stats[20..23] = A entries of the rows in each
- * numeric tier (team, CTA, dense, window), for per-kernel byte accounting. */
-kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[24]);
+ * numeric tier (team, CTA, dense, window), for per-kernel byte accounting;
+ * stats[24] = window rows whose structure the last symbolic call kept for the
+ * numeric phase (options.structure_cache), stats[25] = (word, mask) pairs of
+ * the compressed B it built (compare with nnz(B)); stats[26..31] = 0. */
+kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[32]);
 
 #ifdef __cplusplus
 }

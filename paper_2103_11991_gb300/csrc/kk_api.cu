@@ -587,8 +587,20 @@ struct kk_spgemm_handle_s {
   int32_t b_sorted = 1;
   std::vector<BinSpec> sym_bins, num_bins;
   std::vector<int32_t> num_start;  // nb + 1
-  int64_t stats[24] = {0};
+  int64_t stats[32] = {0};
   int32_t last_arith = kArithDF32;
+  // compressed B (window tier) and the arrays it was built from
+  DevBuf d_bc;         // int2[nnzB]
+  DevBuf d_bclen;      // int32[B.m]
+  bool bc_valid = false;
+  const void* bc_key[2] = {nullptr, nullptr};
+  int32_t bc_m = 0, bc_nnz = 0;
+  // structure kept by the symbolic window kernel, and the arrays it is for
+  DevBuf d_cw;         // uint16[m * kCacheWords]
+  DevBuf d_cm;         // uint32[m * kCacheWords]
+  DevBuf d_cn;         // int32[m]
+  bool cache_valid = false;
+  const void* cache_key[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -603,6 +615,8 @@ struct Misc {
   long long grand2;
   unsigned long long tier_c[4];  // numeric tiers: C entries of their rows
   unsigned long long tier_a[4];  // numeric tiers: A entries of their rows
+  unsigned long long kept;       // window rows whose structure was kept
+  unsigned long long bc_pairs;   // pairs of the compressed B
 };
 
 kk_status fail(kk_spgemm_handle h, kk_status s, const std::string& msg) {
@@ -720,6 +734,65 @@ LaunchCtx ctx_of(kk_spgemm_handle h) {
                    h->d_rowlo.as<int32_t>()};
 }
 
+// Compressed B for the window tier (sorted B only).  A symbolic call always
+// rebuilds it (force); a numeric call rebuilds it only when B's index arrays
+// are not the ones it was built from.  *built = 1 when a kernel was launched.
+kk_status ensure_bcomp(kk_spgemm_handle h, const CsrView& bv, bool force, BComp* out, int* built) {
+  out->bc = nullptr;
+  out->len = nullptr;
+  *built = 0;
+  if (!h->opt.use_window || !h->b_sorted || bv.m <= 0) return KK_OK;
+  const bool same = h->bc_valid && h->bc_key[0] == bv.rowptr && h->bc_key[1] == bv.colind &&
+                    h->bc_m == bv.m && h->bc_nnz == bv.nnz;
+  if (force || !same) {
+    h->bc_valid = false;
+    KK_CUDA(h, h->d_bc.ensure(sizeof(int2) * (size_t)(bv.nnz > 0 ? bv.nnz : 1)), "alloc compressed B");
+    KK_CUDA(h, h->d_bclen.ensure(sizeof(int32_t) * (size_t)bv.m), "alloc compressed B");
+    KK_CUDA(h, launch_compress_b(ctx_of(h), bv, h->d_bc.as<int2>(), h->d_bclen.as<int32_t>(),
+                                 &h->d_misc.as<Misc>()->bc_pairs),
+            "compress launch");
+    h->bc_valid = true;
+    h->bc_key[0] = bv.rowptr;
+    h->bc_key[1] = bv.colind;
+    h->bc_m = bv.m;
+    h->bc_nnz = bv.nnz;
+    *built = 1;
+  }
+  out->bc = h->d_bc.as<int2>();
+  out->len = h->d_bclen.as<int32_t>();
+  return KK_OK;
+}
+
+// Structure cache for the symbolic window kernel: every row starts without
+// kept structure (n = -1); null pointers when the option is off or no row of
+// the call takes the window tier.
+kk_status cache_for_symbolic(kk_spgemm_handle h, int32_t m, bool any_window, const CsrView& av,
+                             const CsrView& bv, WinCache* out) {
+  *out = WinCache{nullptr, nullptr, nullptr, nullptr};
+  h->cache_valid = false;
+  if (!h->opt.structure_cache || !any_window || m <= 0) return KK_OK;
+  KK_CUDA(h, h->d_cw.ensure(sizeof(uint16_t) * (size_t)m * kCacheWords), "alloc structure cache");
+  KK_CUDA(h, h->d_cm.ensure(sizeof(uint32_t) * (size_t)m * kCacheWords), "alloc structure cache");
+  KK_CUDA(h, h->d_cn.ensure(sizeof(int32_t) * (size_t)m), "alloc structure cache");
+  KK_CUDA(h, cudaMemsetAsync(h->d_cn.p, 0xFF, sizeof(int32_t) * (size_t)m, h->stream), "memset cache");
+  *out = WinCache{h->d_cw.as<uint16_t>(), h->d_cm.as<uint32_t>(), h->d_cn.as<int32_t>(),
+                  &h->d_misc.as<Misc>()->kept};
+  h->cache_valid = true;
+  h->cache_key[0] = av.rowptr;
+  h->cache_key[1] = av.colind;
+  h->cache_key[2] = bv.rowptr;
+  h->cache_key[3] = bv.colind;
+  return KK_OK;
+}
+
+// The kept structure, if it belongs to these index arrays.
+WinCacheView cache_view(kk_spgemm_handle h, const CsrView& av, const CsrView& bv) {
+  if (!h->cache_valid || h->cache_key[0] != av.rowptr || h->cache_key[1] != av.colind ||
+      h->cache_key[2] != bv.rowptr || h->cache_key[3] != bv.colind)
+    return WinCacheView{nullptr, nullptr, nullptr};
+  return WinCacheView{h->d_cw.as<uint16_t>(), h->d_cm.as<uint32_t>(), h->d_cn.as<int32_t>()};
+}
+
 int grid_for(long long work, int per_block, int cap) {
   long long g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -795,6 +868,7 @@ kk_status kk_spgemm_options_default(kk_spgemm_options* opt) {
   opt->batched_graph = 1;
   opt->sym_load_pct = 75;
   opt->num_load_pct = 50;
+  opt->structure_cache = 1;
   return KK_OK;
 }
 
@@ -807,7 +881,7 @@ kk_status kk_spgemm_handle_create(kk_spgemm_handle* out, const kk_spgemm_options
   if (opt) h->opt = *opt; else kk_spgemm_options_default(&h->opt);
   if (h->opt.arith < 0 || h->opt.arith > 2 || h->opt.force_tier < -1 || h->opt.force_tier > 3 ||
       h->opt.sym_load_pct < 10 || h->opt.sym_load_pct > 100 || h->opt.num_load_pct < 10 ||
-      h->opt.num_load_pct > 50 ||
+      h->opt.num_load_pct > 50 || h->opt.structure_cache < 0 || h->opt.structure_cache > 1 ||
       h->opt.team_vec_min_len < 0) {
     delete h;
     return KK_ERR_INVALID_ARG;
@@ -843,9 +917,9 @@ const char* kk_spgemm_last_error(kk_spgemm_handle h) { return h ? h->last_error.
 
 int32_t kk_spgemm_last_arith(kk_spgemm_handle h) { return h ? h->last_arith : 0; }
 
-kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[24]) {
+kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[32]) {
   if (!h || !stats) return KK_ERR_INVALID_ARG;
-  for (int i = 0; i < 24; ++i) stats[i] = h->stats[i];
+  for (int i = 0; i < 32; ++i) stats[i] = h->stats[i];
   return KK_OK;
 }
 
@@ -917,6 +991,14 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   if (m > 0) {
     KK_CUDA(h, cudaMemsetAsync(h->d_cnt.p, 0, sizeof(int32_t) * (size_t)m, s), "memset counts");
     LaunchCtx ctx = ctx_of(h);
+    bool any_win = false;
+    for (int b = 0; b < nbs; ++b)
+      if (h->sym_bins[b].tier == kTierWindow && h_start[b + 1] > h_start[b]) any_win = true;
+    BComp bcomp;
+    int bc_built = 0;
+    if ((st = ensure_bcomp(h, bv, true, &bcomp, &bc_built)) != KK_OK) return st;
+    WinCache wcache;
+    if ((st = cache_for_symbolic(h, m, any_win, av, bv, &wcache)) != KK_OK) return st;
     int64_t tier_rows[4] = {0, 0, 0, 0};
     for (int b = 0; b < nbs; ++b) {
       const int cnt = h_start[b + 1] - h_start[b];
@@ -924,8 +1006,8 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
       tier_rows[h->sym_bins[b].tier] += cnt;
       const int32_t* rows = h->d_srows.as<int32_t>() + h_start[b];
       cudaError_t e = h->sym_bins[b].tier == kTierWindow
-                          ? launch_symbolic_window(ctx, h->sym_bins[b], av, bv, rows, cnt,
-                                                   h->d_cnt.as<int32_t>())
+                          ? launch_symbolic_window(ctx, h->sym_bins[b], av, bv, bcomp, rows, cnt,
+                                                   h->d_cnt.as<int32_t>(), wcache)
                           : launch_symbolic_bin(ctx, h->sym_bins[b], av, bv, h->b_sorted, rows, cnt,
                                                 h->d_cnt.as<int32_t>());
       if (e != cudaSuccess) return cuda_fail(h, e, "symbolic launch");
@@ -935,7 +1017,7 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
     int64_t nb_launched = 0;
     for (int b = 0; b < nbs; ++b) nb_launched += (h_start[b + 1] - h_start[b]) > 0 ? 1 : 0;
     // analyze (2) + binning (3) + symbolic bins + scan (3) + numeric binning (3)
-    h->stats[8] = (bv.m > 0 ? 1 : 0) + 1 + 3 + nb_launched + 3 + 3;
+    h->stats[8] = (bv.m > 0 ? 1 : 0) + 1 + 3 + bc_built + nb_launched + 3 + 3 + 1;
     // scan + numeric bins
     timer_begin(h->timer, s, "scan");
     k_scan_partial<<<nblk_scan, kScanBlock, 0, s>>>(m, h->d_cnt.as<int32_t>(), h->d_scan.as<long long>());
@@ -969,6 +1051,8 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
     h->stats[16 + t] = (int64_t)hm->tier_c[t];
     h->stats[20 + t] = (int64_t)hm->tier_a[t];
   }
+  h->stats[24] = (int64_t)hm->kept;
+  h->stats[25] = (int64_t)hm->bc_pairs;
   h->am = m;
   h->an = A->n;
   h->bn = B->n;
@@ -1012,14 +1096,25 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
   LaunchCtx ctx = ctx_of(h);
   const int nbn = (int)h->num_bins.size();
   h->stats[9] = (arith == kArithDF32 && bv.nnz > 0) ? 1 : 0;
+  bool any_win = false;
+  for (int b = 0; b < nbn; ++b)
+    if (h->num_bins[b].tier == kTierWindow && h->num_start[b + 1] > h->num_start[b]) any_win = true;
+  BComp bcomp{nullptr, nullptr};
+  if (any_win) {
+    int built = 0;
+    if ((st = ensure_bcomp(h, bv, false, &bcomp, &built)) != KK_OK) return st;
+    h->stats[9] += built;
+  }
+  const WinCacheView wview = cache_view(h, av, bv);
   for (int b = 0; b < nbn; ++b) {
     const int cnt = h->num_start[b + 1] - h->num_start[b];
     if (cnt <= 0) continue;
     h->stats[9] += 1;
     const int32_t* rows = h->d_nrows.as<int32_t>() + h->num_start[b];
     cudaError_t e = h->num_bins[b].tier == kTierWindow
-                        ? launch_numeric_window(ctx, h->num_bins[b], av, bv, bsplit, &dm->range_bad,
-                                                arith, c_rowptr, rows, cnt, c_colind, c_vals)
+                        ? launch_numeric_window(ctx, h->num_bins[b], av, bv, bcomp, wview, bsplit,
+                                                &dm->range_bad, arith, c_rowptr, rows, cnt, c_colind,
+                                                c_vals)
                         : launch_numeric_bin(ctx, h->num_bins[b], av, bv, h->b_sorted, bsplit,
                                              &dm->range_bad, arith, c_rowptr, rows, cnt, c_colind,
                                              c_vals, h->opt.debug_checks);
@@ -1169,6 +1264,12 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
     timer_end(h->timer, s);
   }
   int64_t light = 0, heavy = 0;
+  BComp bcomp{nullptr, nullptr};
+  if (m > 0) {
+    int bc_built = 0;
+    if ((st = ensure_bcomp(h, bv, true, &bcomp, &bc_built)) != KK_OK) return st;
+  }
+  h->cache_valid = false;
   if (m > 0) {
     KK_CUDA(h, cudaMemsetAsync(h->d_cnt.p, 0, sizeof(int32_t) * (size_t)m, s), "memset counts");
     for (int c = 0; c < kLearnedHeavy; ++c) {
@@ -1181,7 +1282,7 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
               ? launch_onepass(ctx, 5 + c, av, bv, h->d_bsplit.as<float2>(), &dm->range_bad, arith,
                                h->d_soff.as<int64_t>(), lrows, n, h->d_scol.as<int32_t>(),
                                h->d_sval.as<double>(), h->d_cnt.as<int32_t>())
-              : launch_onepass_window(ctx, c - kOnepassClasses, av, bv, h->d_bsplit.as<float2>(),
+              : launch_onepass_window(ctx, c - kOnepassClasses, av, bv, bcomp, h->d_bsplit.as<float2>(),
                                       &dm->range_bad, arith, h->d_soff.as<int64_t>(), h->d_cap.as<int32_t>(),
                                       lrows, n, h->d_scol.as<int32_t>(), h->d_sval.as<double>(),
                                       h->d_cnt.as<int32_t>());
@@ -1201,6 +1302,11 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
     KK_CUDA(h, cudaMemcpyAsync(h_start, sym_start, sizeof(int32_t) * (nbs + 1), cudaMemcpyDeviceToHost, s),
             "readback");
     KK_CUDA(h, cudaStreamSynchronize(s), "sync");
+    bool any_win = false;
+    for (int b = 0; b < nbs; ++b)
+      if (h->sym_bins[b].tier == kTierWindow && h_start[b + 1] > h_start[b]) any_win = true;
+    WinCache wcache;
+    if ((st = cache_for_symbolic(h, m, any_win, av, bv, &wcache)) != KK_OK) return st;
     int64_t plain_rows = 0;
     for (int b = 0; b < nbs; ++b) {
       const int cnt = h_start[b + 1] - h_start[b];
@@ -1208,7 +1314,8 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
       plain_rows += cnt;
       const int32_t* rows = h->d_srows.as<int32_t>() + h_start[b];
       cudaError_t e2 = h->sym_bins[b].tier == kTierWindow
-                           ? launch_symbolic_window(ctx, h->sym_bins[b], av, bv, rows, cnt, h->d_cnt.as<int32_t>())
+                           ? launch_symbolic_window(ctx, h->sym_bins[b], av, bv, bcomp, rows, cnt,
+                                                    h->d_cnt.as<int32_t>(), wcache)
                            : launch_symbolic_bin(ctx, h->sym_bins[b], av, bv, h->b_sorted, rows, cnt,
                                                  h->d_cnt.as<int32_t>());
       if (e2 != cudaSuccess) return cuda_fail(h, e2, "symbolic launch");
@@ -1242,6 +1349,8 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
   h->nnz_c = m > 0 ? hm->grand : 0;
   h->num_start.assign(h_start, h_start + nbn + 1);
   h->lnum_start.assign(h_start2, h_start2 + nbn + 1);
+  h->stats[24] = (int64_t)hm->kept;
+  h->stats[25] = (int64_t)hm->bc_pairs;
   h->am = m;
   h->an = A->n;
   h->bn = B->n;
@@ -1275,13 +1384,22 @@ kk_status kk_spgemm_learned_numeric(kk_spgemm_handle h, const kk_csr* A, const k
   const int32_t arith = h->last_arith;
   const float2* bsplit = arith == kArithDF32 ? h->d_bsplit.as<float2>() : nullptr;
   const int nbn = (int)h->num_bins.size();
+  bool any_win = false;
+  for (int b = 0; b < nbn; ++b)
+    if (h->num_bins[b].tier == kTierWindow && h->lnum_start[b + 1] > h->lnum_start[b]) any_win = true;
+  BComp bcomp{nullptr, nullptr};
+  if (any_win) {
+    int built = 0;
+    if ((st = ensure_bcomp(h, bv, false, &bcomp, &built)) != KK_OK) return st;
+  }
+  const WinCacheView wview = cache_view(h, av, bv);
   for (int b = 0; b < nbn; ++b) {
     const int cnt = h->lnum_start[b + 1] - h->lnum_start[b];
     if (cnt <= 0) continue;
     const int32_t* rows = h->d_lrows2.as<int32_t>() + h->lnum_start[b];
     e = h->num_bins[b].tier == kTierWindow
-            ? launch_numeric_window(ctx, h->num_bins[b], av, bv, bsplit, &dm->range_bad, arith, c_rowptr,
-                                    rows, cnt, c_colind, c_vals)
+            ? launch_numeric_window(ctx, h->num_bins[b], av, bv, bcomp, wview, bsplit, &dm->range_bad,
+                                    arith, c_rowptr, rows, cnt, c_colind, c_vals)
             : launch_numeric_bin(ctx, h->num_bins[b], av, bv, h->b_sorted, bsplit, &dm->range_bad, arith,
                                  c_rowptr, rows, cnt, c_colind, c_vals, h->opt.debug_checks);
     if (e != cudaSuccess) return cuda_fail(h, e, "numeric launch");
@@ -1586,7 +1704,7 @@ kk_status kk_spgemm_destroy(kk_spgemm_handle h) {
                     &h->d_sval, &h->d_sball, &h->d_nbin2, &h->d_lrows, &h->d_lrows2, &h->d_mm,
                     &h->d_bdesc, &h->d_rowpair, &h->d_bflop, &h->d_bsbin, &h->d_bnbin, &h->d_bsrows,
                     &h->d_bnrows, &h->d_bcnt, &h->d_btiles, &h->d_bstart, &h->d_bqueue, &h->d_bsplit2,
-                    &h->d_boff})
+                    &h->d_boff, &h->d_bc, &h->d_bclen, &h->d_cw, &h->d_cm, &h->d_cn})
     b->release();
   for (void* p : {h->h_bdesc, h->h_bdesc2, h->h_boff})
     if (p) cudaFreeHost(p);

@@ -42,6 +42,33 @@ __host__ __device__ constexpr int32_t window_bits(int w) {
 constexpr int32_t kWindowMaxNnz = 256;   // numeric window rows: nnz(C(i,:)) <= this
 constexpr int32_t kWindowFlopRatio = 128;  // window used only when W <= ratio * flop
 
+// Compressed B (the paper's B_C): row j of B as (column >> 5, 32-bit column
+// mask) pairs in column order, stored at B's own row offsets
+// bc[B.rowptr[j] .. B.rowptr[j] + len[j]).  Built only for sorted B.
+struct BComp {
+  const int2* bc;
+  const int32_t* len;
+};
+
+// Per-row structure kept by the symbolic window kernel for the numeric phase
+// of the same A and B: the row's non-empty window words (index relative to
+// the word of row_lo, at most kCacheWords) and their bits; n[i] = number of
+// words, -1 if the row has no kept structure.
+constexpr int kCacheWords = 64;
+struct WinCache {
+  uint16_t* w;
+  uint32_t* m;
+  int32_t* n;
+  unsigned long long* kept;  // += rows whose structure was kept
+};
+struct WinCacheView {
+  const uint16_t* w;
+  const uint32_t* m;
+  const int32_t* n;
+};
+cudaError_t launch_compress_b(const LaunchCtx& ctx, const CsrView& B, int2* bc, int32_t* len,
+                              unsigned long long* pairs);
+
 // One bin of rows: its tier and the accumulator geometry.
 struct BinSpec {
   int32_t tier;
@@ -69,11 +96,11 @@ cudaError_t launch_numeric_bin(const LaunchCtx& ctx, const BinSpec& bin, const C
 
 // Window-tier launches (kk_window.cu).
 cudaError_t launch_symbolic_window(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,
-                                   const CsrView& B, const int32_t* rows, int32_t nrows,
-                                   int32_t* cnt);
+                                   const CsrView& B, const BComp& bcomp, const int32_t* rows,
+                                   int32_t nrows, int32_t* cnt, const WinCache& cache);
 cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,
-                                  const CsrView& B, const float2* b_split,
-                                  const int32_t* b_range_bad, int32_t arith,
+                                  const CsrView& B, const BComp& bcomp, const WinCacheView& cache,
+                                  const float2* b_split, const int32_t* b_range_bad, int32_t arith,
                                   const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
                                   int32_t* c_colind, double* c_vals);
 
@@ -92,7 +119,7 @@ constexpr int kOnepassClasses = 5;
 // kLearnedHeavy = plain path.
 constexpr int kLearnedHeavy = kOnepassClasses + kNumWindowClasses;
 cudaError_t launch_onepass_window(const LaunchCtx& ctx, int32_t wclass, const CsrView& A,
-                                  const CsrView& B, const float2* b_split,
+                                  const CsrView& B, const BComp& bcomp, const float2* b_split,
                                   const int32_t* b_range_bad, int32_t arith, const int64_t* soff,
                                   const int32_t* cap, const int32_t* rows, int32_t nrows,
                                   int32_t* scol, double* sval, int32_t* cnt_out);

@@ -2,181 +2,185 @@
 //
 // The paper's dense accumulator (Sec. "Standard SpGEMM Kernel": a bit vector
 // for the symbolic phase, a scalar array for the numeric phase) is kept in
-// shared memory here, over the window [lo, lo + W) that holds every column of
-// C(i,:) (lo = the smallest first column, lo + span - 1 the largest last column
-// of the B rows that A(i,:) references; rows of B must be sorted).  One warp per
-// row; lanes split each B row, A entries are taken in storage order.
+// shared memory here, over a window of 32-column words starting at the word
+// that holds lo = the smallest first column of the B rows A(i,:) references
+// (rows of B must be sorted, so the window spans at most W + 31 columns).  One
+// warp per row.
 //
-//   symbolic: set the bit of every product's column (atomicOr), then
-//             nnz(C(i,:)) = popcount of the window;
-//   numeric:  same bits; per-word prefix counts give every column its rank
-//             (its position in the sorted row), so the column indices are
-//             written straight from the bits and each product adds into the
-//             dense value slot rank = prefix[w] + popc(bits[w] & below(b)).
+//   symbolic: OR every (word, mask) pair of the compressed rows B_C(j,:)
+//             (the paper's B_C, Sec. "Standard SpGEMM Kernel": columns stored
+//             as bits, accumulation = bitwise OR) into the window; nnz(C(i,:))
+//             is the popcount of the non-empty words, found through one
+//             summary bit per word.  The row's non-empty words (up to
+//             kCacheWords) are kept as its structure for the numeric phase.
+//   numeric:  the words come from that structure (or are rebuilt from B_C);
+//             per-word prefix counts give every column its rank (its position
+//             in the sorted row), so column indices are written straight from
+//             the bits and each product adds into the dense value slot
+//             rank = prefix[w] + popc(bits[w] & below(b)).
 // There is no hashing, no probing and no sort: the bit vector is the sorted
 // order.  Updates of one output entry happen in A-row order without atomics
 // because the columns of a sorted B row are distinct.
 #include "kk_internal.h"
+#include "kk_rowops.cuh"
 #include "kk_visit.cuh"
 
 namespace kk {
 namespace {
 
 using u64 = unsigned long long;
+constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWinWarps = 4;  // warps (rows in flight) per CTA
 constexpr int kWinBatch = 8;  // A entries whose B loads are issued together
 
+constexpr size_t al16(size_t x) { return (x + 15) / 16 * 16; }
+
+// Words of a W-bit window that may start anywhere inside its first word,
+// padded to a multiple of 4; one summary bit per word.
 template <int W>
-struct SymWinGeom {
-  static constexpr int WORDS = W / 32;
-  static constexpr int SUMS = (WORDS + 31) / 32;  // summary words: one bit per word
-  // bits u32[WORDS] | sum u32[SUMS] (padded to 16 B) | ainfo int2[32]
-  static constexpr size_t kSumOff = (size_t)WORDS * 4;
-  static constexpr size_t kInfoOff = kSumOff + (size_t)((SUMS + 3) / 4) * 16;
-  static constexpr size_t kWarpBytes = kInfoOff + 32 * 8;
+struct WinWords {
+  static constexpr int WORDS = W / 32 + 4;
+  static constexpr int SUMS = (WORDS + 31) / 32;
 };
 
 template <int W>
-struct NumWinGeom {
-  static constexpr int WORDS = W / 32;
-  static constexpr int SUMS = (WORDS + 31) / 32;
+struct SymWinGeom : WinWords<W> {
+  using WinWords<W>::WORDS;
+  using WinWords<W>::SUMS;
+  // bits u32[WORDS] | sum u32[SUMS] | list u16[kCacheWords]
+  static constexpr size_t kSumOff = al16((size_t)WORDS * 4);
+  static constexpr size_t kListOff = al16(kSumOff + (size_t)SUMS * 4);
+  static constexpr size_t kWarpBytes = al16(kListOff + (size_t)kCacheWords * 2);
+};
+
+template <int W>
+struct NumWinGeom : WinWords<W> {
+  using WinWords<W>::WORDS;
+  using WinWords<W>::SUMS;
   // bits u32[WORDS] | sum u32[SUMS] | prefix u16[WORDS] | list u16[kWindowMaxNnz]
-  // | vacc u64[kWindowMaxNnz] | ainfo int4[32]
-  static constexpr size_t kSumOff = (size_t)WORDS * 4;
-  static constexpr size_t kPreOff = kSumOff + (size_t)((SUMS + 3) / 4) * 16;
-  static constexpr size_t kListOff = kPreOff + (size_t)WORDS * 2;
-  static constexpr size_t kValOff = kListOff + (size_t)kWindowMaxNnz * 2;
-  static constexpr size_t kInfoOff = kValOff + (size_t)(kWindowMaxNnz + 2) * 8;  // + spare slot
+  // | vacc u64[kWindowMaxNnz + 2] (the last ones: spare slot) | ainfo int4[32]
+  static constexpr size_t kSumOff = al16((size_t)WORDS * 4);
+  static constexpr size_t kPreOff = al16(kSumOff + (size_t)SUMS * 4);
+  static constexpr size_t kListOff = al16(kPreOff + (size_t)WORDS * 2);
+  static constexpr size_t kValOff = al16(kListOff + (size_t)kWindowMaxNnz * 2);
+  static constexpr size_t kInfoOff = al16(kValOff + (size_t)(kWindowMaxNnz + 2) * 8);
   static constexpr size_t kWarpBytes = kInfoOff + 32 * 16;
 };
 
-// Set bit o of the window and, the first time a word becomes non-empty, its
-// summary bit.
-__device__ __forceinline__ void window_set(uint32_t* bits, uint32_t* sum, uint32_t o) {
-  const uint32_t w = o >> 5;
-  const uint32_t old = atomicOr(&bits[w], 1u << (o & 31));
-  if (old == 0u) atomicOr(&sum[w >> 5], 1u << (w & 31));
-}
-
-// Set the window bits of every product of row entries [pa, pe).  ainfo2 is
-// the warp's staging area for (B row start, length).
-template <int W>
-__device__ __forceinline__ void window_set_bits(uint32_t* bits, uint32_t* sum, int2* ainfo2, int lo,
-                                                int pa, int pe, const int32_t* __restrict__ acol,
-                                                const int32_t* __restrict__ brp,
-                                                const int32_t* __restrict__ bcol, int lane,
-                                                int* status) {
+// OR the compressed rows B_C(j,:) of the entries [pa, pe) of A(i,:) into the
+// window whose word 0 is column word lo_w; the first setter of a word also sets
+// its summary bit.  Lanes take the pairs of 32 / G A entries at a time, G the
+// power of two that covers the longest compressed row of the chunk.
+template <int WORDS>
+__device__ __forceinline__ void bc_set_bits(uint32_t* bits, uint32_t* sum, int lo_w, int pa, int pe,
+                                            const int32_t* __restrict__ acol,
+                                            const int32_t* __restrict__ brp,
+                                            const int2* __restrict__ bc,
+                                            const int32_t* __restrict__ bclen, int lane,
+                                            int* status) {
+  int bad = 0;
   for (int p0 = pa; p0 < pe; p0 += 32) {
     const int p = p0 + lane;
-    int2 info = make_int2(0, 0);
+    int x = 0, y = 0;
     if (p < pe) {
       const int j = acol[p];
-      info.x = brp[j];
-      info.y = brp[j + 1] - info.x;
+      x = brp[j];
+      y = bclen[j];
     }
-    ainfo2[lane] = info;
-    __syncwarp();
     const int nch = min(32, pe - p0);
-    const unsigned maxlen = __reduce_max_sync(0xffffffffu, (unsigned)info.y);
-    int bad = 0;
-    if (maxlen <= 32u) {
-      for (int t0 = 0; t0 < nch; t0 += kWinBatch) {
-        int cols[kWinBatch];
+    const unsigned maxlen = __reduce_max_sync(kFull, (unsigned)y);
+    if (maxlen <= 16u) {
+      const int lg = maxlen <= 1u ? 0 : maxlen <= 2u ? 1 : maxlen <= 4u ? 2 : maxlen <= 8u ? 3 : 4;
+      const int per = 32 >> lg;
+      const int sub = lane >> lg, e = lane & ((1 << lg) - 1);
+      for (int t0 = 0; t0 < nch; t0 += 4 * per) {
+        int2 v[4];
 #pragma unroll
-        for (int u = 0; u < kWinBatch; ++u) {
-          cols[u] = -1;
-          if (t0 + u < nch) {
-            const int2 in = ainfo2[t0 + u];
-            if (lane < in.y) cols[u] = bcol[in.x + lane];
-          }
+        for (int u = 0; u < 4; ++u) {
+          const int t = t0 + u * per + sub;
+          const int xs = __shfl_sync(kFull, x, t & 31);
+          const int ys = __shfl_sync(kFull, y, t & 31);
+          v[u] = make_int2(0, 0);
+          if (t < nch && e < ys) v[u] = bc[xs + e];
         }
 #pragma unroll
-        for (int u = 0; u < kWinBatch; ++u) {
-          if (cols[u] >= 0) {
-            const uint32_t o = (uint32_t)(cols[u] - lo);
-            if (o < (uint32_t)W) window_set(bits, sum, o);
-            else bad = 1;
+        for (int u = 0; u < 4; ++u) {
+          if (v[u].y != 0) {
+            const uint32_t w = (uint32_t)(v[u].x - lo_w);
+            if (w < (uint32_t)WORDS) {
+              const uint32_t old = atomicOr(&bits[w], (uint32_t)v[u].y);
+              if (old == 0u) atomicOr(&sum[w >> 5], 1u << (w & 31));
+            } else {
+              bad = 1;
+            }
           }
         }
       }
     } else {
       for (int t = 0; t < nch; ++t) {
-        const int2 in = ainfo2[t];
-        for (int q = lane; q < in.y; q += 32) {
-          const uint32_t o = (uint32_t)(bcol[in.x + q] - lo);
-          if (o < (uint32_t)W) window_set(bits, sum, o);
-          else bad = 1;
+        const int xs = __shfl_sync(kFull, x, t);
+        const int ys = __shfl_sync(kFull, y, t);
+        for (int e = lane; e < ys; e += 32) {
+          const int2 v = bc[xs + e];
+          const uint32_t w = (uint32_t)(v.x - lo_w);
+          if (w < (uint32_t)WORDS) {
+            const uint32_t old = atomicOr(&bits[w], (uint32_t)v.y);
+            if (old == 0u) atomicOr(&sum[w >> 5], 1u << (w & 31));
+          } else {
+            bad = 1;
+          }
         }
       }
     }
-    if (bad) set_status(status, KK_ERR_CAPACITY);
-    __syncwarp();
   }
+  if (bad) set_status(status, KK_ERR_CAPACITY);
+  __syncwarp();
 }
 
-// Value pass of a compact row (columns of the lane's products in pcol[],
-// -1 where the lane has no product).  Ranks are computed for a whole batch
-// before the updates; lanes without a product update a spare slot
-// (kWindowMaxNnz) instead of branching, so the update path does not diverge.
-template <int W, bool DFM>
-__device__ __forceinline__ void compact_values(const int (&pcol)[32], const int4* ainfo, int nch,
-                                               int lo, const uint32_t* bits, const uint16_t* pre,
-                                               u64* vacc, const float2* __restrict__ bspl,
-                                               const double* __restrict__ bval, int lane) {
-  constexpr int WORDS = W / 32;
+// Ordered list of the window's non-empty words from the summary bits (which
+// are cleared); list receives the first `cap` of them.  Returns their number.
+template <int SUMS>
+__device__ __forceinline__ int window_list(uint32_t* sum, uint16_t* list, int cap, int lane) {
+  int carry = 0;
 #pragma unroll
-  for (int t0 = 0; t0 < 32; t0 += kWinBatch) {
-    if (t0 < nch) {
-      float2 bv[kWinBatch];
-      int rk[kWinBatch];
-#pragma unroll
-      for (int u = 0; u < kWinBatch; ++u) {
-        const int c = pcol[t0 + u];
-        const bool ok = c >= 0;
-        const int q = ainfo[t0 + u].x + lane;
-        if (DFM) {
-          bv[u] = ok ? bspl[q] : make_float2(0.f, 0.f);
-        } else {
-          const long long bb = ok ? __double_as_longlong(bval[q]) : 0ll;
-          bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)), __int_as_float((int)(bb >> 32)));
-        }
-        const uint32_t o = ok ? (uint32_t)(c - lo) : 0u;
-        const uint32_t w = min(o >> 5, (uint32_t)(WORDS - 1));
-        const int r = (int)pre[w] + __popc(bits[w] & ((1u << (o & 31)) - 1u));
-        rk[u] = (ok && o < (uint32_t)W) ? min(r, kWindowMaxNnz) : kWindowMaxNnz;
-      }
-#pragma unroll
-      for (int u = 0; u < kWinBatch; ++u) {
-        if (t0 + u < nch) {
-          const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
-          if (DFM) {
-            DF a, b;
-            a.hi = __int_as_float(az.x);
-            a.lo = __int_as_float(az.y);
-            b.hi = bv[u].x;
-            b.lo = bv[u].y;
-            DF acc = df_unpack(vacc[rk[u]]);
-            df_fma(acc, a, b);
-            vacc[rk[u]] = df_pack(acc);
-          } else {
-            const double a = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
-            const double b = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
-                                                  (unsigned)__float_as_int(bv[u].x));
-            double* v = reinterpret_cast<double*>(&vacc[rk[u]]);
-            *v = fma(a, b, *v);
-          }
-          __syncwarp();  // this A entry's updates are visible before the next one's
-        }
-      }
+  for (int k = 0; k < (SUMS + 31) / 32; ++k) {
+    const int sw = k * 32 + lane;
+    uint32_t m = sw < SUMS ? sum[sw] : 0u;
+    const int c = __popc(m);
+    const int incl = team_inclusive_scan<32>(c, lane, kFull);
+    int pos = carry + incl - c;
+    carry += __shfl_sync(kFull, incl, 31);
+    if (sw < SUMS) sum[sw] = 0u;
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      if (pos < cap) list[pos] = (uint16_t)(sw * 32 + b);
+      ++pos;
     }
   }
+  __syncwarp();
+  return carry;
+}
+
+// Popcount of the whole window, clearing it (rows with more non-empty words
+// than the list holds).
+template <int WORDS>
+__device__ __forceinline__ int window_count_clear(uint32_t* bits, int lane) {
+  int c = 0;
+  for (int w = lane * 4; w < WORDS; w += 128) {
+    uint4* q = reinterpret_cast<uint4*>(&bits[w]);
+    const uint4 v = *q;
+    c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+    *q = make_uint4(0u, 0u, 0u, 0u);
+  }
+  return c;
 }
 
 template <int W>
 __global__ void __launch_bounds__(kWinWarps * 32, 8)
-k_sym_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo,
+k_sym_window(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ row_lo,
              const int32_t* __restrict__ rows, int32_t nrows, int32_t* __restrict__ cnt,
-             int* status) {
+             WinCache cache, int* status) {
   using G = SymWinGeom<W>;
   constexpr int WORDS = G::WORDS;
   constexpr int SUMS = G::SUMS;
@@ -185,8 +189,8 @@ k_sym_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo,
   unsigned char* base = smem_raw + (size_t)warp * G::kWarpBytes;
   uint32_t* bits = reinterpret_cast<uint32_t*>(base);
   uint32_t* sum = reinterpret_cast<uint32_t*>(base + G::kSumOff);
-  int2* ainfo2 = reinterpret_cast<int2*>(base + G::kInfoOff);
-  // whole window cleared once; afterwards each row clears only what it set
+  uint16_t* list = reinterpret_cast<uint16_t*>(base + G::kListOff);
+  // whole window cleared once; afterwards each row clears what it set
   for (int w = lane * 4; w < WORDS; w += 128)
     *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
   for (int w = lane; w < SUMS; w += 32) sum[w] = 0u;
@@ -194,27 +198,50 @@ k_sym_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo,
   const int per_cta = (nrows + gridDim.x - 1) / gridDim.x;
   const int r_begin = blockIdx.x * per_cta;
   const int r_end = min(nrows, r_begin + per_cta);
+  int kept = 0;
   for (int r = r_begin + warp; r < r_end; r += kWinWarps) {
     const int i = rows[r];
-    const int lo = row_lo[i];
-    window_set_bits<W>(bits, sum, ainfo2, lo, A.rowptr[i], A.rowptr[i + 1], A.colind, B.rowptr,
-                       B.colind, lane, status);
+    const int lo_w = row_lo[i] >> 5;
+    bc_set_bits<WORDS>(bits, sum, lo_w, A.rowptr[i], A.rowptr[i + 1], A.colind, B.rowptr, bcomp.bc,
+                       bcomp.len, lane, status);
+    const int L = window_list<SUMS>(sum, list, kCacheWords, lane);
     int c = 0;
-    for (int sw = lane; sw < SUMS; sw += 32) {
-      uint32_t m = sum[sw];
-      sum[sw] = 0u;
-      while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        const int w = sw * 32 + b;
-        c += __popc(bits[w]);
+    if (L <= kCacheWords) {
+      for (int e = lane; e < L; e += 32) {
+        const int w = list[e];
+        const uint32_t m = bits[w];
         bits[w] = 0u;
+        c += __popc(m);
+        if (cache.w) {
+          cache.w[(size_t)i * kCacheWords + e] = (uint16_t)w;
+          cache.m[(size_t)i * kCacheWords + e] = m;
+        }
       }
+    } else {
+      c = window_count_clear<WORDS>(bits, lane);
     }
-    c = team_sum<32>(c, 0xffffffffu);
-    if (lane == 0) cnt[i] = c;
+    c = team_sum<32>(c, kFull);
+    if (lane == 0) {
+      cnt[i] = c;
+      if (cache.n) cache.n[i] = L <= kCacheWords ? L : -1;
+    }
+    kept += (cache.n && L <= kCacheWords) ? 1 : 0;
     __syncwarp();
   }
+  if (lane == 0 && kept) atomicAdd(cache.kept, (unsigned long long)kept);
+}
+
+// Rank of column o (relative to the window) from the bits and prefixes, or
+// the spare slot kWindowMaxNnz when o is not a column of the row.
+template <int WORDS>
+__device__ __forceinline__ int window_rank(const uint32_t* bits, const uint16_t* pre, uint32_t o,
+                                           bool ok, int& missing) {
+  const uint32_t w = min(o >> 5, (uint32_t)(WORDS - 1));
+  const uint32_t word = bits[w];
+  const bool member = ok && o < (uint32_t)(WORDS * 32) && ((word >> (o & 31)) & 1u);
+  if (ok && !member) missing = 1;
+  const int r = (int)pre[w] + __popc(word & ((1u << (o & 31)) - 1u));
+  return member ? min(r, kWindowMaxNnz) : kWindowMaxNnz;
 }
 
 // SPEC = true: speculative one-pass of the learned form.  c_rowptr then holds
@@ -223,7 +250,8 @@ k_sym_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo,
 // (cnt_out[i] = -1, re-run by the plain path), otherwise cnt_out[i] = nnz.
 template <int W, bool SPEC>
 __global__ void __launch_bounds__(kWinWarps * 32, 4)
-k_num_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo, const float2* __restrict__ bspl,
+k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
+             const int32_t* __restrict__ row_lo, const float2* __restrict__ bspl,
              const int32_t* __restrict__ b_range_bad, int32_t arith,
              const int64_t* __restrict__ c_rowptr, const int32_t* __restrict__ rows, int32_t nrows,
              int32_t* __restrict__ c_colind, double* __restrict__ c_vals, int* status,
@@ -240,7 +268,6 @@ k_num_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo, const flo
   uint16_t* list = reinterpret_cast<uint16_t*>(base + G::kListOff);
   u64* vacc = reinterpret_cast<u64*>(base + G::kValOff);
   int4* ainfo = reinterpret_cast<int4*>(base + G::kInfoOff);
-  int2* ainfo2 = reinterpret_cast<int2*>(base + G::kInfoOff);
   const bool df_all = arith == kArithDF32 && *b_range_bad == 0;
   const int32_t* __restrict__ acol = A.colind;
   const double* __restrict__ aval = A.vals;
@@ -256,229 +283,166 @@ k_num_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo, const flo
   const int r_end = min(nrows, r_begin + per_cta);
   for (int r = r_begin + warp; r < r_end; r += kWinWarps) {
     const int i = rows[r];
-    const int lo = row_lo[i];
+    const int lo_w = row_lo[i] >> 5;
+    const int lo_c = lo_w * 32;
     const int64_t off = c_rowptr[i];
     const int cnt = SPEC ? min(cap[i], kWindowMaxNnz) : (int)(c_rowptr[i + 1] - off);
     const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
+    const int Lc = (!SPEC && cache.n) ? cache.n[i] : -1;
     for (int e = lane; e < kWindowMaxNnz; e += 32) vacc[e] = 0ull;
-    // Compact rows (at most 32 A entries, every B row at most 32 long): each
-    // lane keeps the columns of its products in registers for both passes.
-    int4 cinfo = make_int4(0, 0, 0, 0);
-    if (pa + lane < pe) {
-      const int j = acol[pa + lane];
-      cinfo.x = brp[j];
-      cinfo.y = brp[j + 1] - cinfo.x;
-    }
-    const bool compact =
-        (pe - pa <= 32) && __reduce_max_sync(0xffffffffu, (unsigned)cinfo.y) <= 32u;
-    int pcol[32];
-    if (compact) {
-      ainfo2[lane] = make_int2(cinfo.x, cinfo.y);
-      __syncwarp();
-      const int nch = pe - pa;
-      int bad = 0;
-#pragma unroll
-      for (int t0 = 0; t0 < 32; t0 += kWinBatch) {
-        if (t0 < nch) {
-#pragma unroll
-          for (int u = 0; u < kWinBatch; ++u) {
-            pcol[t0 + u] = -1;
-            if (t0 + u < nch) {
-              const int2 in = ainfo2[t0 + u];
-              if (lane < in.y) pcol[t0 + u] = bcol[in.x + lane];
-            }
+    int L, run = 0, bad = 0;
+    if (Lc >= 0 && Lc <= kCacheWords) {
+      // structure kept by the symbolic phase: words, bits, prefixes, columns
+      L = Lc;
+      for (int e0 = 0; e0 < L; e0 += 32) {
+        const int e = e0 + lane;
+        int w = 0;
+        uint32_t m = 0u;
+        if (e < L) {
+          w = cache.w[(size_t)i * kCacheWords + e];
+          m = cache.m[(size_t)i * kCacheWords + e];
+          if (w >= WORDS) {
+            bad = 1;
+            m = 0u;
+            w = 0;
           }
-#pragma unroll
-          for (int u = 0; u < kWinBatch; ++u) {
-            if (pcol[t0 + u] >= 0) {
-              const uint32_t o = (uint32_t)(pcol[t0 + u] - lo);
-              if (o < (uint32_t)W) window_set(bits, sum, o);
-              else bad = 1;
-            }
+        }
+        const int c = __popc(m);
+        const int incl = team_inclusive_scan<32>(c, lane, kFull);
+        int pos = run + incl - c;
+        run += __shfl_sync(kFull, incl, 31);
+        if (e < L) {
+          list[e] = (uint16_t)w;
+          bits[w] = m;
+          pre[w] = (uint16_t)pos;
+          while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            if (pos < cnt) c_colind[off + pos] = lo_c + w * 32 + b;
+            ++pos;
           }
-        } else {
-#pragma unroll
-          for (int u = 0; u < kWinBatch; ++u) pcol[t0 + u] = -1;
         }
       }
-      if (bad) set_status(status, KK_ERR_CAPACITY);
-      __syncwarp();
     } else {
-      // pass 1: structure bits (and summary bits of the non-empty words)
-      window_set_bits<W>(bits, sum, ainfo2, lo, pa, pe, acol, brp, bcol, lane, status);
-    }
-    // ordered list of non-empty words (summary words in order, bits in order)
-    int nsum[(SUMS + 31) / 32];
-    int mine = 0;
-#pragma unroll
-    for (int k = 0; k < (SUMS + 31) / 32; ++k) {
-      const int sw = k * 32 + lane;
-      nsum[k] = sw < SUMS ? __popc(sum[sw]) : 0;
-      mine += nsum[k];
-    }
-    // lane-major order is not word order when SUMS > 32: scan per round
-    int carry = 0;
-#pragma unroll
-    for (int k = 0; k < (SUMS + 31) / 32; ++k) {
-      const int sw = k * 32 + lane;
-      const int incl = team_inclusive_scan<32>(nsum[k], lane, 0xffffffffu);
-      int pos = carry + incl - nsum[k];
-      carry += __shfl_sync(0xffffffffu, incl, 31);
-      if (sw < SUMS) {
-        uint32_t m = sum[sw];
-        sum[sw] = 0u;
-        while (m) {
-          const int b = __ffs(m) - 1;
-          m &= m - 1;
-          if (pos < kWindowMaxNnz) list[pos] = (uint16_t)(sw * 32 + b);
-          ++pos;
+      // rebuild: bits from B_C, ordered word list, prefixes and columns
+      bc_set_bits<WORDS>(bits, sum, lo_w, pa, pe, acol, brp, bcomp.bc, bcomp.len, lane, status);
+      L = window_list<SUMS>(sum, list, kWindowMaxNnz, lane);
+      if (L > kWindowMaxNnz) {  // more words than a window row has columns
+        for (int w = lane * 4; w < WORDS; w += 128)
+          *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
+        if (lane == 0) {
+          if (SPEC) cnt_out[i] = -1;
+          else set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+        }
+        __syncwarp();
+        continue;
+      }
+      for (int e0 = 0; e0 < L; e0 += 32) {
+        const int e = e0 + lane;
+        const int w = e < L ? (int)list[e] : 0;
+        uint32_t m = e < L ? bits[w] : 0u;
+        const int c = __popc(m);
+        const int incl = team_inclusive_scan<32>(c, lane, kFull);
+        int pos = run + incl - c;
+        run += __shfl_sync(kFull, incl, 31);
+        if (e < L) {
+          pre[w] = (uint16_t)pos;
+          while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            if (pos < cnt) c_colind[off + pos] = lo_c + w * 32 + b;
+            ++pos;
+          }
         }
       }
     }
-    (void)mine;
-    const int L = min(carry, kWindowMaxNnz);
-    __syncwarp();
-    // prefix counts of the listed words, column indices written from the bits
-    int run = 0;
-    for (int e0 = 0; e0 < L; e0 += 32) {
-      const int e = e0 + lane;
-      const int w = e < L ? (int)list[e] : 0;
-      const uint32_t word = e < L ? bits[w] : 0u;
-      const int c = __popc(word);
-      const int incl = team_inclusive_scan<32>(c, lane, 0xffffffffu);
-      int pos = run + incl - c;
-      run += __shfl_sync(0xffffffffu, incl, 31);
-      if (e < L) {
-        pre[w] = (uint16_t)pos;
-        uint32_t m = word;
-        while (m) {
-          const int b = __ffs(m) - 1;
-          m &= m - 1;
-          if (pos < cnt) c_colind[off + pos] = lo + w * 32 + b;
-          ++pos;
-        }
-      }
-    }
+    if (bad) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
     if (!SPEC && run != cnt && lane == 0) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
     if (SPEC) {
       if (run > cnt) {  // overflow: abandon the row, clear what it set
         if (lane == 0) cnt_out[i] = -1;
-        if (carry > kWindowMaxNnz) {
-          for (int w = lane * 4; w < WORDS; w += 128)
-            *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
-        } else {
-          for (int e = lane; e < L; e += 32) bits[list[e]] = 0u;
-        }
+        for (int e = lane; e < L; e += 32) bits[list[e]] = 0u;
         __syncwarp();
         continue;
       }
       if (lane == 0) cnt_out[i] = run;
     }
     __syncwarp();
-    // arithmetic of this row: DF32 unless a value of the row is outside its window
+    // arithmetic of this row: DF32 unless a value of the row is outside its
+    // window (rows of up to 32 entries decide from the split below)
     bool df = df_all;
-    if (df_all) {
-      int bad = 0;
-      for (int p = pa + lane; p < pe; p += 32) {
-        DF t;
-        bad |= df_split(aval[p], t) ? 0 : 1;
-      }
-      df = __any_sync(0xffffffffu, bad) == 0;
-    }
-    // pass 2: values; rank = prefix + popc(bits below the column)
-    if (compact) {
-      int4 info = make_int4(cinfo.x, cinfo.y, 0, 0);
-      if (pa + lane < pe) {
-        const double a = aval[pa + lane];
-        if (df) {
-          DF ad;
-          df_split(a, ad);
-          info.z = __float_as_int(ad.hi);
-          info.w = __float_as_int(ad.lo);
-        } else {
-          const long long ab = __double_as_longlong(a);
-          info.z = (int)(ab & 0xffffffffll);
-          info.w = (int)(ab >> 32);
-        }
-      }
-      ainfo[lane] = info;
-      __syncwarp();
-      const int nch = pe - pa;
-      if (df) compact_values<W, true>(pcol, ainfo, nch, lo, bits, pre, vacc, bspl, bval, lane);
-      else compact_values<W, false>(pcol, ainfo, nch, lo, bits, pre, vacc, bspl, bval, lane);
-    }
-    for (int p0 = pa; p0 < (compact ? pa : pe); p0 += 32) {
+    if (df_all && pe - pa > 32) df = row_df_ok<32>(aval, pa, pe, lane, kFull);
+    int missing = 0;
+    for (int p0 = pa; p0 < pe; p0 += 32) {
       const int p = p0 + lane;
       int4 info = make_int4(0, 0, 0, 0);
+      double a = 0.0;
       if (p < pe) {
         const int j = acol[p];
         info.x = brp[j];
         info.y = brp[j + 1] - info.x;
-        const double a = aval[p];
-        if (df) {
-          DF ad;
-          df_split(a, ad);
-          info.z = __float_as_int(ad.hi);
-          info.w = __float_as_int(ad.lo);
-        } else {
-          const long long ab = __double_as_longlong(a);
-          info.z = (int)(ab & 0xffffffffll);
-          info.w = (int)(ab >> 32);
-        }
+        a = aval[p];
+      }
+      DF ad;
+      const int split_bad = df_all ? (df_split(a, ad) ? 0 : 1) : 1;
+      if (df_all && pe - pa <= 32) df = __any_sync(kFull, split_bad) == 0;
+      if (df) {
+        info.z = __float_as_int(ad.hi);
+        info.w = __float_as_int(ad.lo);
+      } else {
+        const long long ab = __double_as_longlong(a);
+        info.z = (int)(ab & 0xffffffffll);
+        info.w = (int)(ab >> 32);
       }
       ainfo[lane] = info;
       __syncwarp();
       const int nch = min(32, pe - p0);
-      const unsigned maxlen = __reduce_max_sync(0xffffffffu, (unsigned)info.y);
+      const unsigned maxlen = __reduce_max_sync(kFull, (unsigned)info.y);
       if (maxlen <= 32u) {
         for (int t0 = 0; t0 < nch; t0 += kWinBatch) {
-          int cols[kWinBatch];
           float2 bv[kWinBatch];
+          int rk[kWinBatch];
 #pragma unroll
           for (int u = 0; u < kWinBatch; ++u) {
-            cols[u] = -1;
+            int c = 0;
+            bool ok = false;
             bv[u] = make_float2(0.f, 0.f);
             if (t0 + u < nch) {
               const int2 in = *reinterpret_cast<const int2*>(&ainfo[t0 + u]);
               if (lane < in.y) {
                 const int q = in.x + lane;
-                cols[u] = bcol[q];
+                ok = true;
+                c = bcol[q];
                 if (df) {
                   bv[u] = bspl[q];
                 } else {
                   const long long bb = __double_as_longlong(bval[q]);
-                  bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)), __int_as_float((int)(bb >> 32)));
+                  bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)),
+                                      __int_as_float((int)(bb >> 32)));
                 }
               }
             }
+            rk[u] = window_rank<WORDS>(bits, pre, (uint32_t)(c - lo_c), ok, missing);
           }
 #pragma unroll
           for (int u = 0; u < kWinBatch; ++u) {
             if (t0 + u < nch) {
-              if (cols[u] >= 0) {
-                const uint32_t o = (uint32_t)(cols[u] - lo);
-                if (o < (uint32_t)W) {
-                  const int rank = (int)pre[o >> 5] + __popc(bits[o >> 5] & ((1u << (o & 31)) - 1u));
-                  if (rank < kWindowMaxNnz) {
-                    const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
-                    if (df) {
-                      DF a, b;
-                      a.hi = __int_as_float(az.x);
-                      a.lo = __int_as_float(az.y);
-                      b.hi = bv[u].x;
-                      b.lo = bv[u].y;
-                      DF s = df_unpack(vacc[rank]);
-                      df_fma(s, a, b);
-                      vacc[rank] = df_pack(s);
-                    } else {
-                      const double a = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
-                      const double b = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
-                                                            (unsigned)__float_as_int(bv[u].x));
-                      double* v = reinterpret_cast<double*>(&vacc[rank]);
-                      *v = fma(a, b, *v);
-                    }
-                  }
-                }
+              const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
+              if (df) {
+                DF av2, b2;
+                av2.hi = __int_as_float(az.x);
+                av2.lo = __int_as_float(az.y);
+                b2.hi = bv[u].x;
+                b2.lo = bv[u].y;
+                DF s = df_unpack(vacc[rk[u]]);
+                df_fma(s, av2, b2);
+                vacc[rk[u]] = df_pack(s);
+              } else {
+                const double x = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
+                const double y = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
+                                                      (unsigned)__float_as_int(bv[u].x));
+                double* v = reinterpret_cast<double*>(&vacc[rk[u]]);
+                *v = fma(x, y, *v);
               }
               __syncwarp();  // this A entry's updates are visible before the next one's
             }
@@ -487,42 +451,81 @@ k_num_window(CsrView A, CsrView B, const int32_t* __restrict__ row_lo, const flo
       } else {
         for (int t = 0; t < nch; ++t) {
           const int4 in = ainfo[t];
-          for (int q = lane; q < in.y; q += 32) {
-            const int qq = in.x + q;
-            const uint32_t o = (uint32_t)(bcol[qq] - lo);
-            if (o >= (uint32_t)W) continue;
-            const int rank = (int)pre[o >> 5] + __popc(bits[o >> 5] & ((1u << (o & 31)) - 1u));
-            if (rank >= kWindowMaxNnz) continue;
+          for (int q0 = 0; q0 < in.y; q0 += 32) {
+            const int q = in.x + q0 + lane;
+            const bool ok = q0 + lane < in.y;
+            const int c = ok ? bcol[q] : 0;
+            const int rank = window_rank<WORDS>(bits, pre, (uint32_t)(c - lo_c), ok, missing);
             if (df) {
-              DF a, b;
-              a.hi = __int_as_float(in.z);
-              a.lo = __int_as_float(in.w);
-              const float2 bb = bspl[qq];
-              b.hi = bb.x;
-              b.lo = bb.y;
+              DF av2, b2;
+              av2.hi = __int_as_float(in.z);
+              av2.lo = __int_as_float(in.w);
+              const float2 bb = ok ? bspl[q] : make_float2(0.f, 0.f);
+              b2.hi = bb.x;
+              b2.lo = bb.y;
               DF s = df_unpack(vacc[rank]);
-              df_fma(s, a, b);
+              df_fma(s, av2, b2);
               vacc[rank] = df_pack(s);
             } else {
-              const double a = __longlong_as_double(((long long)in.w << 32) | (unsigned)in.z);
+              const double x = __longlong_as_double(((long long)in.w << 32) | (unsigned)in.z);
               double* v = reinterpret_cast<double*>(&vacc[rank]);
-              *v = fma(a, bval[qq], *v);
+              *v = fma(x, ok ? bval[q] : 0.0, *v);
             }
+            __syncwarp();
           }
-          __syncwarp();  // this A entry's updates are visible before the next one's
         }
       }
       __syncwarp();
     }
+    if (missing) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
     const int n = min(SPEC ? run : cnt, kWindowMaxNnz);
     for (int e = lane; e < n; e += 32) {
       const u64 v = vacc[e];
       c_vals[off + e] = df ? df_to_double(df_unpack(v)) : __longlong_as_double((long long)v);
     }
-    // clear the words this row set (listed) for the next row
+    // clear the words this row set for the next row
     for (int e = lane; e < L; e += 32) bits[list[e]] = 0u;
     __syncwarp();
   }
+}
+
+// Compressed B: row j as (column >> 5, OR of 1 << (column & 31)) pairs in
+// column order at B's own row offsets, len[j] = number of pairs.  A word whose
+// columns straddle two 32-entry chunks of the row gives two pairs (harmless:
+// every use ORs them).  Rows must be sorted.
+__global__ void k_compress_b(CsrView B, int2* __restrict__ bc, int32_t* __restrict__ len,
+                             unsigned long long* pairs) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned long long tot = 0;
+  for (long long r = w0; r < B.m; r += nw) {
+    const int bs = B.rowptr[r], be = B.rowptr[r + 1];
+    int n = 0;
+    for (int q0 = bs; q0 < be; q0 += 32) {
+      const int q = q0 + lane;
+      const bool valid = q < be;
+      const int c = valid ? B.colind[q] : 0;
+      const int w = valid ? (c >> 5) : -1 - lane;  // invalid lanes match nothing
+      uint32_t acc = valid ? (1u << (c & 31)) : 0u;
+      const int wp = __shfl_up_sync(kFull, w, 1);
+      const bool head = valid && (lane == 0 || wp != w);
+      // segmented OR over the lanes of the same word (contiguous: sorted row)
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_down_sync(kFull, acc, d);
+        const int w2 = __shfl_down_sync(kFull, w, d);
+        if (lane + d < 32 && w2 == w) acc |= v;
+      }
+      const unsigned hm = __ballot_sync(kFull, head);
+      if (head) bc[bs + n + __popc(hm & lt)] = make_int2(w, (int)acc);
+      n += __popc(hm);
+    }
+    if (lane == 0) len[r] = n;
+    tot += (unsigned long long)n;
+  }
+  if (lane == 0 && tot) atomicAdd(pairs, tot);
 }
 
 template <class K>
@@ -539,90 +542,111 @@ int grid_for_rows(const LaunchCtx& ctx, int nrows) {
 }
 
 template <int W>
-cudaError_t sym_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
-                       const int32_t* rows, int32_t nrows, int32_t* cnt) {
+cudaError_t sym_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B, const BComp& bcomp,
+                       const int32_t* rows, int32_t nrows, int32_t* cnt, const WinCache& cache) {
   const size_t smem = (size_t)kWinWarps * SymWinGeom<W>::kWarpBytes;
   auto kern = k_sym_window<W>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid_for_rows(ctx, nrows), kWinWarps * 32, smem, ctx.stream>>>(A, B, ctx.row_lo, rows,
-                                                                        nrows, cnt, ctx.status);
+  kern<<<grid_for_rows(ctx, nrows), kWinWarps * 32, smem, ctx.stream>>>(
+      A, B, bcomp, ctx.row_lo, rows, nrows, cnt, cache, ctx.status);
   return cudaGetLastError();
 }
 
 template <int W, bool SPEC = false>
-cudaError_t num_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
-                       const float2* b_split, const int32_t* b_range_bad, int32_t arith,
-                       const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
-                       int32_t* c_colind, double* c_vals, const int32_t* cap = nullptr,
-                       int32_t* cnt_out = nullptr) {
+cudaError_t num_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B, const BComp& bcomp,
+                       const WinCacheView& cache, const float2* b_split,
+                       const int32_t* b_range_bad, int32_t arith, const int64_t* c_rowptr,
+                       const int32_t* rows, int32_t nrows, int32_t* c_colind, double* c_vals,
+                       const int32_t* cap = nullptr, int32_t* cnt_out = nullptr) {
   const size_t smem = (size_t)kWinWarps * NumWinGeom<W>::kWarpBytes;
   auto kern = k_num_window<W, SPEC>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid_for_rows(ctx, nrows), kWinWarps * 32, smem, ctx.stream>>>(
-      A, B, ctx.row_lo, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals,
-      ctx.status, cap, cnt_out);
+      A, B, bcomp, cache, ctx.row_lo, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind,
+      c_vals, ctx.status, cap, cnt_out);
   return cudaGetLastError();
 }
 
 }  // namespace
 
+cudaError_t launch_compress_b(const LaunchCtx& ctx, const CsrView& B, int2* bc, int32_t* len,
+                              unsigned long long* pairs) {
+  if (B.m <= 0) return cudaSuccess;
+  timer_begin(ctx.timer, ctx.stream, "compress_b");
+  long long blocks = ((long long)B.m * 32 + 255) / 256;
+  const long long cap = (long long)ctx.num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  k_compress_b<<<(int)blocks, 256, 0, ctx.stream>>>(B, bc, len, pairs);
+  timer_end(ctx.timer, ctx.stream);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_symbolic_window(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,
-                                   const CsrView& B, const int32_t* rows, int32_t nrows,
-                                   int32_t* cnt) {
+                                   const CsrView& B, const BComp& bcomp, const int32_t* rows,
+                                   int32_t nrows, int32_t* cnt, const WinCache& cache) {
   if (nrows <= 0) return cudaSuccess;
   timer_begin(ctx.timer, ctx.stream, "sym_window");
   cudaError_t e = cudaErrorInvalidValue;
   switch (bin.slots) {
-    case 4096: e = sym_window<4096>(ctx, A, B, rows, nrows, cnt); break;
-    case 12288: e = sym_window<12288>(ctx, A, B, rows, nrows, cnt); break;
-    case 24576: e = sym_window<24576>(ctx, A, B, rows, nrows, cnt); break;
-    case 40960: e = sym_window<40960>(ctx, A, B, rows, nrows, cnt); break;
-    case 65536: e = sym_window<65536>(ctx, A, B, rows, nrows, cnt); break;
+    case 4096: e = sym_window<4096>(ctx, A, B, bcomp, rows, nrows, cnt, cache); break;
+    case 12288: e = sym_window<12288>(ctx, A, B, bcomp, rows, nrows, cnt, cache); break;
+    case 24576: e = sym_window<24576>(ctx, A, B, bcomp, rows, nrows, cnt, cache); break;
+    case 40960: e = sym_window<40960>(ctx, A, B, bcomp, rows, nrows, cnt, cache); break;
+    case 65536: e = sym_window<65536>(ctx, A, B, bcomp, rows, nrows, cnt, cache); break;
   }
   timer_end(ctx.timer, ctx.stream);
   return e;
 }
 
 cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,
-                                  const CsrView& B, const float2* b_split,
-                                  const int32_t* b_range_bad, int32_t arith,
+                                  const CsrView& B, const BComp& bcomp, const WinCacheView& cache,
+                                  const float2* b_split, const int32_t* b_range_bad, int32_t arith,
                                   const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
                                   int32_t* c_colind, double* c_vals) {
   if (nrows <= 0) return cudaSuccess;
   timer_begin(ctx.timer, ctx.stream, "num_window");
   cudaError_t e = cudaErrorInvalidValue;
+#define KK_NUM_WIN(WB)                                                                          \
+  case WB:                                                                                      \
+    e = num_window<WB>(ctx, A, B, bcomp, cache, b_split, b_range_bad, arith, c_rowptr, rows,    \
+                       nrows, c_colind, c_vals);                                                \
+    break;
   switch (bin.slots) {
-    case 4096: e = num_window<4096>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
-    case 12288: e = num_window<12288>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
-    case 24576: e = num_window<24576>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
-    case 40960: e = num_window<40960>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
-    case 65536: e = num_window<65536>(ctx, A, B, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
+    KK_NUM_WIN(4096)
+    KK_NUM_WIN(12288)
+    KK_NUM_WIN(24576)
+    KK_NUM_WIN(40960)
+    KK_NUM_WIN(65536)
   }
+#undef KK_NUM_WIN
   timer_end(ctx.timer, ctx.stream);
   return e;
 }
 
-}  // namespace kk
-
-namespace kk {
-
 cudaError_t launch_onepass_window(const LaunchCtx& ctx, int32_t wclass, const CsrView& A,
-                                  const CsrView& B, const float2* b_split,
+                                  const CsrView& B, const BComp& bcomp, const float2* b_split,
                                   const int32_t* b_range_bad, int32_t arith, const int64_t* soff,
                                   const int32_t* cap, const int32_t* rows, int32_t nrows,
                                   int32_t* scol, double* sval, int32_t* cnt_out) {
   if (nrows <= 0) return cudaSuccess;
   timer_begin(ctx.timer, ctx.stream, "onepass_window");
   cudaError_t e = cudaErrorInvalidValue;
+  const WinCacheView none{nullptr, nullptr, nullptr};
+#define KK_ONE_WIN(WB)                                                                          \
+  case WB:                                                                                      \
+    e = num_window<WB, true>(ctx, A, B, bcomp, none, b_split, b_range_bad, arith, soff, rows,   \
+                             nrows, scol, sval, cap, cnt_out);                                  \
+    break;
   switch (kWindowBits[wclass]) {
-    case 4096: e = num_window<4096, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
-    case 12288: e = num_window<12288, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
-    case 24576: e = num_window<24576, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
-    case 40960: e = num_window<40960, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
-    case 65536: e = num_window<65536, true>(ctx, A, B, b_split, b_range_bad, arith, soff, rows, nrows, scol, sval, cap, cnt_out); break;
+    KK_ONE_WIN(4096)
+    KK_ONE_WIN(12288)
+    KK_ONE_WIN(24576)
+    KK_ONE_WIN(40960)
+    KK_ONE_WIN(65536)
   }
+#undef KK_ONE_WIN
   timer_end(ctx.timer, ctx.stream);
   return e;
 }

@@ -50,7 +50,8 @@ class KkOptions(ctypes.Structure):
                 ("sym_cta_max_flop", ctypes.c_int32), ("num_team_max_nnz", ctypes.c_int32),
                 ("num_cta_max_nnz", ctypes.c_int32), ("use_window", ctypes.c_int32),
                 ("batched_graph", ctypes.c_int32), ("sym_load_pct", ctypes.c_int32),
-                ("num_load_pct", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("num_load_pct", ctypes.c_int32), ("structure_cache", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -199,13 +200,14 @@ def kk_spgemm_kernel_times(h, reset: bool = False) -> dict:
 
 
 def kk_spgemm_stats(h) -> dict:
-    arr = (ctypes.c_int64 * 24)()
+    arr = (ctypes.c_int64 * 32)()
     _check(load_library().kk_spgemm_stats(h, arr), h)
     keys = ["sym_team_rows", "sym_cta_rows", "sym_dense_rows", "num_team_rows", "num_cta_rows",
             "num_dense_rows", "flops", "b_sorted", "launches_sym", "launches_num",
             "sym_window_rows", "num_window_rows", "onepass_rows", "overflow_rows", "heavy_rows",
             "staging_entries", "num_team_c", "num_cta_c", "num_dense_c", "num_window_c",
-            "num_team_a", "num_cta_a", "num_dense_a", "num_window_a"]
+            "num_team_a", "num_cta_a", "num_dense_a", "num_window_a", "kept_structure_rows",
+            "compressed_b_pairs"]
     return {k: int(arr[i]) for i, k in enumerate(keys)}
 
 

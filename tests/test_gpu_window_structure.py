@@ -1,0 +1,103 @@
+"""GPU: compressed B (the paper's B_C) in the window tier, and the structure the
+symbolic phase keeps for the numeric phase of the same A and B arrays.
+
+The kept structure must give bit-identical C to the rebuild from B_C; it must
+not be used for other index arrays; and a structure that changed behind the
+same arrays is reported (KK_ERR_STRUCTURE_MISMATCH) instead of silently used."""
+import numpy as np
+import pytest
+
+from paper_2103_11991_gb300 import inputs as I
+from tests._gpu import check_against_oracle, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _stencil_random(scale, seed):
+    d = I.config_inputs("stencil3d27_100", scale=scale)
+    A = d["A"].copy()
+    A.vals = I.uniform01(seed, "ws", A.nnz) * 2 - 1
+    return A
+
+
+@pytest.mark.parametrize("arith", [1, 2])
+def test_kept_structure_matches_rebuild(arith):
+    A = _stencil_random(18, 1)
+    S = I.stencil_2d(70, 50, 9, 8.0, -1.0)
+    S.vals = I.uniform01(2, "ws2", S.nnz) * 2 - 1
+    # uniform random rows: windows too full to keep (more than 64 words)
+    B2 = I.random_rows(3000, 3000, 20, 40, seed=4)
+    A2 = I.random_rows(700, 3000, 5, 30, seed=5)
+    for X, Y, keeps in ((A, A, True), (S, S, True), (A2, B2, False)):
+        kept = run_gpu(X, Y, arith=arith, force_tier=3, structure_cache=1)
+        rebuilt = run_gpu(X, Y, arith=arith, force_tier=3, structure_cache=0)
+        for a, b in zip(kept[:3], rebuilt[:3]):
+            assert np.array_equal(a, b)
+        check_against_oracle(X, Y, *kept[:3])
+        assert kept[4]["sym_window_rows"] > 0
+        assert (kept[4]["kept_structure_rows"] > 0) == keeps
+        assert rebuilt[4]["kept_structure_rows"] == 0
+        assert 0 < kept[4]["compressed_b_pairs"] <= Y.nnz
+
+
+def _distinct_words(B):
+    # rows of at most 32 entries: one pair per distinct (row, column >> 5)
+    assert np.diff(B.rowptr).max() <= 32
+    w = B.colind.astype(np.int64) >> 5
+    row = np.repeat(np.arange(B.m), np.diff(B.rowptr))
+    first = np.ones(B.nnz, bool)
+    first[1:] = (w[1:] != w[:-1]) | (row[1:] != row[:-1])
+    return int(first.sum())
+
+
+@pytest.mark.parametrize("scale", [20, 33])
+def test_compressed_b_pairs_of_stencil(scale):
+    A = I.config_inputs("stencil3d27_100", scale=scale)["A"]
+    _, _, _, _, st = run_gpu(A, A)
+    assert st["sym_window_rows"] == A.m
+    assert st["compressed_b_pairs"] == _distinct_words(A)
+
+
+def test_kept_structure_only_for_its_arrays():
+    import torch
+    from paper_2103_11991_gb300 import spgemm as K
+    A = _stencil_random(12, 2)
+    dA, dB = K.DeviceCSR.from_host(A), K.DeviceCSR.from_host(A)
+    with K.SpGEMM() as op:
+        rp, nnz = op.symbolic(dA, dB)
+        assert op.stats()["kept_structure_rows"] == A.m
+        c1, v1 = op.numeric(dA, dB, rp, nnz)
+        # same structure and values in other arrays: the structure is rebuilt
+        dA2 = K.DeviceCSR(A.m, A.n, dA.rowptr.clone(), dA.colind.clone(), dA.vals.clone())
+        c2, v2 = op.numeric(dA2, dB, rp, nnz)
+        op.sync()
+        assert torch.equal(c1, c2) and torch.equal(v1, v2)
+        check_against_oracle(A, A, rp.cpu().numpy(), c1.cpu().numpy(), v1.cpu().numpy())
+
+
+@pytest.mark.parametrize("cache", [0, 1])
+def test_changed_structure_behind_same_arrays_is_reported(cache):
+    import torch
+    from paper_2103_11991_gb300 import spgemm as K
+    A = I.config_inputs("stencil3d27_100", scale=10)["A"]
+    dA, dB = K.DeviceCSR.from_host(A), K.DeviceCSR.from_host(A)
+    with K.SpGEMM(structure_cache=cache) as op:
+        rp, nnz = op.symbolic(dA, dB)
+        st = op.stats()
+        assert st["sym_window_rows"] == A.m and st["num_window_rows"] == A.m
+        # B's rows swapped in pairs (same nnz, rows still sorted and in range),
+        # written into the arrays the symbolic phase saw
+        perm = np.arange(A.m)
+        perm[0:A.m - 1:2] += 1
+        perm[1:A.m:2] -= 1
+        Bp = I.permute(A, perm, None)
+        assert Bp.nnz == A.nnz
+        # every read of the (stale) compressed rows stays inside its array
+        assert np.all(Bp.rowptr[:-1].astype(np.int64) + np.diff(A.rowptr) <= A.nnz)
+        dB.rowptr.copy_(torch.from_numpy(Bp.rowptr).cuda())
+        dB.colind.copy_(torch.from_numpy(Bp.colind).cuda())
+        dB.vals.copy_(torch.from_numpy(Bp.vals).cuda())
+        with pytest.raises(K.KKError) as e:
+            op.numeric(dA, dB, rp, nnz)
+            op.sync()
+        assert e.value.status == 4
