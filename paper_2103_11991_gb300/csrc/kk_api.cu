@@ -599,6 +599,7 @@ struct kk_spgemm_handle_s {
   DevBuf d_cw;         // uint16[m * kCacheWords]
   DevBuf d_cm;         // uint32[m * kCacheWords]
   DevBuf d_cn;         // int32[m]
+  DevBuf d_left;       // int32[1 + m]: count, then rows left to the window kernel
   bool cache_valid = false;
   const void* cache_key[4] = {nullptr, nullptr, nullptr, nullptr};
 };
@@ -785,12 +786,19 @@ kk_status cache_for_symbolic(kk_spgemm_handle h, int32_t m, bool any_window, con
   return KK_OK;
 }
 
-// The kept structure, if it belongs to these index arrays.
-WinCacheView cache_view(kk_spgemm_handle h, const CsrView& av, const CsrView& bv) {
+// The kept structure, if it belongs to these index arrays, and the scratch
+// its numeric launches need.
+kk_status cache_view(kk_spgemm_handle h, const CsrView& av, const CsrView& bv, WinCacheView* view,
+                     WinScratch* scratch) {
+  *view = WinCacheView{nullptr, nullptr, nullptr};
+  *scratch = WinScratch{nullptr, nullptr};
   if (!h->cache_valid || h->cache_key[0] != av.rowptr || h->cache_key[1] != av.colind ||
       h->cache_key[2] != bv.rowptr || h->cache_key[3] != bv.colind)
-    return WinCacheView{nullptr, nullptr, nullptr};
-  return WinCacheView{h->d_cw.as<uint16_t>(), h->d_cm.as<uint32_t>(), h->d_cn.as<int32_t>()};
+    return KK_OK;
+  KK_CUDA(h, h->d_left.ensure(sizeof(int32_t) * ((size_t)av.m + 1)), "alloc window scratch");
+  *view = WinCacheView{h->d_cw.as<uint16_t>(), h->d_cm.as<uint32_t>(), h->d_cn.as<int32_t>()};
+  *scratch = WinScratch{h->d_left.as<int32_t>() + 1, h->d_left.as<int32_t>()};
+  return KK_OK;
 }
 
 int grid_for(long long work, int per_block, int cap) {
@@ -1105,14 +1113,16 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
     if ((st = ensure_bcomp(h, bv, false, &bcomp, &built)) != KK_OK) return st;
     h->stats[9] += built;
   }
-  const WinCacheView wview = cache_view(h, av, bv);
+  WinCacheView wview;
+  WinScratch wscratch;
+  if ((st = cache_view(h, av, bv, &wview, &wscratch)) != KK_OK) return st;
   for (int b = 0; b < nbn; ++b) {
     const int cnt = h->num_start[b + 1] - h->num_start[b];
     if (cnt <= 0) continue;
     h->stats[9] += 1;
     const int32_t* rows = h->d_nrows.as<int32_t>() + h->num_start[b];
     cudaError_t e = h->num_bins[b].tier == kTierWindow
-                        ? launch_numeric_window(ctx, h->num_bins[b], av, bv, bcomp, wview, bsplit,
+                        ? launch_numeric_window(ctx, h->num_bins[b], av, bv, bcomp, wview, wscratch, bsplit,
                                                 &dm->range_bad, arith, c_rowptr, rows, cnt, c_colind,
                                                 c_vals)
                         : launch_numeric_bin(ctx, h->num_bins[b], av, bv, h->b_sorted, bsplit,
@@ -1392,13 +1402,15 @@ kk_status kk_spgemm_learned_numeric(kk_spgemm_handle h, const kk_csr* A, const k
     int built = 0;
     if ((st = ensure_bcomp(h, bv, false, &bcomp, &built)) != KK_OK) return st;
   }
-  const WinCacheView wview = cache_view(h, av, bv);
+  WinCacheView wview;
+  WinScratch wscratch;
+  if ((st = cache_view(h, av, bv, &wview, &wscratch)) != KK_OK) return st;
   for (int b = 0; b < nbn; ++b) {
     const int cnt = h->lnum_start[b + 1] - h->lnum_start[b];
     if (cnt <= 0) continue;
     const int32_t* rows = h->d_lrows2.as<int32_t>() + h->lnum_start[b];
     e = h->num_bins[b].tier == kTierWindow
-            ? launch_numeric_window(ctx, h->num_bins[b], av, bv, bcomp, wview, bsplit, &dm->range_bad,
+            ? launch_numeric_window(ctx, h->num_bins[b], av, bv, bcomp, wview, wscratch, bsplit, &dm->range_bad,
                                     arith, c_rowptr, rows, cnt, c_colind, c_vals)
             : launch_numeric_bin(ctx, h->num_bins[b], av, bv, h->b_sorted, bsplit, &dm->range_bad, arith,
                                  c_rowptr, rows, cnt, c_colind, c_vals, h->opt.debug_checks);
@@ -1704,7 +1716,7 @@ kk_status kk_spgemm_destroy(kk_spgemm_handle h) {
                     &h->d_sval, &h->d_sball, &h->d_nbin2, &h->d_lrows, &h->d_lrows2, &h->d_mm,
                     &h->d_bdesc, &h->d_rowpair, &h->d_bflop, &h->d_bsbin, &h->d_bnbin, &h->d_bsrows,
                     &h->d_bnrows, &h->d_bcnt, &h->d_btiles, &h->d_bstart, &h->d_bqueue, &h->d_bsplit2,
-                    &h->d_boff, &h->d_bc, &h->d_bclen, &h->d_cw, &h->d_cm, &h->d_cn})
+                    &h->d_boff, &h->d_bc, &h->d_bclen, &h->d_cw, &h->d_cm, &h->d_cn, &h->d_left})
     b->release();
   for (void* p : {h->h_bdesc, h->h_bdesc2, h->h_boff})
     if (p) cudaFreeHost(p);

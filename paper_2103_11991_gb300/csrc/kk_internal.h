@@ -66,6 +66,12 @@ struct WinCacheView {
   const uint32_t* m;
   const int32_t* n;
 };
+// Scratch of the numeric window launch: rows left to the window kernel by the
+// kept-structure kernel (count first, then the rows).
+struct WinScratch {
+  int32_t* rows;
+  int32_t* count;
+};
 cudaError_t launch_compress_b(const LaunchCtx& ctx, const CsrView& B, int2* bc, int32_t* len,
                               unsigned long long* pairs);
 
@@ -100,7 +106,8 @@ cudaError_t launch_symbolic_window(const LaunchCtx& ctx, const BinSpec& bin, con
                                    int32_t nrows, int32_t* cnt, const WinCache& cache);
 cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,
                                   const CsrView& B, const BComp& bcomp, const WinCacheView& cache,
-                                  const float2* b_split, const int32_t* b_range_bad, int32_t arith,
+                                  const WinScratch& scratch, const float2* b_split,
+                                  const int32_t* b_range_bad, int32_t arith,
                                   const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
                                   int32_t* c_colind, double* c_vals);
 

@@ -255,7 +255,8 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
              const int32_t* __restrict__ b_range_bad, int32_t arith,
              const int64_t* __restrict__ c_rowptr, const int32_t* __restrict__ rows, int32_t nrows,
              int32_t* __restrict__ c_colind, double* __restrict__ c_vals, int* status,
-             const int32_t* __restrict__ cap, int32_t* __restrict__ cnt_out) {
+             const int32_t* __restrict__ cap, int32_t* __restrict__ cnt_out,
+             const int32_t* __restrict__ nrows_dev) {
   using G = NumWinGeom<W>;
   constexpr int WORDS = G::WORDS;
   constexpr int SUMS = G::SUMS;
@@ -274,13 +275,15 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
   const int32_t* __restrict__ brp = B.rowptr;
   const int32_t* __restrict__ bcol = B.colind;
   const double* __restrict__ bval = B.vals;
+  if (nrows_dev) nrows = *nrows_dev;
+  const int per_cta = (nrows + gridDim.x - 1) / gridDim.x;
+  const int r_begin = blockIdx.x * per_cta;
+  const int r_end = min(nrows, r_begin + per_cta);
+  if (r_begin + warp >= r_end) return;  // warps share no shared memory or barrier
   for (int w = lane * 4; w < WORDS; w += 128)
     *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
   for (int w = lane; w < SUMS; w += 32) sum[w] = 0u;
   __syncwarp();
-  const int per_cta = (nrows + gridDim.x - 1) / gridDim.x;
-  const int r_begin = blockIdx.x * per_cta;
-  const int r_end = min(nrows, r_begin + per_cta);
   for (int r = r_begin + warp; r < r_end; r += kWinWarps) {
     const int i = rows[r];
     const int lo_w = row_lo[i] >> 5;
@@ -489,6 +492,224 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
   }
 }
 
+// Numeric phase of the rows whose structure the symbolic phase kept: the
+// row's words go into a small open-addressing table (slot = word mod 128,
+// linear probing; at most kCacheWords words in 128 slots) instead of a
+// W-bit window, so a warp needs about 3.6 KB of shared memory whatever the
+// row's span and more rows are in flight per SM.  An entry packs the word's
+// bits (low 32), its prefix count (bits 32..47) and the word index (48..63).
+// Rows without kept structure are appended to `left` for k_num_window.
+constexpr int kKeptWarps = 8;
+constexpr int kKeptSlots = 128;
+constexpr u64 kKeptEmpty = ~0ull;
+struct KeptGeom {
+  // table u64[kKeptSlots] | vacc u64[kWindowMaxNnz + 2] | ainfo int4[32]
+  static constexpr size_t kValOff = (size_t)kKeptSlots * 8;
+  static constexpr size_t kInfoOff = al16(kValOff + (size_t)(kWindowMaxNnz + 2) * 8);
+  static constexpr size_t kWarpBytes = kInfoOff + 32 * 16;
+};
+
+// Rank of column o (relative to the row's first word) through the table, or
+// the spare slot when o is not a column of the row.
+__device__ __forceinline__ int kept_rank(const u64* table, uint32_t o, bool ok, int& missing) {
+  const uint32_t w = o >> 5;
+  uint32_t s = w & (kKeptSlots - 1);
+  u64 e = table[s];
+  for (int k = 0; k < kKeptSlots && e != kKeptEmpty && (uint32_t)(e >> 48) != w; ++k) {
+    s = (s + 1) & (kKeptSlots - 1);
+    e = table[s];
+  }
+  const bool hit = e != kKeptEmpty && (uint32_t)(e >> 48) == w;
+  const uint32_t word = hit ? (uint32_t)e : 0u;
+  const bool member = ok && hit && ((word >> (o & 31)) & 1u);
+  if (ok && !member) missing = 1;
+  const int r = (int)((e >> 32) & 0xFFFFu) + __popc(word & ((1u << (o & 31)) - 1u));
+  return member ? min(r, kWindowMaxNnz) : kWindowMaxNnz;
+}
+
+__global__ void __launch_bounds__(kKeptWarps * 32, 4)
+k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__ row_lo,
+           const float2* __restrict__ bspl, const int32_t* __restrict__ b_range_bad, int32_t arith,
+           const int64_t* __restrict__ c_rowptr, const int32_t* __restrict__ rows, int32_t nrows,
+           int32_t* __restrict__ c_colind, double* __restrict__ c_vals, int* status,
+           int32_t* __restrict__ left_rows, int32_t* __restrict__ left_count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = smem_raw + (size_t)warp * KeptGeom::kWarpBytes;
+  u64* table = reinterpret_cast<u64*>(base);
+  u64* vacc = reinterpret_cast<u64*>(base + KeptGeom::kValOff);
+  int4* ainfo = reinterpret_cast<int4*>(base + KeptGeom::kInfoOff);
+  const bool df_all = arith == kArithDF32 && *b_range_bad == 0;
+  const int32_t* __restrict__ acol = A.colind;
+  const double* __restrict__ aval = A.vals;
+  const int32_t* __restrict__ brp = B.rowptr;
+  const int32_t* __restrict__ bcol = B.colind;
+  const double* __restrict__ bval = B.vals;
+  const int per_cta = (nrows + gridDim.x - 1) / gridDim.x;
+  const int r_begin = blockIdx.x * per_cta;
+  const int r_end = min(nrows, r_begin + per_cta);
+  for (int r = r_begin + warp; r < r_end; r += kKeptWarps) {
+    const int i = rows[r];
+    const int L = cache.n[i];
+    if (L < 0 || L > kCacheWords) {
+      if (lane == 0) left_rows[atomicAdd(left_count, 1)] = i;
+      continue;
+    }
+    const int lo_c = (row_lo[i] >> 5) * 32;
+    const int64_t off = c_rowptr[i];
+    const int cnt = (int)(c_rowptr[i + 1] - off);
+    const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
+    for (int s = lane; s < kKeptSlots; s += 32) table[s] = kKeptEmpty;
+    for (int e = lane; e < kWindowMaxNnz; e += 32) vacc[e] = 0ull;
+    __syncwarp();
+    int run = 0, bad = 0;
+    for (int e0 = 0; e0 < L; e0 += 32) {
+      const int e = e0 + lane;
+      uint32_t w = 0u, m = 0u;
+      if (e < L) {
+        w = cache.w[(size_t)i * kCacheWords + e];
+        m = cache.m[(size_t)i * kCacheWords + e];
+      }
+      const int c = __popc(m);
+      const int incl = team_inclusive_scan<32>(c, lane, kFull);
+      int pos = run + incl - c;
+      run += __shfl_sync(kFull, incl, 31);
+      if (e < L) {
+        const u64 entry = (u64)m | ((u64)(uint32_t)pos << 32) | ((u64)w << 48);
+        uint32_t s = w & (kKeptSlots - 1);
+        bool placed = false;
+        for (int k = 0; k < kKeptSlots && !placed; ++k) {
+          placed = atomicCAS(&table[s], kKeptEmpty, entry) == kKeptEmpty;
+          s = (s + 1) & (kKeptSlots - 1);
+        }
+        if (!placed) bad = 1;
+        while (m) {
+          const int b = __ffs(m) - 1;
+          m &= m - 1;
+          if (pos < cnt) c_colind[off + pos] = lo_c + (int)w * 32 + b;
+          ++pos;
+        }
+      }
+    }
+    if (bad || (run != cnt && lane == 0)) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    __syncwarp();
+    bool df = df_all;
+    if (df_all && pe - pa > 32) df = row_df_ok<32>(aval, pa, pe, lane, kFull);
+    int missing = 0;
+    for (int p0 = pa; p0 < pe; p0 += 32) {
+      const int p = p0 + lane;
+      int4 info = make_int4(0, 0, 0, 0);
+      double a = 0.0;
+      if (p < pe) {
+        const int j = acol[p];
+        info.x = brp[j];
+        info.y = brp[j + 1] - info.x;
+        a = aval[p];
+      }
+      DF ad;
+      const int split_bad = df_all ? (df_split(a, ad) ? 0 : 1) : 1;
+      if (df_all && pe - pa <= 32) df = __any_sync(kFull, split_bad) == 0;
+      if (df) {
+        info.z = __float_as_int(ad.hi);
+        info.w = __float_as_int(ad.lo);
+      } else {
+        const long long ab = __double_as_longlong(a);
+        info.z = (int)(ab & 0xffffffffll);
+        info.w = (int)(ab >> 32);
+      }
+      ainfo[lane] = info;
+      __syncwarp();
+      const int nch = min(32, pe - p0);
+      const unsigned maxlen = __reduce_max_sync(kFull, (unsigned)info.y);
+      if (maxlen <= 32u) {
+        for (int t0 = 0; t0 < nch; t0 += kWinBatch) {
+          float2 bv[kWinBatch];
+          int rk[kWinBatch];
+#pragma unroll
+          for (int u = 0; u < kWinBatch; ++u) {
+            int c = 0;
+            bool ok = false;
+            bv[u] = make_float2(0.f, 0.f);
+            if (t0 + u < nch) {
+              const int2 in = *reinterpret_cast<const int2*>(&ainfo[t0 + u]);
+              if (lane < in.y) {
+                const int q = in.x + lane;
+                ok = true;
+                c = bcol[q];
+                if (df) {
+                  bv[u] = bspl[q];
+                } else {
+                  const long long bb = __double_as_longlong(bval[q]);
+                  bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)),
+                                      __int_as_float((int)(bb >> 32)));
+                }
+              }
+            }
+            rk[u] = kept_rank(table, (uint32_t)(c - lo_c), ok, missing);
+          }
+#pragma unroll
+          for (int u = 0; u < kWinBatch; ++u) {
+            if (t0 + u < nch) {
+              const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
+              if (df) {
+                DF av2, b2;
+                av2.hi = __int_as_float(az.x);
+                av2.lo = __int_as_float(az.y);
+                b2.hi = bv[u].x;
+                b2.lo = bv[u].y;
+                DF s = df_unpack(vacc[rk[u]]);
+                df_fma(s, av2, b2);
+                vacc[rk[u]] = df_pack(s);
+              } else {
+                const double x = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
+                const double y = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
+                                                      (unsigned)__float_as_int(bv[u].x));
+                double* v = reinterpret_cast<double*>(&vacc[rk[u]]);
+                *v = fma(x, y, *v);
+              }
+              __syncwarp();  // this A entry's updates are visible before the next one's
+            }
+          }
+        }
+      } else {
+        for (int t = 0; t < nch; ++t) {
+          const int4 in = ainfo[t];
+          for (int q0 = 0; q0 < in.y; q0 += 32) {
+            const int q = in.x + q0 + lane;
+            const bool ok = q0 + lane < in.y;
+            const int c = ok ? bcol[q] : 0;
+            const int rank = kept_rank(table, (uint32_t)(c - lo_c), ok, missing);
+            if (df) {
+              DF av2, b2;
+              av2.hi = __int_as_float(in.z);
+              av2.lo = __int_as_float(in.w);
+              const float2 bb = ok ? bspl[q] : make_float2(0.f, 0.f);
+              b2.hi = bb.x;
+              b2.lo = bb.y;
+              DF s = df_unpack(vacc[rank]);
+              df_fma(s, av2, b2);
+              vacc[rank] = df_pack(s);
+            } else {
+              const double x = __longlong_as_double(((long long)in.w << 32) | (unsigned)in.z);
+              double* v = reinterpret_cast<double*>(&vacc[rank]);
+              *v = fma(x, ok ? bval[q] : 0.0, *v);
+            }
+            __syncwarp();
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (missing) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    const int n = min(cnt, kWindowMaxNnz);
+    for (int e = lane; e < n; e += 32) {
+      const u64 v = vacc[e];
+      c_vals[off + e] = df ? df_to_double(df_unpack(v)) : __longlong_as_double((long long)v);
+    }
+    __syncwarp();
+  }
+}
+
 // Compressed B: row j as (column >> 5, OR of 1 << (column & 31)) pairs in
 // column order at B's own row offsets, len[j] = number of pairs.  A word whose
 // columns straddle two 32-entry chunks of the row gives two pairs (harmless:
@@ -558,14 +779,32 @@ cudaError_t num_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
                        const WinCacheView& cache, const float2* b_split,
                        const int32_t* b_range_bad, int32_t arith, const int64_t* c_rowptr,
                        const int32_t* rows, int32_t nrows, int32_t* c_colind, double* c_vals,
-                       const int32_t* cap = nullptr, int32_t* cnt_out = nullptr) {
+                       const int32_t* cap = nullptr, int32_t* cnt_out = nullptr,
+                       const int32_t* nrows_dev = nullptr) {
   const size_t smem = (size_t)kWinWarps * NumWinGeom<W>::kWarpBytes;
   auto kern = k_num_window<W, SPEC>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid_for_rows(ctx, nrows), kWinWarps * 32, smem, ctx.stream>>>(
       A, B, bcomp, cache, ctx.row_lo, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind,
-      c_vals, ctx.status, cap, cnt_out);
+      c_vals, ctx.status, cap, cnt_out, nrows_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t num_kept(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                     const WinCacheView& cache, const float2* b_split, const int32_t* b_range_bad,
+                     int32_t arith, const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
+                     int32_t* c_colind, double* c_vals, int32_t* left_rows, int32_t* left_count) {
+  const size_t smem = (size_t)kKeptWarps * KeptGeom::kWarpBytes;
+  cudaError_t e = set_smem(k_num_kept, smem);
+  if (e != cudaSuccess) return e;
+  long long blocks = (nrows + kKeptWarps * 4 - 1) / (kKeptWarps * 4);
+  const long long capb = (long long)ctx.num_sms * 16;
+  if (blocks > capb) blocks = capb;
+  if (blocks < 1) blocks = 1;
+  k_num_kept<<<(int)blocks, kKeptWarps * 32, smem, ctx.stream>>>(
+      A, B, cache, ctx.row_lo, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals,
+      ctx.status, left_rows, left_count);
   return cudaGetLastError();
 }
 
@@ -602,16 +841,31 @@ cudaError_t launch_symbolic_window(const LaunchCtx& ctx, const BinSpec& bin, con
 
 cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,
                                   const CsrView& B, const BComp& bcomp, const WinCacheView& cache,
-                                  const float2* b_split, const int32_t* b_range_bad, int32_t arith,
+                                  const WinScratch& scratch, const float2* b_split,
+                                  const int32_t* b_range_bad, int32_t arith,
                                   const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
                                   int32_t* c_colind, double* c_vals) {
   if (nrows <= 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  const int32_t* wrows = rows;
+  const int32_t* wcount = nullptr;
+  if (cache.n && scratch.rows) {
+    timer_begin(ctx.timer, ctx.stream, "num_kept");
+    e = cudaMemsetAsync(scratch.count, 0, sizeof(int32_t), ctx.stream);
+    if (e == cudaSuccess)
+      e = num_kept(ctx, A, B, cache, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind,
+                   c_vals, scratch.rows, scratch.count);
+    timer_end(ctx.timer, ctx.stream);
+    if (e != cudaSuccess) return e;
+    wrows = scratch.rows;
+    wcount = scratch.count;
+  }
   timer_begin(ctx.timer, ctx.stream, "num_window");
-  cudaError_t e = cudaErrorInvalidValue;
+  e = cudaErrorInvalidValue;
 #define KK_NUM_WIN(WB)                                                                          \
   case WB:                                                                                      \
-    e = num_window<WB>(ctx, A, B, bcomp, cache, b_split, b_range_bad, arith, c_rowptr, rows,    \
-                       nrows, c_colind, c_vals);                                                \
+    e = num_window<WB>(ctx, A, B, bcomp, cache, b_split, b_range_bad, arith, c_rowptr, wrows,   \
+                       nrows, c_colind, c_vals, nullptr, nullptr, wcount);                      \
     break;
   switch (bin.slots) {
     KK_NUM_WIN(4096)
