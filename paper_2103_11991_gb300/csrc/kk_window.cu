@@ -493,14 +493,16 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
 }
 
 // Numeric phase of the rows whose structure the symbolic phase kept: the
-// row's words go into a small open-addressing table (slot = word mod 128,
-// linear probing; at most kCacheWords words in 128 slots) instead of a
-// W-bit window, so a warp needs about 3.6 KB of shared memory whatever the
-// row's span and more rows are in flight per SM.  An entry packs the word's
-// bits (low 32), its prefix count (bits 32..47) and the word index (48..63).
-// Rows without kept structure are appended to `left` for k_num_window.
+// row's words go into a small open-addressing table (slot = word mod 256,
+// linear probing; at most kCacheWords words in 256 slots) instead of a W-bit
+// window, so a warp needs about 4.6 KB of shared memory whatever the row's
+// span and more rows are in flight per SM.  Words less than 256 apart never
+// share a slot; a row whose words did collide takes the probing variant of the
+// value pass.  An entry packs the word's bits (low 32), its prefix count (bits
+// 32..47) and the word index (48..63).  Rows without kept structure are
+// appended to `left` for k_num_window.
 constexpr int kKeptWarps = 8;
-constexpr int kKeptSlots = 128;
+constexpr int kKeptSlots = 256;
 constexpr u64 kKeptEmpty = ~0ull;
 struct KeptGeom {
   // table u64[kKeptSlots] | vacc u64[kWindowMaxNnz + 2] | ainfo int4[32]
@@ -510,21 +512,153 @@ struct KeptGeom {
 };
 
 // Rank of column o (relative to the row's first word) through the table, or
-// the spare slot when o is not a column of the row.
+// the spare slot kWindowMaxNnz when o is not a column of the row.
+template <bool PROBE>
 __device__ __forceinline__ int kept_rank(const u64* table, uint32_t o, bool ok, int& missing) {
   const uint32_t w = o >> 5;
   uint32_t s = w & (kKeptSlots - 1);
   u64 e = table[s];
-  for (int k = 0; k < kKeptSlots && e != kKeptEmpty && (uint32_t)(e >> 48) != w; ++k) {
-    s = (s + 1) & (kKeptSlots - 1);
-    e = table[s];
+  if (PROBE) {
+    for (int k = 0; k < kKeptSlots && e != kKeptEmpty && (uint32_t)(e >> 48) != w; ++k) {
+      s = (s + 1) & (kKeptSlots - 1);
+      e = table[s];
+    }
   }
-  const bool hit = e != kKeptEmpty && (uint32_t)(e >> 48) == w;
-  const uint32_t word = hit ? (uint32_t)e : 0u;
-  const bool member = ok && hit && ((word >> (o & 31)) & 1u);
+  const uint32_t word = (uint32_t)e;
+  const bool member = ok && (uint32_t)(e >> 48) == w && ((word >> (o & 31)) & 1u);
   if (ok && !member) missing = 1;
   const int r = (int)((e >> 32) & 0xFFFFu) + __popc(word & ((1u << (o & 31)) - 1u));
   return member ? min(r, kWindowMaxNnz) : kWindowMaxNnz;
+}
+
+// Value pass over one chunk of at most 32 A entries (ainfo: B row start and
+// length, A value as two 32-bit halves; entries past the chunk have length
+// 0).  Batches of kWinBatch entries: every lane loads its products of the
+// batch, ranks them, then the batch's updates go in entry order; lanes without
+// a product update the spare slot, so nothing branches per entry.
+template <bool DFM, bool PROBE>
+__device__ __forceinline__ void kept_chunk(const int4* ainfo, int nch, int lo_c, const u64* table,
+                                           u64* vacc, const int32_t* __restrict__ bcol,
+                                           const float2* __restrict__ bspl,
+                                           const double* __restrict__ bval, int lane,
+                                           int& missing) {
+  for (int t0 = 0; t0 < nch; t0 += kWinBatch) {
+    float2 bv[kWinBatch];
+    int rk[kWinBatch];
+#pragma unroll
+    for (int u = 0; u < kWinBatch; ++u) {
+      const int2 in = *reinterpret_cast<const int2*>(&ainfo[t0 + u]);
+      const bool ok = lane < in.y;
+      const int q = in.x + lane;
+      int c = 0;
+      bv[u] = make_float2(0.f, 0.f);
+      if (ok) {
+        c = bcol[q];
+        if (DFM) {
+          bv[u] = bspl[q];
+        } else {
+          const long long bb = __double_as_longlong(bval[q]);
+          bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)), __int_as_float((int)(bb >> 32)));
+        }
+      }
+      rk[u] = kept_rank<PROBE>(table, (uint32_t)(c - lo_c), ok, missing);
+    }
+#pragma unroll
+    for (int u = 0; u < kWinBatch; ++u) {
+      const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
+      if (DFM) {
+        DF a, b;
+        a.hi = __int_as_float(az.x);
+        a.lo = __int_as_float(az.y);
+        b.hi = bv[u].x;
+        b.lo = bv[u].y;
+        DF s = df_unpack(vacc[rk[u]]);
+        df_fma(s, a, b);
+        vacc[rk[u]] = df_pack(s);
+      } else {
+        const double x = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
+        const double y = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
+                                              (unsigned)__float_as_int(bv[u].x));
+        double* v = reinterpret_cast<double*>(&vacc[rk[u]]);
+        *v = fma(x, y, *v);
+      }
+      __syncwarp();  // this A entry's updates are visible before the next one's
+    }
+  }
+}
+
+// Value pass for B rows longer than 32: one A entry at a time, lanes stride
+// the B row.
+template <bool DFM, bool PROBE>
+__device__ __forceinline__ void kept_chunk_long(const int4* ainfo, int nch, int lo_c,
+                                                const u64* table, u64* vacc,
+                                                const int32_t* __restrict__ bcol,
+                                                const float2* __restrict__ bspl,
+                                                const double* __restrict__ bval, int lane,
+                                                int& missing) {
+  for (int t = 0; t < nch; ++t) {
+    const int4 in = ainfo[t];
+    for (int q0 = 0; q0 < in.y; q0 += 32) {
+      const int q = in.x + q0 + lane;
+      const bool ok = q0 + lane < in.y;
+      const int c = ok ? bcol[q] : 0;
+      const int rank = kept_rank<PROBE>(table, (uint32_t)(c - lo_c), ok, missing);
+      if (DFM) {
+        DF a, b;
+        a.hi = __int_as_float(in.z);
+        a.lo = __int_as_float(in.w);
+        const float2 bb = ok ? bspl[q] : make_float2(0.f, 0.f);
+        b.hi = bb.x;
+        b.lo = bb.y;
+        DF s = df_unpack(vacc[rank]);
+        df_fma(s, a, b);
+        vacc[rank] = df_pack(s);
+      } else {
+        const double x = __longlong_as_double(((long long)in.w << 32) | (unsigned)in.z);
+        double* v = reinterpret_cast<double*>(&vacc[rank]);
+        *v = fma(x, ok ? bval[q] : 0.0, *v);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+template <bool DFM, bool PROBE>
+__device__ __forceinline__ void kept_values(int pa, int pe, const int32_t* __restrict__ acol,
+                                            const double* __restrict__ aval,
+                                            const int32_t* __restrict__ brp, int4* ainfo, int lo_c,
+                                            const u64* table, u64* vacc,
+                                            const int32_t* __restrict__ bcol,
+                                            const float2* __restrict__ bspl,
+                                            const double* __restrict__ bval, int lane, int& missing) {
+  for (int p0 = pa; p0 < pe; p0 += 32) {
+    const int p = p0 + lane;
+    int4 info = make_int4(0, 0, 0, 0);
+    if (p < pe) {
+      const int j = acol[p];
+      info.x = brp[j];
+      info.y = brp[j + 1] - info.x;
+      const double a = aval[p];
+      if (DFM) {
+        DF ad;
+        df_split(a, ad);
+        info.z = __float_as_int(ad.hi);
+        info.w = __float_as_int(ad.lo);
+      } else {
+        const long long ab = __double_as_longlong(a);
+        info.z = (int)(ab & 0xffffffffll);
+        info.w = (int)(ab >> 32);
+      }
+    }
+    ainfo[lane] = info;
+    __syncwarp();
+    const int nch = min(32, pe - p0);
+    if (__reduce_max_sync(kFull, (unsigned)info.y) <= 32u)
+      kept_chunk<DFM, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+    else
+      kept_chunk_long<DFM, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+    __syncwarp();
+  }
 }
 
 __global__ void __launch_bounds__(kKeptWarps * 32, 4)
@@ -540,11 +674,6 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
   u64* vacc = reinterpret_cast<u64*>(base + KeptGeom::kValOff);
   int4* ainfo = reinterpret_cast<int4*>(base + KeptGeom::kInfoOff);
   const bool df_all = arith == kArithDF32 && *b_range_bad == 0;
-  const int32_t* __restrict__ acol = A.colind;
-  const double* __restrict__ aval = A.vals;
-  const int32_t* __restrict__ brp = B.rowptr;
-  const int32_t* __restrict__ bcol = B.colind;
-  const double* __restrict__ bval = B.vals;
   const int per_cta = (nrows + gridDim.x - 1) / gridDim.x;
   const int r_begin = blockIdx.x * per_cta;
   const int r_end = min(nrows, r_begin + per_cta);
@@ -562,7 +691,7 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
     for (int s = lane; s < kKeptSlots; s += 32) table[s] = kKeptEmpty;
     for (int e = lane; e < kWindowMaxNnz; e += 32) vacc[e] = 0ull;
     __syncwarp();
-    int run = 0, bad = 0;
+    int run = 0, bad = 0, probe = 0;
     for (int e0 = 0; e0 < L; e0 += 32) {
       const int e = e0 + lane;
       uint32_t w = 0u, m = 0u;
@@ -580,6 +709,7 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
         bool placed = false;
         for (int k = 0; k < kKeptSlots && !placed; ++k) {
           placed = atomicCAS(&table[s], kKeptEmpty, entry) == kKeptEmpty;
+          if (!placed) probe = 1;
           s = (s + 1) & (kKeptSlots - 1);
         }
         if (!placed) bad = 1;
@@ -592,113 +722,17 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
       }
     }
     if (bad || (run != cnt && lane == 0)) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    probe = __any_sync(kFull, probe);
     __syncwarp();
-    bool df = df_all;
-    if (df_all && pe - pa > 32) df = row_df_ok<32>(aval, pa, pe, lane, kFull);
+    // arithmetic of this row: DF32 unless a value of the row is outside its window
+    const bool df = df_all && row_df_ok<32>(A.vals, pa, pe, lane, kFull);
     int missing = 0;
-    for (int p0 = pa; p0 < pe; p0 += 32) {
-      const int p = p0 + lane;
-      int4 info = make_int4(0, 0, 0, 0);
-      double a = 0.0;
-      if (p < pe) {
-        const int j = acol[p];
-        info.x = brp[j];
-        info.y = brp[j + 1] - info.x;
-        a = aval[p];
-      }
-      DF ad;
-      const int split_bad = df_all ? (df_split(a, ad) ? 0 : 1) : 1;
-      if (df_all && pe - pa <= 32) df = __any_sync(kFull, split_bad) == 0;
-      if (df) {
-        info.z = __float_as_int(ad.hi);
-        info.w = __float_as_int(ad.lo);
-      } else {
-        const long long ab = __double_as_longlong(a);
-        info.z = (int)(ab & 0xffffffffll);
-        info.w = (int)(ab >> 32);
-      }
-      ainfo[lane] = info;
-      __syncwarp();
-      const int nch = min(32, pe - p0);
-      const unsigned maxlen = __reduce_max_sync(kFull, (unsigned)info.y);
-      if (maxlen <= 32u) {
-        for (int t0 = 0; t0 < nch; t0 += kWinBatch) {
-          float2 bv[kWinBatch];
-          int rk[kWinBatch];
-#pragma unroll
-          for (int u = 0; u < kWinBatch; ++u) {
-            int c = 0;
-            bool ok = false;
-            bv[u] = make_float2(0.f, 0.f);
-            if (t0 + u < nch) {
-              const int2 in = *reinterpret_cast<const int2*>(&ainfo[t0 + u]);
-              if (lane < in.y) {
-                const int q = in.x + lane;
-                ok = true;
-                c = bcol[q];
-                if (df) {
-                  bv[u] = bspl[q];
-                } else {
-                  const long long bb = __double_as_longlong(bval[q]);
-                  bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)),
-                                      __int_as_float((int)(bb >> 32)));
-                }
-              }
-            }
-            rk[u] = kept_rank(table, (uint32_t)(c - lo_c), ok, missing);
-          }
-#pragma unroll
-          for (int u = 0; u < kWinBatch; ++u) {
-            if (t0 + u < nch) {
-              const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
-              if (df) {
-                DF av2, b2;
-                av2.hi = __int_as_float(az.x);
-                av2.lo = __int_as_float(az.y);
-                b2.hi = bv[u].x;
-                b2.lo = bv[u].y;
-                DF s = df_unpack(vacc[rk[u]]);
-                df_fma(s, av2, b2);
-                vacc[rk[u]] = df_pack(s);
-              } else {
-                const double x = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
-                const double y = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
-                                                      (unsigned)__float_as_int(bv[u].x));
-                double* v = reinterpret_cast<double*>(&vacc[rk[u]]);
-                *v = fma(x, y, *v);
-              }
-              __syncwarp();  // this A entry's updates are visible before the next one's
-            }
-          }
-        }
-      } else {
-        for (int t = 0; t < nch; ++t) {
-          const int4 in = ainfo[t];
-          for (int q0 = 0; q0 < in.y; q0 += 32) {
-            const int q = in.x + q0 + lane;
-            const bool ok = q0 + lane < in.y;
-            const int c = ok ? bcol[q] : 0;
-            const int rank = kept_rank(table, (uint32_t)(c - lo_c), ok, missing);
-            if (df) {
-              DF av2, b2;
-              av2.hi = __int_as_float(in.z);
-              av2.lo = __int_as_float(in.w);
-              const float2 bb = ok ? bspl[q] : make_float2(0.f, 0.f);
-              b2.hi = bb.x;
-              b2.lo = bb.y;
-              DF s = df_unpack(vacc[rank]);
-              df_fma(s, av2, b2);
-              vacc[rank] = df_pack(s);
-            } else {
-              const double x = __longlong_as_double(((long long)in.w << 32) | (unsigned)in.z);
-              double* v = reinterpret_cast<double*>(&vacc[rank]);
-              *v = fma(x, ok ? bval[q] : 0.0, *v);
-            }
-            __syncwarp();
-          }
-        }
-      }
-      __syncwarp();
+    if (df) {
+      if (probe) kept_values<true, true>(pa, pe, A.colind, A.vals, B.rowptr, ainfo, lo_c, table, vacc, B.colind, bspl, B.vals, lane, missing);
+      else kept_values<true, false>(pa, pe, A.colind, A.vals, B.rowptr, ainfo, lo_c, table, vacc, B.colind, bspl, B.vals, lane, missing);
+    } else {
+      if (probe) kept_values<false, true>(pa, pe, A.colind, A.vals, B.rowptr, ainfo, lo_c, table, vacc, B.colind, bspl, B.vals, lane, missing);
+      else kept_values<false, false>(pa, pe, A.colind, A.vals, B.rowptr, ainfo, lo_c, table, vacc, B.colind, bspl, B.vals, lane, missing);
     }
     if (missing) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
     const int n = min(cnt, kWindowMaxNnz);
