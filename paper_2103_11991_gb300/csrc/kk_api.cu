@@ -159,35 +159,6 @@ __device__ __forceinline__ uint8_t classify(const BinTable& t, long long q, int 
 // ---------------------------------------------------------------------------
 constexpr int kAnaTeam = 8;
 
-// B rows: strictly ascending columns?  column range [0, k)?
-__global__ void k_analyze_b(CsrView B, int32_t* sorted_flag, int* status) {
-  const int tl = threadIdx.x % kAnaTeam;
-  const unsigned mask = team_mask<kAnaTeam>();
-  const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kAnaTeam;
-  const long long nteams = (long long)gridDim.x * blockDim.x / kAnaTeam;
-  int unsorted = 0, bad = 0;
-  if (team0 == 0 && tl == 0 && B.rowptr[0] != 0) bad = 1;
-  for (long long r = team0; r < B.m; r += nteams) {
-    const int bs = B.rowptr[r], be = B.rowptr[r + 1];
-    if (bs < 0 || be < bs || be > B.nnz) {
-      bad = 1;
-      continue;
-    }
-    for (int q = bs + tl; q < be; q += kAnaTeam) {
-      const int c = B.colind[q];
-      if ((unsigned)c >= (unsigned)B.n) bad = 1;
-      if (q > bs && B.colind[q - 1] >= c) unsorted = 1;
-    }
-  }
-  unsorted = __any_sync(0xffffffffu, unsorted);
-  bad = __any_sync(0xffffffffu, bad);
-  (void)mask;
-  if ((threadIdx.x & 31) == 0) {
-    if (unsorted) atomicAnd(sorted_flag, 0);
-    if (bad) set_status(status, KK_ERR_BAD_INDEX);
-  }
-}
-
 // A rows: flop bound, column range, symbolic bin id; optional total flops.
 __global__ void k_analyze_a(CsrView A, const int32_t* __restrict__ brp,
                             const int32_t* __restrict__ bcol, int32_t nb_rows,
@@ -732,31 +703,57 @@ BinTable to_table(const std::vector<BinSpec>& bins) {
 
 LaunchCtx ctx_of(kk_spgemm_handle h) {
   return LaunchCtx{h->stream, h->timer, &h->d_misc.as<Misc>()->status, h->num_sms, h->max_smem,
-                   h->d_rowlo.as<int32_t>()};
+                   h->d_rowlo.as<int32_t>(), h->d_flop.as<long long>()};
 }
 
-// Compressed B for the window tier (sorted B only).  A symbolic call always
-// rebuilds it (force); a numeric call rebuilds it only when B's index arrays
-// are not the ones it was built from.  *built = 1 when a kernel was launched.
-kk_status ensure_bcomp(kk_spgemm_handle h, const CsrView& bv, bool force, BComp* out, int* built) {
+// Analysis of B at the start of a symbolic call; with the window tier on, the
+// same pass writes the compressed B (valid once B is known to be sorted, see
+// accept_bcomp).
+kk_status analyze_b(kk_spgemm_handle h, const CsrView& bv) {
+  h->bc_valid = false;
+  if (bv.m <= 0) return KK_OK;
+  int2* bc = nullptr;
+  int32_t* len = nullptr;
+  if (h->opt.use_window) {
+    KK_CUDA(h, h->d_bc.ensure(sizeof(int2) * (size_t)(bv.nnz > 0 ? bv.nnz : 1)), "alloc compressed B");
+    KK_CUDA(h, h->d_bclen.ensure(sizeof(int32_t) * (size_t)bv.m), "alloc compressed B");
+    bc = h->d_bc.as<int2>();
+    len = h->d_bclen.as<int32_t>();
+  }
+  Misc* dm = h->d_misc.as<Misc>();
+  KK_CUDA(h, launch_analyze_b(ctx_of(h), bv, &dm->sorted, bc, len, &dm->bc_pairs), "analyze launch");
+  return KK_OK;
+}
+
+// After the symbolic call's readback: the compressed B written by analyze_b
+// belongs to these arrays if B is sorted.
+void accept_bcomp(kk_spgemm_handle h, const CsrView& bv, bool analyzed) {
+  h->bc_valid = analyzed && h->opt.use_window && h->b_sorted && bv.m > 0;
+  h->bc_key[0] = bv.rowptr;
+  h->bc_key[1] = bv.colind;
+  h->bc_m = bv.m;
+  h->bc_nnz = bv.nnz;
+}
+
+// Compressed B for a window launch (sorted B only): the one of the last
+// symbolic call, rebuilt when B's index arrays are not the ones it was built
+// from.  *built = 1 when a kernel was launched.
+kk_status ensure_bcomp(kk_spgemm_handle h, const CsrView& bv, BComp* out, int* built) {
   out->bc = nullptr;
   out->len = nullptr;
   *built = 0;
   if (!h->opt.use_window || !h->b_sorted || bv.m <= 0) return KK_OK;
   const bool same = h->bc_valid && h->bc_key[0] == bv.rowptr && h->bc_key[1] == bv.colind &&
                     h->bc_m == bv.m && h->bc_nnz == bv.nnz;
-  if (force || !same) {
+  if (!same) {
     h->bc_valid = false;
     KK_CUDA(h, h->d_bc.ensure(sizeof(int2) * (size_t)(bv.nnz > 0 ? bv.nnz : 1)), "alloc compressed B");
     KK_CUDA(h, h->d_bclen.ensure(sizeof(int32_t) * (size_t)bv.m), "alloc compressed B");
-    KK_CUDA(h, launch_compress_b(ctx_of(h), bv, h->d_bc.as<int2>(), h->d_bclen.as<int32_t>(),
-                                 &h->d_misc.as<Misc>()->bc_pairs),
+    // sortedness is not re-decided here: the flag goes to a scratch word
+    KK_CUDA(h, launch_analyze_b(ctx_of(h), bv, &h->d_misc.as<Misc>()->pad, h->d_bc.as<int2>(),
+                                h->d_bclen.as<int32_t>(), nullptr),
             "compress launch");
-    h->bc_valid = true;
-    h->bc_key[0] = bv.rowptr;
-    h->bc_key[1] = bv.colind;
-    h->bc_m = bv.m;
-    h->bc_nnz = bv.nnz;
+    accept_bcomp(h, bv, true);
     *built = 1;
   }
   out->bc = h->d_bc.as<int2>();
@@ -972,9 +969,7 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   int32_t* num_start = sym_start + (kMaxBins + 1);
   if (m > 0) {
     timer_begin(h->timer, s, "analyze");
-    if (bv.m > 0)
-      k_analyze_b<<<grid_for((long long)bv.m * kAnaTeam, 256, h->num_sms * 8), 256, 0, s>>>(
-          bv, &dm->sorted, &dm->status);
+    if ((st = analyze_b(h, bv)) != KK_OK) return st;
     k_analyze_a<<<grid_for((long long)m * kAnaTeam, 256, h->num_sms * 8), 256, 0, s>>>(
         av, bv.rowptr, bv.colind, bv.m, &dm->sorted, to_table(h->sym_bins), h->opt.team_vec_min_len,
         h->d_flop.as<long long>(), h->d_sbin.as<uint8_t>(), h->d_rowlo.as<int32_t>(),
@@ -994,6 +989,7 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   h->b_sorted = hm->sorted;
   h->stats[6] = (int64_t)hm->total_flop;
   h->stats[7] = hm->sorted;
+  accept_bcomp(h, bv, m > 0);
 
   // symbolic kernels per bin
   if (m > 0) {
@@ -1004,7 +1000,7 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
       if (h->sym_bins[b].tier == kTierWindow && h_start[b + 1] > h_start[b]) any_win = true;
     BComp bcomp;
     int bc_built = 0;
-    if ((st = ensure_bcomp(h, bv, true, &bcomp, &bc_built)) != KK_OK) return st;
+    if ((st = ensure_bcomp(h, bv, &bcomp, &bc_built)) != KK_OK) return st;
     WinCache wcache;
     if ((st = cache_for_symbolic(h, m, any_win, av, bv, &wcache)) != KK_OK) return st;
     int64_t tier_rows[4] = {0, 0, 0, 0};
@@ -1025,7 +1021,7 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
     int64_t nb_launched = 0;
     for (int b = 0; b < nbs; ++b) nb_launched += (h_start[b + 1] - h_start[b]) > 0 ? 1 : 0;
     // analyze (2) + binning (3) + symbolic bins + scan (3) + numeric binning (3)
-    h->stats[8] = (bv.m > 0 ? 1 : 0) + 1 + 3 + bc_built + nb_launched + 3 + 3 + 1;
+    h->stats[8] = (bv.m > 0 ? 1 : 0) + 1 + 3 + nb_launched + 3 + 3 + 1;
     // scan + numeric bins
     timer_begin(h->timer, s, "scan");
     k_scan_partial<<<nblk_scan, kScanBlock, 0, s>>>(m, h->d_cnt.as<int32_t>(), h->d_scan.as<long long>());
@@ -1110,7 +1106,7 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
   BComp bcomp{nullptr, nullptr};
   if (any_win) {
     int built = 0;
-    if ((st = ensure_bcomp(h, bv, false, &bcomp, &built)) != KK_OK) return st;
+    if ((st = ensure_bcomp(h, bv, &bcomp, &built)) != KK_OK) return st;
     h->stats[9] += built;
   }
   WinCacheView wview;
@@ -1233,10 +1229,7 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
   KK_CUDA(h, cudaMemcpyAsync(dm, &init, sizeof(Misc), cudaMemcpyHostToDevice, s), "init");
   LaunchCtx ctx = ctx_of(h);
   if (m > 0) {
-    if (bv.m > 0)
-      k_analyze_b<<<grid_for((long long)bv.m * kAnaTeam, 256, h->num_sms * 8), 256, 0, s>>>(
-          bv, &dm->sorted, &dm->status);
-    KK_CUDA(h, cudaGetLastError(), "analyze launch");
+    if ((st = analyze_b(h, bv)) != KK_OK) return st;
     cudaError_t e = launch_learned_analyze(
         ctx, av, bv, &dm->sorted, h->have_pred ? h->d_params.as<float>() : nullptr, h->quantile,
         h->have_pred ? 1 : 0, h->d_flop.as<long long>(), h->d_rowlo.as<int32_t>(),
@@ -1259,6 +1252,7 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
   h->b_sorted = hm->sorted;
   h->stats[6] = (int64_t)hm->total_flop;
   h->stats[7] = hm->sorted;
+  accept_bcomp(h, bv, m > 0);
   const long long staging = m > 0 ? hm->grand2 : 0;
   std::vector<int32_t> lstart(h_start, h_start + nbl + 1);
   KK_CUDA(h, h->d_scol.ensure(sizeof(int32_t) * (size_t)(staging > 0 ? staging : 1)), "alloc staging");
@@ -1277,7 +1271,7 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
   BComp bcomp{nullptr, nullptr};
   if (m > 0) {
     int bc_built = 0;
-    if ((st = ensure_bcomp(h, bv, true, &bcomp, &bc_built)) != KK_OK) return st;
+    if ((st = ensure_bcomp(h, bv, &bcomp, &bc_built)) != KK_OK) return st;
   }
   h->cache_valid = false;
   if (m > 0) {
@@ -1400,7 +1394,7 @@ kk_status kk_spgemm_learned_numeric(kk_spgemm_handle h, const kk_csr* A, const k
   BComp bcomp{nullptr, nullptr};
   if (any_win) {
     int built = 0;
-    if ((st = ensure_bcomp(h, bv, false, &bcomp, &built)) != KK_OK) return st;
+    if ((st = ensure_bcomp(h, bv, &bcomp, &built)) != KK_OK) return st;
   }
   WinCacheView wview;
   WinScratch wscratch;

@@ -20,6 +20,7 @@ struct LaunchCtx {
   int num_sms;
   int max_smem_optin;
   const int32_t* row_lo;  // first column of each row's span window (window tier)
+  const long long* flop;  // flop bound of each row (wide tier)
 };
 
 struct CsrView {
@@ -72,8 +73,11 @@ struct WinScratch {
   int32_t* rows;
   int32_t* count;
 };
-cudaError_t launch_compress_b(const LaunchCtx& ctx, const CsrView& B, int2* bc, int32_t* len,
-                              unsigned long long* pairs);
+// Analysis of B (kk_window.cu): clears *sorted_flag unless every row is
+// strictly ascending, sets KK_ERR_BAD_INDEX on out-of-range structure, and,
+// when bc is non-null, writes the compressed rows (pairs counted into *pairs).
+cudaError_t launch_analyze_b(const LaunchCtx& ctx, const CsrView& B, int32_t* sorted_flag,
+                             int2* bc, int32_t* len, unsigned long long* pairs);
 
 // One bin of rows: its tier and the accumulator geometry.
 struct BinSpec {
@@ -99,6 +103,17 @@ cudaError_t launch_numeric_bin(const LaunchCtx& ctx, const BinSpec& bin, const C
                                const int32_t* b_range_bad, int32_t arith,
                                const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
                                int32_t* c_colind, double* c_vals, int32_t debug_checks);
+
+// Wide tier (kk_wide.cu): CTA-per-row bit vector over all k columns, used for
+// the CTA and dense bins when it fits in shared memory.
+bool wide_symbolic_fits(const LaunchCtx& ctx, int32_t k);
+bool wide_numeric_fits(const LaunchCtx& ctx, int32_t k);
+cudaError_t launch_symbolic_wide(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                                 const long long* flop, const int32_t* rows, int32_t nrows,
+                                 int32_t* cnt);
+cudaError_t launch_numeric_wide(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                                const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
+                                int32_t* c_colind, double* c_vals);
 
 // Window-tier launches (kk_window.cu).
 cudaError_t launch_symbolic_window(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,

@@ -725,6 +725,12 @@ cudaError_t launch_numeric_bin(const LaunchCtx& ctx, const BinSpec& bin, const C
     timer_end(ctx.timer, ctx.stream);
     return e;
   }
+  if ((bin.tier == kTierCta || bin.tier == kTierDense) && wide_numeric_fits(ctx, B.n)) {
+    timer_begin(ctx.timer, ctx.stream, "num_wide");
+    e = launch_numeric_wide(ctx, A, B, c_rowptr, rows, nrows, c_colind, c_vals);
+    timer_end(ctx.timer, ctx.stream);
+    return e;
+  }
   if (bin.tier == kTierCta) {
     timer_begin(ctx.timer, ctx.stream, "num_cta");
     switch (log2s) {

@@ -334,6 +334,12 @@ cudaError_t launch_symbolic_bin(const LaunchCtx& ctx, const BinSpec& bin, const 
     timer_end(ctx.timer, ctx.stream);
     return e;
   }
+  if ((bin.tier == kTierCta || bin.tier == kTierDense) && ctx.flop && wide_symbolic_fits(ctx, B.n)) {
+    timer_begin(ctx.timer, ctx.stream, "sym_wide");
+    cudaError_t e = launch_symbolic_wide(ctx, A, B, ctx.flop, rows, nrows, cnt);
+    timer_end(ctx.timer, ctx.stream);
+    return e;
+  }
   if (bin.tier == kTierCta) {
     timer_begin(ctx.timer, ctx.stream, "sym_cta");
     cudaError_t e;

@@ -1,0 +1,418 @@
+// Wide tier: rows too heavy for a team hash (the CTA and dense bins), when the
+// bit vector of all k columns of C fits in shared memory.
+//
+// The paper's dense accumulator (Sec. "Standard SpGEMM Kernel") over the full
+// column range: one CTA per row keeps a k-bit vector in shared memory, plus
+// one summary bit per 32-bit word for rows whose products touch few words.
+//   symbolic: every product ORs its column bit (no probing, no chunk passes);
+//             nnz(C(i,:)) = popcount of the touched words, cleared as they are
+//             counted;
+//   numeric:  the same bits; prefix counts over the touched words give every
+//             column its rank, the column indices are written from the bits
+//             in order, and each product adds a*b into value slot `rank`: in
+//             shared memory when the row's nnz fits, else directly into C's
+//             values (zeroed first) with global float64 atomics.  The order of
+//             the additions is not fixed, so the values carry the float64 bound
+//             of an unordered sum.
+// Warps take the row's A entries eight at a time and split the flattened
+// (A entry, B entry) products of those eight; each lane issues kWideU loads
+// before it uses them, so every warp keeps several B loads in flight.
+#include "kk_internal.h"
+#include "kk_device.cuh"
+
+namespace kk {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWideChunk = 8;  // A entries per warp chunk
+constexpr int kWideU = 4;      // warp steps whose loads are issued together
+constexpr int kWideBlock = 1024;
+
+// Words of the column bit vector: ceil(k / 32) rounded up to a multiple of 32.
+__host__ __device__ inline int wide_words(int k) { return (((k + 31) >> 5) + 31) & ~31; }
+
+// Shared memory: bits u32[words] | sum u32[words / 32] | region u8[2 * words]
+// | values f64[vcap].  The region holds either per-word prefixes (u16, rows
+// with values in shared memory) or per-group (8 words) u32 prefixes and
+// per-word u8 offsets (rows with values in C); the ordered list of touched
+// words (u16) is built in the value area before the values are zeroed.
+struct WideGeom {
+  size_t sum_off, reg_off, val_off, bytes;
+  int vcap;
+};
+inline WideGeom wide_geom(int words, size_t max_smem, bool numeric) {
+  WideGeom g;
+  g.sum_off = (size_t)words * 4;
+  g.reg_off = g.sum_off + (size_t)words / 32 * 4;
+  g.reg_off = (g.reg_off + 15) / 16 * 16;
+  g.val_off = numeric ? g.reg_off + (size_t)words * 2 : g.reg_off;
+  const long long left = (long long)max_smem - (long long)g.val_off;
+  g.vcap = (numeric && left > 0) ? (int)(left / 8) : 0;
+  if (g.vcap > 32768) g.vcap = 32768;
+  g.bytes = g.val_off + (size_t)g.vcap * 8;
+  return g;
+}
+
+// Lanes 0..7 hold A entry p0 + lane of the chunk: B row start and length.
+// Returns the chunk's product count; incl / base are the lane's inclusive
+// length prefix and B start minus its exclusive prefix.
+__device__ __forceinline__ int wide_chunk_setup(const CsrView& A, const CsrView& B, int p0, int pe,
+                                                int lane, int& incl, int& base, int& bad) {
+  int bs = 0, bl = 0;
+  const int p = p0 + lane;
+  if (lane < kWideChunk && p < pe) {
+    const int j = A.colind[p];
+    if ((unsigned)j < (unsigned)B.m) {
+      bs = B.rowptr[j];
+      bl = B.rowptr[j + 1] - bs;
+    } else {
+      bad = 1;
+    }
+  }
+  incl = team_inclusive_scan<32>(bl, lane, kFull);
+  base = bs - (incl - bl);
+  return __shfl_sync(kFull, incl, kWideChunk - 1);
+}
+
+// Owner (0..7) of flattened product f of the chunk.
+__device__ __forceinline__ int wide_owner(int incl, int f) {
+  int own = 0;
+#pragma unroll
+  for (int step = kWideChunk / 2; step > 0; step >>= 1) {
+    const int v = __shfl_sync(kFull, incl, own + step - 1);
+    if (v <= f) own += step;
+  }
+  return own;
+}
+
+// Exclusive block scan of v (blockDim.x <= 1024); *total receives the sum.
+__device__ __forceinline__ int block_exscan(int v, int* tmp, int* total) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int incl = team_inclusive_scan<32>(v, lane, kFull);
+  if (lane == 31) tmp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int x = lane < nwarps ? tmp[lane] : 0;
+    const int xi = team_inclusive_scan<32>(x, lane, kFull);
+    tmp[lane] = xi - x;
+    if (lane == 31) tmp[32] = xi;
+  }
+  __syncthreads();
+  const int r = tmp[warp] + incl - v;
+  *total = tmp[32];
+  __syncthreads();
+  return r;
+}
+
+// OR the column bits of the products of A entries [pa, pe) into bits (and,
+// with SUM, the summary bits of their words).
+template <bool SUM>
+__device__ __forceinline__ void wide_set_bits(const CsrView& A, const CsrView& B, int pa, int pe,
+                                              uint32_t* bits, uint32_t* sum, int words, int& bad) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int32_t* __restrict__ bcol = B.colind;
+  for (int p0 = pa + warp * kWideChunk; p0 < pe; p0 += nwarps * kWideChunk) {
+    int incl, base;
+    const int total = wide_chunk_setup(A, B, p0, pe, lane, incl, base, bad);
+    for (int f0 = 0; f0 < total; f0 += 32 * kWideU) {
+      int col[kWideU];
+#pragma unroll
+      for (int u = 0; u < kWideU; ++u) {
+        const int f = f0 + u * 32 + lane;
+        const int own = wide_owner(incl, f);
+        const int qb = __shfl_sync(kFull, base, own);
+        col[u] = f < total ? bcol[qb + f] : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < kWideU; ++u) {
+        const int c = col[u];
+        if (c >= 0) {
+          if ((unsigned)c < (unsigned)(words * 32)) {
+            atomicOr(&bits[c >> 5], 1u << (c & 31));
+            if (SUM) atomicOr(&sum[c >> 10], 1u << ((c >> 5) & 31));
+          } else {
+            bad = 1;
+          }
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWideBlock, 1)
+k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long long* __restrict__ flop,
+           const int32_t* __restrict__ rows, int32_t nrows, int32_t* __restrict__ cnt, int* status) {
+  extern __shared__ __align__(16) unsigned char wsm[];
+  uint32_t* bits = reinterpret_cast<uint32_t*>(wsm);
+  uint32_t* sum = reinterpret_cast<uint32_t*>(wsm + sum_off);
+  __shared__ int tmp[33];
+  const int nsum = words >> 5;
+  for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4)
+    *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
+  for (int s = threadIdx.x; s < nsum; s += blockDim.x) sum[s] = 0u;
+  __syncthreads();
+  int bad = 0;
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int i = rows[r];
+    const bool sparse = flop[i] < (long long)words;  // few words touched: walk the summary
+    int c = 0;
+    if (sparse) {
+      wide_set_bits<true>(A, B, A.rowptr[i], A.rowptr[i + 1], bits, sum, words, bad);
+      __syncthreads();
+      for (int s = threadIdx.x; s < nsum; s += blockDim.x) {
+        uint32_t m = sum[s];
+        sum[s] = 0u;
+        while (m) {
+          const int b = __ffs(m) - 1;
+          m &= m - 1;
+          const int w = s * 32 + b;
+          c += __popc(bits[w]);
+          bits[w] = 0u;
+        }
+      }
+    } else {
+      wide_set_bits<false>(A, B, A.rowptr[i], A.rowptr[i + 1], bits, sum, words, bad);
+      __syncthreads();
+      for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4) {
+        uint4* q = reinterpret_cast<uint4*>(&bits[w]);
+        const uint4 v = *q;
+        c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        *q = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+    int tot;
+    block_exscan(c, tmp, &tot);
+    if (threadIdx.x == 0) cnt[i] = tot;
+  }
+  if (bad) set_status(status, KK_ERR_BAD_INDEX);
+}
+
+__global__ void __launch_bounds__(kWideBlock, 1)
+k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, uint32_t reg_off,
+           uint32_t val_off, const int64_t* __restrict__ c_rowptr, const int32_t* __restrict__ rows,
+           int32_t nrows, int32_t* __restrict__ c_colind, double* __restrict__ c_vals, int* status) {
+  extern __shared__ __align__(16) unsigned char wsm[];
+  uint32_t* bits = reinterpret_cast<uint32_t*>(wsm);
+  uint32_t* sum = reinterpret_cast<uint32_t*>(wsm + sum_off);
+  uint16_t* wpre16 = reinterpret_cast<uint16_t*>(wsm + reg_off);  // sparse rows
+  uint32_t* gpre = reinterpret_cast<uint32_t*>(wsm + reg_off);    // dense rows
+  uint8_t* wpre8 = wsm + reg_off + (size_t)(words / 8) * 4;       // dense rows
+  double* vals = reinterpret_cast<double*>(wsm + val_off);
+  uint16_t* list = reinterpret_cast<uint16_t*>(wsm + val_off);
+  __shared__ int tmp[33];
+  const int nsum = words >> 5;
+  const int groups = words >> 3;
+  for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4)
+    *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
+  for (int s = threadIdx.x; s < nsum; s += blockDim.x) sum[s] = 0u;
+  __syncthreads();
+  int bad = 0, mismatch = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int32_t* __restrict__ bcol = B.colind;
+  const double* __restrict__ bval = B.vals;
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int i = rows[r];
+    const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
+    const int64_t off = c_rowptr[i];
+    const int cnt = (int)(c_rowptr[i + 1] - off);
+    // values in shared memory (and the word list in their place) when the row fits
+    const bool sparse = cnt <= vcap && cnt <= 65535;
+    bool row_bad = false;
+    int total;
+    if (sparse) {
+      wide_set_bits<true>(A, B, pa, pe, bits, sum, words, bad);
+      __syncthreads();
+      // ordered list of touched words: summary words in order, bits in order,
+      // in rounds of blockDim summary words
+      int L = 0;
+      for (int s0 = 0; s0 < nsum; s0 += blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        uint32_t m = s < nsum ? sum[s] : 0u;
+        int t;
+        int pos = L + block_exscan(__popc(m), tmp, &t);
+        L += t;
+        if (s < nsum) sum[s] = 0u;
+        while (m) {
+          const int b = __ffs(m) - 1;
+          m &= m - 1;
+          if (pos < cnt) list[pos] = (uint16_t)(s * 32 + b);
+          ++pos;
+        }
+      }
+      __syncthreads();
+      if (L > cnt) {  // more touched words than the row has columns
+        row_bad = true;
+        L = cnt;
+      }
+      // per-word prefixes over the list, columns written in order
+      int run = 0;
+      for (int e0 = 0; e0 < L; e0 += blockDim.x) {
+        const int e = e0 + threadIdx.x;
+        const int w = e < L ? (int)list[e] : 0;
+        uint32_t m = e < L ? bits[w] : 0u;
+        int t;
+        int pos = run + block_exscan(__popc(m), tmp, &t);
+        run += t;
+        if (e < L) {
+          wpre16[w] = (uint16_t)pos;
+          while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            if (pos < cnt) c_colind[off + pos] = w * 32 + b;
+            ++pos;
+          }
+        }
+      }
+      total = run;
+      __syncthreads();
+      // the list area now holds the values; the touched words are found again
+      // from C's columns when they are cleared
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) vals[e] = 0.0;
+    } else {
+      wide_set_bits<false>(A, B, pa, pe, bits, sum, words, bad);
+      __syncthreads();
+      const int gpt = (groups + blockDim.x - 1) / blockDim.x;
+      const int g0 = threadIdx.x * gpt, g1 = min(groups, g0 + gpt);
+      int mine = 0;
+      for (int g = g0; g < g1; ++g)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) mine += __popc(bits[g * 8 + k]);
+      int run = block_exscan(mine, tmp, &total);
+      for (int g = g0; g < g1; ++g) {
+        gpre[g] = (uint32_t)run;
+        int in = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int w = g * 8 + k;
+          wpre8[w] = (uint8_t)in;
+          uint32_t m = bits[w];
+          int pos = run + in;
+          in += __popc(m);
+          while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            if (pos < cnt) c_colind[off + pos] = w * 32 + b;
+            ++pos;
+          }
+        }
+        run += in;
+      }
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) c_vals[off + e] = 0.0;
+    }
+    if (total != cnt) row_bad = true;
+    if (row_bad) mismatch = 1;
+    __syncthreads();
+    // values: rank = prefix of the word + popc(bits below the column)
+    for (int p0 = pa + warp * kWideChunk; p0 < pe; p0 += nwarps * kWideChunk) {
+      int incl, base;
+      const int tot = wide_chunk_setup(A, B, p0, pe, lane, incl, base, bad);
+      const double a_l = (lane < kWideChunk && p0 + lane < pe) ? A.vals[p0 + lane] : 0.0;
+      for (int f0 = 0; f0 < tot; f0 += 32 * kWideU) {
+        int col[kWideU];
+        double prod[kWideU];
+#pragma unroll
+        for (int u = 0; u < kWideU; ++u) {
+          const int f = f0 + u * 32 + lane;
+          const int own = wide_owner(incl, f);
+          const int qb = __shfl_sync(kFull, base, own);
+          const double a = __shfl_sync(kFull, a_l, own);
+          col[u] = -1;
+          prod[u] = 0.0;
+          if (f < tot) {
+            col[u] = bcol[qb + f];
+            prod[u] = a * bval[qb + f];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kWideU; ++u) {
+          const int c = col[u];
+          if (c >= 0 && (unsigned)c < (unsigned)(words * 32)) {
+            const int w = c >> 5;
+            const uint32_t word = bits[w];
+            const int below = __popc(word & ((1u << (c & 31)) - 1u));
+            const int rank = sparse ? (int)wpre16[w] + below
+                                    : (int)gpre[w >> 3] + (int)wpre8[w] + below;
+            if (rank < cnt) {
+              if (sparse) atomicAdd(&vals[rank], prod[u]);
+              else atomicAdd(&c_vals[off + rank], prod[u]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (sparse) {
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) c_vals[off + e] = vals[e];
+    }
+    if (sparse && !row_bad) {
+      // clear the touched words: they are the words of this row's columns
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) bits[c_colind[off + e] >> 5] = 0u;
+    } else {
+      for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4)
+        *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
+  }
+  if (bad) set_status(status, KK_ERR_BAD_INDEX);
+  if (mismatch) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+}
+
+// Dynamic shared memory available to the wide kernels (their static arrays
+// take the rest of the opt-in limit).
+size_t wide_budget(const LaunchCtx& ctx) {
+  return ctx.max_smem_optin > 1024 ? (size_t)ctx.max_smem_optin - 1024 : 0;
+}
+
+int wide_grid(const LaunchCtx& ctx, size_t smem, int nrows) {
+  int per_sm = (int)(((size_t)ctx.max_smem_optin + 1024) / (smem + 1024));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 2048 / kWideBlock) per_sm = 2048 / kWideBlock;
+  long long g = (long long)ctx.num_sms * per_sm;
+  if (g > nrows) g = nrows;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+bool wide_symbolic_fits(const LaunchCtx& ctx, int32_t k) {
+  if (k <= 0) return false;
+  return wide_geom(wide_words(k), wide_budget(ctx), false).bytes <= wide_budget(ctx);
+}
+
+bool wide_numeric_fits(const LaunchCtx& ctx, int32_t k) {
+  if (k <= 0) return false;
+  const WideGeom g = wide_geom(wide_words(k), wide_budget(ctx), true);
+  return g.val_off <= wide_budget(ctx) && g.vcap >= 64;
+}
+
+cudaError_t launch_symbolic_wide(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                                 const long long* flop, const int32_t* rows, int32_t nrows,
+                                 int32_t* cnt) {
+  if (nrows <= 0) return cudaSuccess;
+  const int words = wide_words(B.n);
+  const WideGeom g = wide_geom(words, wide_budget(ctx), false);
+  cudaError_t e = cudaFuncSetAttribute(k_sym_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.bytes);
+  if (e != cudaSuccess) return e;
+  k_sym_wide<<<wide_grid(ctx, g.bytes, nrows), kWideBlock, g.bytes, ctx.stream>>>(
+      A, B, words, (uint32_t)g.sum_off, flop, rows, nrows, cnt, ctx.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_numeric_wide(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                                const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
+                                int32_t* c_colind, double* c_vals) {
+  if (nrows <= 0) return cudaSuccess;
+  const int words = wide_words(B.n);
+  const WideGeom g = wide_geom(words, wide_budget(ctx), true);
+  cudaError_t e = cudaFuncSetAttribute(k_num_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.bytes);
+  if (e != cudaSuccess) return e;
+  k_num_wide<<<wide_grid(ctx, g.bytes, nrows), kWideBlock, g.bytes, ctx.stream>>>(
+      A, B, words, g.vcap, (uint32_t)g.sum_off, (uint32_t)g.reg_off, (uint32_t)g.val_off, c_rowptr,
+      rows, nrows, c_colind, c_vals, ctx.status);
+  return cudaGetLastError();
+}
+
+}  // namespace kk

@@ -744,43 +744,93 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
   }
 }
 
-// Compressed B: row j as (column >> 5, OR of 1 << (column & 31)) pairs in
-// column order at B's own row offsets, len[j] = number of pairs.  A word whose
-// columns straddle two 32-entry chunks of the row gives two pairs (harmless:
-// every use ORs them).  Rows must be sorted.
-__global__ void k_compress_b(CsrView B, int2* __restrict__ bc, int32_t* __restrict__ len,
-                             unsigned long long* pairs) {
+// Analysis of B, one team of 8 lanes per row: rows strictly ascending?
+// columns inside [0, k)?  And, when bc is given, the compressed rows B_C:
+// row j as (column >> 5, OR of 1 << (column & 31)) pairs in column order at
+// B's own row offsets, len[j] = number of pairs (meaningful only if B turns
+// out sorted).  The team walks the row in chunks of 8 entries; the word being
+// built when a chunk ends is carried into the next chunk, so every word of a
+// sorted row gives exactly one pair.
+constexpr int kAnaBTeam = 8;
+__global__ void k_analyze_b(CsrView B, int32_t* sorted_flag, int* status, int2* __restrict__ bc,
+                            int32_t* __restrict__ len, unsigned long long* pairs) {
+  constexpr int T = kAnaBTeam;
   const int lane = threadIdx.x & 31;
-  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  const unsigned lt = (1u << lane) - 1u;
+  const int tl = lane & (T - 1);
+  const int tbase = lane & ~(T - 1);
+  const unsigned mask = team_mask<T>();
+  const unsigned lt = (1u << tl) - 1u;
+  const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / T;
+  const long long nteams = (long long)gridDim.x * blockDim.x / T;
+  int unsorted = 0, bad = 0;
   unsigned long long tot = 0;
-  for (long long r = w0; r < B.m; r += nw) {
+  if (team0 == 0 && tl == 0 && B.rowptr[0] != 0) bad = 1;
+  for (long long r = team0; r < B.m; r += nteams) {
     const int bs = B.rowptr[r], be = B.rowptr[r + 1];
-    int n = 0;
-    for (int q0 = bs; q0 < be; q0 += 32) {
-      const int q = q0 + lane;
+    if (bs < 0 || be < bs || be > B.nnz) {
+      bad = 1;
+      continue;
+    }
+    int cw = -1, n = 0;
+    uint32_t cm = 0u;
+    for (int q0 = bs; q0 < be; q0 += T) {
+      const int q = q0 + tl;
       const bool valid = q < be;
       const int c = valid ? B.colind[q] : 0;
-      const int w = valid ? (c >> 5) : -1 - lane;  // invalid lanes match nothing
-      uint32_t acc = valid ? (1u << (c & 31)) : 0u;
-      const int wp = __shfl_up_sync(kFull, w, 1);
-      const bool head = valid && (lane == 0 || wp != w);
-      // segmented OR over the lanes of the same word (contiguous: sorted row)
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t v = __shfl_down_sync(kFull, acc, d);
-        const int w2 = __shfl_down_sync(kFull, w, d);
-        if (lane + d < 32 && w2 == w) acc |= v;
+      if (valid) {
+        if ((unsigned)c >= (unsigned)B.n) bad = 1;
+        if (q > bs && B.colind[q - 1] >= c) unsorted = 1;
       }
-      const unsigned hm = __ballot_sync(kFull, head);
-      if (head) bc[bs + n + __popc(hm & lt)] = make_int2(w, (int)acc);
-      n += __popc(hm);
+      if (!bc) continue;
+      const int w = valid ? (c >> 5) : (-2 - tl);  // invalid lanes match nothing
+      uint32_t acc = valid ? (1u << (c & 31)) : 0u;
+      int pw = __shfl_up_sync(mask, w, 1, T);
+      if (tl == 0) pw = cw;
+      const bool head = valid && w != pw;
+#pragma unroll
+      for (int d = 1; d < T; d <<= 1) {
+        const uint32_t v = __shfl_down_sync(mask, acc, d, T);
+        const int w2 = __shfl_down_sync(mask, w, d, T);
+        if (tl + d < T && w2 == w) acc |= v;
+      }
+      // a chunk that starts inside the carried word adds its first segment to it
+      const uint32_t acc0 = __shfl_sync(mask, acc, 0, T);
+      const bool cont0 = __shfl_sync(mask, (int)(valid && !head), 0, T) != 0;
+      if (cont0) cm |= acc0;
+      const unsigned hm = (__ballot_sync(mask, head) >> tbase) & ((1u << T) - 1u);
+      if (hm) {
+        // a new word started: the carried pair is complete
+        if (cm) {
+          if (tl == 0) bc[bs + n] = make_int2(cw, (int)cm);
+          ++n;
+        }
+        const int last = 31 - __clz(hm);
+        if (head && tl != last) bc[bs + n + __popc(hm & lt)] = make_int2(w, (int)acc);
+        n += __popc(hm) - 1;
+        cw = __shfl_sync(mask, w, last, T);
+        cm = __shfl_sync(mask, acc, last, T);
+      }
     }
-    if (lane == 0) len[r] = n;
-    tot += (unsigned long long)n;
+    if (bc) {
+      if (cm) {
+        if (tl == 0) bc[bs + n] = make_int2(cw, (int)cm);
+        ++n;
+      }
+      if (tl == 0) {
+        len[r] = n;
+        tot += (unsigned long long)n;
+      }
+    }
   }
-  if (lane == 0 && tot) atomicAdd(pairs, tot);
+  unsorted = __any_sync(kFull, unsorted);
+  bad = __any_sync(kFull, bad);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(kFull, tot, o);
+  if (lane == 0) {
+    if (unsorted) atomicAnd(sorted_flag, 0);
+    if (bad) set_status(status, KK_ERR_BAD_INDEX);
+    if (tot && pairs) atomicAdd(pairs, tot);
+  }
 }
 
 template <class K>
@@ -844,15 +894,13 @@ cudaError_t num_kept(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
 
 }  // namespace
 
-cudaError_t launch_compress_b(const LaunchCtx& ctx, const CsrView& B, int2* bc, int32_t* len,
-                              unsigned long long* pairs) {
+cudaError_t launch_analyze_b(const LaunchCtx& ctx, const CsrView& B, int32_t* sorted_flag,
+                             int2* bc, int32_t* len, unsigned long long* pairs) {
   if (B.m <= 0) return cudaSuccess;
-  timer_begin(ctx.timer, ctx.stream, "compress_b");
-  long long blocks = ((long long)B.m * 32 + 255) / 256;
-  const long long cap = (long long)ctx.num_sms * 16;
+  long long blocks = ((long long)B.m * kAnaBTeam + 255) / 256;
+  const long long cap = (long long)ctx.num_sms * 8;
   if (blocks > cap) blocks = cap;
-  k_compress_b<<<(int)blocks, 256, 0, ctx.stream>>>(B, bc, len, pairs);
-  timer_end(ctx.timer, ctx.stream);
+  k_analyze_b<<<(int)blocks, 256, 0, ctx.stream>>>(B, sorted_flag, ctx.status, bc, len, pairs);
   return cudaGetLastError();
 }
 
