@@ -14,9 +14,10 @@
 //             values (zeroed first) with global float64 atomics.  The order of
 //             the additions is not fixed, so the values carry the float64 bound
 //             of an unordered sum.
-// Warps take the row's A entries eight at a time and split the flattened
-// (A entry, B entry) products of those eight; each lane issues kWideU loads
-// before it uses them, so every warp keeps several B loads in flight.
+// The CTA walks the row's products (the flattened (A entry, B entry) pairs in
+// storage order) in work items of kItem products that warps claim from a
+// shared counter, so one long B row does not leave the other warps waiting at
+// the row's barrier; each lane issues kWideU loads before it uses them.
 #include "kk_internal.h"
 #include "kk_device.cuh"
 
@@ -24,7 +25,6 @@ namespace kk {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWideChunk = 8;  // A entries per warp chunk
 constexpr int kWideU = 4;      // warp steps whose loads are issued together
 constexpr int kWideBlock = 1024;
 
@@ -53,92 +53,165 @@ inline WideGeom wide_geom(int words, size_t max_smem, bool numeric) {
   return g;
 }
 
-// Lanes 0..7 hold A entry p0 + lane of the chunk: B row start and length.
-// Returns the chunk's product count; incl / base are the lane's inclusive
-// length prefix and B start minus its exclusive prefix.
-__device__ __forceinline__ int wide_chunk_setup(const CsrView& A, const CsrView& B, int p0, int pe,
-                                                int lane, int& incl, int& base, int& bad) {
-  int bs = 0, bl = 0;
-  const int p = p0 + lane;
-  if (lane < kWideChunk && p < pe) {
-    const int j = A.colind[p];
-    if ((unsigned)j < (unsigned)B.m) {
-      bs = B.rowptr[j];
-      bl = B.rowptr[j + 1] - bs;
-    } else {
-      bad = 1;
-    }
-  }
-  incl = team_inclusive_scan<32>(bl, lane, kFull);
-  base = bs - (incl - bl);
-  return __shfl_sync(kFull, incl, kWideChunk - 1);
-}
-
-// Owner (0..7) of flattened product f of the chunk.
-__device__ __forceinline__ int wide_owner(int incl, int f) {
-  int own = 0;
-#pragma unroll
-  for (int step = kWideChunk / 2; step > 0; step >>= 1) {
-    const int v = __shfl_sync(kFull, incl, own + step - 1);
-    if (v <= f) own += step;
-  }
-  return own;
-}
-
 // Exclusive block scan of v (blockDim.x <= 1024); *total receives the sum.
-__device__ __forceinline__ int block_exscan(int v, int* tmp, int* total) {
+template <class T>
+__device__ __forceinline__ T block_exscan(T v, T* tmp, T* total) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
-  const int incl = team_inclusive_scan<32>(v, lane, kFull);
+  T incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T n = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += n;
+  }
   if (lane == 31) tmp[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    const int x = lane < nwarps ? tmp[lane] : 0;
-    const int xi = team_inclusive_scan<32>(x, lane, kFull);
+    const T x = lane < nwarps ? tmp[lane] : T(0);
+    T xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T n = __shfl_up_sync(kFull, xi, o);
+      if (lane >= o) xi += n;
+    }
     tmp[lane] = xi - x;
     if (lane == 31) tmp[32] = xi;
   }
   __syncthreads();
-  const int r = tmp[warp] + incl - v;
+  const T r = tmp[warp] + incl - v;
   *total = tmp[32];
   __syncthreads();
   return r;
 }
 
-// OR the column bits of the products of A entries [pa, pe) into bits (and,
-// with SUM, the summary bits of their words).
-template <bool SUM>
-__device__ __forceinline__ void wide_set_bits(const CsrView& A, const CsrView& B, int pa, int pe,
-                                              uint32_t* bits, uint32_t* sum, int words, int& bad) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
+// Shared scratch of the product walk: the segment's product prefix and B row
+// starts, the work-item counter and the scan buffer.
+constexpr int kSeg = kWideBlock;       // A entries per segment (one per thread)
+constexpr int kItem = 32 * kWideU * 2;  // products per work item
+struct WalkSmem {
+  long long pre[kSeg + 1];
+  int bst[kSeg];
+  long long tmp[33];
+  int next;
+};
+
+// Visit every product A(i,j)*B(j,c) of the A entries [pa, pe) of a row with
+// the whole CTA, balanced to kItem products: the row's A entries are taken
+// kSeg at a time; their products, flattened in storage order, are cut into
+// items of kItem that warps claim from a shared counter; a warp walks its item
+// with lanes over consecutive products, 32 A entries' bounds held in lanes,
+// and issues kWideU steps of loads before using them.  use(c, ab, ok) gets
+// the column (and with VALS the product a*b in float64).  Ends with a barrier.
+template <bool VALS, class Use>
+__device__ __forceinline__ void wide_walk(const CsrView& A, const CsrView& B, int pa, int pe,
+                                          WalkSmem& ws, int& bad, Use use) {
+  const int lane = threadIdx.x & 31;
   const int32_t* __restrict__ bcol = B.colind;
-  for (int p0 = pa + warp * kWideChunk; p0 < pe; p0 += nwarps * kWideChunk) {
-    int incl, base;
-    const int total = wide_chunk_setup(A, B, p0, pe, lane, incl, base, bad);
-    for (int f0 = 0; f0 < total; f0 += 32 * kWideU) {
-      int col[kWideU];
-#pragma unroll
-      for (int u = 0; u < kWideU; ++u) {
-        const int f = f0 + u * 32 + lane;
-        const int own = wide_owner(incl, f);
-        const int qb = __shfl_sync(kFull, base, own);
-        col[u] = f < total ? bcol[qb + f] : -1;
-      }
-#pragma unroll
-      for (int u = 0; u < kWideU; ++u) {
-        const int c = col[u];
-        if (c >= 0) {
-          if ((unsigned)c < (unsigned)(words * 32)) {
-            atomicOr(&bits[c >> 5], 1u << (c & 31));
-            if (SUM) atomicOr(&sum[c >> 10], 1u << ((c >> 5) & 31));
-          } else {
-            bad = 1;
-          }
+  const double* __restrict__ bval = B.vals;
+  for (int s0 = pa; s0 < pe; s0 += kSeg) {
+    const int ns = min(kSeg, pe - s0);
+    {
+      const int t = threadIdx.x;
+      int bs = 0;
+      long long len = 0;
+      if (t < ns) {
+        const int j = A.colind[s0 + t];
+        if ((unsigned)j < (unsigned)B.m) {
+          bs = B.rowptr[j];
+          len = B.rowptr[j + 1] - bs;
+        } else {
+          bad = 1;
         }
       }
+      long long total;
+      const long long ex = block_exscan<long long>(len, ws.tmp, &total);
+      ws.pre[t] = ex;
+      ws.bst[t] = bs;
+      if (t == 0) {
+        ws.pre[ns] = total;
+        ws.next = 0;
+      }
+      __syncthreads();
     }
+    const long long total = ws.pre[ns];
+    for (;;) {
+      int it = 0;
+      if (lane == 0) it = atomicAdd(&ws.next, 1);
+      it = __shfl_sync(kFull, it, 0);
+      const long long fb = (long long)it * kItem;
+      if (fb >= total) break;
+      const int ilen = (int)min((long long)kItem, total - fb);
+      // entry holding product fb: last t with pre[t] <= fb (32-ary search)
+      int lo = 0, hi = ns;
+      while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int cand = lo + lane * step;
+        const bool le = cand < hi && ws.pre[cand] <= fb;
+        const unsigned m = __ballot_sync(kFull, le);
+        const int last = 31 - __clz(m);
+        lo = lo + last * step;
+        hi = min(hi, lo + step);
+      }
+      int done = 0, t0 = lo;
+      while (done < ilen) {
+        // window of A entries t0 .. t0 + 31: starts relative to fb
+        const int tl = t0 + lane;
+        const long long P = tl < ns ? ws.pre[tl] : total;
+        int rel = (int)max(min(P - fb, (long long)0x7fffffff), -(long long)0x7fffffff);
+        if (tl >= ns) rel = 0x7fffffff;
+        const int bsl = tl < ns ? ws.bst[tl] : 0;
+        double al = 0.0;
+        if (VALS && tl < ns) al = A.vals[s0 + tl];
+        const long long wend = t0 + 32 < ns ? ws.pre[t0 + 32] : total;
+        const int lim = (int)min((long long)ilen, wend - fb);
+        for (int g = done; g < lim; g += 32 * kWideU) {
+          int col[kWideU];
+          double ab[kWideU];
+#pragma unroll
+          for (int u = 0; u < kWideU; ++u) {
+            const int f = g + u * 32 + lane;
+            int own = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+              const int v = __shfl_sync(kFull, rel, own + st);
+              if (own + st < 32 && v <= f) own += st;
+            }
+            const int q = __shfl_sync(kFull, bsl, own) + (f - __shfl_sync(kFull, rel, own));
+            const double a = VALS ? __shfl_sync(kFull, al, own) : 0.0;
+            col[u] = -1;
+            ab[u] = 0.0;
+            if (f < lim) {
+              col[u] = bcol[q];
+              if (VALS) ab[u] = a * bval[q];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kWideU; ++u) use(col[u], ab[u]);
+        }
+        done = lim;
+        t0 += 32;
+      }
+    }
+    __syncthreads();
   }
+}
+
+// OR the column bits of the products of A entries [pa, pe) into bits (and,
+// with SUM, the summary bits of their words).  Ends with a barrier.
+template <bool SUM>
+__device__ __forceinline__ void wide_set_bits(const CsrView& A, const CsrView& B, int pa, int pe,
+                                              WalkSmem& ws, uint32_t* bits, uint32_t* sum,
+                                              int words, int& bad) {
+  wide_walk<false>(A, B, pa, pe, ws, bad, [&](int c, double) {
+    if (c >= 0) {
+      if ((unsigned)c < (unsigned)(words * 32)) {
+        atomicOr(&bits[c >> 5], 1u << (c & 31));
+        if (SUM) atomicOr(&sum[c >> 10], 1u << ((c >> 5) & 31));
+      } else {
+        bad = 1;
+      }
+    }
+  });
 }
 
 __global__ void __launch_bounds__(kWideBlock, 1)
@@ -147,6 +220,7 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
   extern __shared__ __align__(16) unsigned char wsm[];
   uint32_t* bits = reinterpret_cast<uint32_t*>(wsm);
   uint32_t* sum = reinterpret_cast<uint32_t*>(wsm + sum_off);
+  __shared__ WalkSmem ws;
   __shared__ int tmp[33];
   const int nsum = words >> 5;
   for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4)
@@ -159,8 +233,7 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
     const bool sparse = flop[i] < (long long)words;  // few words touched: walk the summary
     int c = 0;
     if (sparse) {
-      wide_set_bits<true>(A, B, A.rowptr[i], A.rowptr[i + 1], bits, sum, words, bad);
-      __syncthreads();
+      wide_set_bits<true>(A, B, A.rowptr[i], A.rowptr[i + 1], ws, bits, sum, words, bad);
       for (int s = threadIdx.x; s < nsum; s += blockDim.x) {
         uint32_t m = sum[s];
         sum[s] = 0u;
@@ -173,8 +246,7 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
         }
       }
     } else {
-      wide_set_bits<false>(A, B, A.rowptr[i], A.rowptr[i + 1], bits, sum, words, bad);
-      __syncthreads();
+      wide_set_bits<false>(A, B, A.rowptr[i], A.rowptr[i + 1], ws, bits, sum, words, bad);
       for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4) {
         uint4* q = reinterpret_cast<uint4*>(&bits[w]);
         const uint4 v = *q;
@@ -183,7 +255,7 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
       }
     }
     int tot;
-    block_exscan(c, tmp, &tot);
+    block_exscan<int>(c, tmp, &tot);
     if (threadIdx.x == 0) cnt[i] = tot;
   }
   if (bad) set_status(status, KK_ERR_BAD_INDEX);
@@ -196,11 +268,12 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
   extern __shared__ __align__(16) unsigned char wsm[];
   uint32_t* bits = reinterpret_cast<uint32_t*>(wsm);
   uint32_t* sum = reinterpret_cast<uint32_t*>(wsm + sum_off);
-  uint16_t* wpre16 = reinterpret_cast<uint16_t*>(wsm + reg_off);  // sparse rows
-  uint32_t* gpre = reinterpret_cast<uint32_t*>(wsm + reg_off);    // dense rows
-  uint8_t* wpre8 = wsm + reg_off + (size_t)(words / 8) * 4;       // dense rows
+  uint16_t* wpre16 = reinterpret_cast<uint16_t*>(wsm + reg_off);  // rows with values here
+  uint32_t* gpre = reinterpret_cast<uint32_t*>(wsm + reg_off);    // rows with values in C
+  uint8_t* wpre8 = wsm + reg_off + (size_t)(words / 8) * 4;       // rows with values in C
   double* vals = reinterpret_cast<double*>(wsm + val_off);
   uint16_t* list = reinterpret_cast<uint16_t*>(wsm + val_off);
+  __shared__ WalkSmem ws;
   __shared__ int tmp[33];
   const int nsum = words >> 5;
   const int groups = words >> 3;
@@ -209,10 +282,6 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
   for (int s = threadIdx.x; s < nsum; s += blockDim.x) sum[s] = 0u;
   __syncthreads();
   int bad = 0, mismatch = 0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
-  const int32_t* __restrict__ bcol = B.colind;
-  const double* __restrict__ bval = B.vals;
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int i = rows[r];
     const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
@@ -223,8 +292,7 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
     bool row_bad = false;
     int total;
     if (sparse) {
-      wide_set_bits<true>(A, B, pa, pe, bits, sum, words, bad);
-      __syncthreads();
+      wide_set_bits<true>(A, B, pa, pe, ws, bits, sum, words, bad);
       // ordered list of touched words: summary words in order, bits in order,
       // in rounds of blockDim summary words
       int L = 0;
@@ -232,7 +300,7 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
         const int s = s0 + threadIdx.x;
         uint32_t m = s < nsum ? sum[s] : 0u;
         int t;
-        int pos = L + block_exscan(__popc(m), tmp, &t);
+        int pos = L + block_exscan<int>(__popc(m), tmp, &t);
         L += t;
         if (s < nsum) sum[s] = 0u;
         while (m) {
@@ -254,7 +322,7 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
         const int w = e < L ? (int)list[e] : 0;
         uint32_t m = e < L ? bits[w] : 0u;
         int t;
-        int pos = run + block_exscan(__popc(m), tmp, &t);
+        int pos = run + block_exscan<int>(__popc(m), tmp, &t);
         run += t;
         if (e < L) {
           wpre16[w] = (uint16_t)pos;
@@ -272,15 +340,14 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
       // from C's columns when they are cleared
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) vals[e] = 0.0;
     } else {
-      wide_set_bits<false>(A, B, pa, pe, bits, sum, words, bad);
-      __syncthreads();
+      wide_set_bits<false>(A, B, pa, pe, ws, bits, sum, words, bad);
       const int gpt = (groups + blockDim.x - 1) / blockDim.x;
       const int g0 = threadIdx.x * gpt, g1 = min(groups, g0 + gpt);
       int mine = 0;
       for (int g = g0; g < g1; ++g)
 #pragma unroll
         for (int k = 0; k < 8; ++k) mine += __popc(bits[g * 8 + k]);
-      int run = block_exscan(mine, tmp, &total);
+      int run = block_exscan<int>(mine, tmp, &total);
       for (int g = g0; g < g1; ++g) {
         gpre[g] = (uint32_t)run;
         int in = 0;
@@ -306,44 +373,18 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
     if (row_bad) mismatch = 1;
     __syncthreads();
     // values: rank = prefix of the word + popc(bits below the column)
-    for (int p0 = pa + warp * kWideChunk; p0 < pe; p0 += nwarps * kWideChunk) {
-      int incl, base;
-      const int tot = wide_chunk_setup(A, B, p0, pe, lane, incl, base, bad);
-      const double a_l = (lane < kWideChunk && p0 + lane < pe) ? A.vals[p0 + lane] : 0.0;
-      for (int f0 = 0; f0 < tot; f0 += 32 * kWideU) {
-        int col[kWideU];
-        double prod[kWideU];
-#pragma unroll
-        for (int u = 0; u < kWideU; ++u) {
-          const int f = f0 + u * 32 + lane;
-          const int own = wide_owner(incl, f);
-          const int qb = __shfl_sync(kFull, base, own);
-          const double a = __shfl_sync(kFull, a_l, own);
-          col[u] = -1;
-          prod[u] = 0.0;
-          if (f < tot) {
-            col[u] = bcol[qb + f];
-            prod[u] = a * bval[qb + f];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kWideU; ++u) {
-          const int c = col[u];
-          if (c >= 0 && (unsigned)c < (unsigned)(words * 32)) {
-            const int w = c >> 5;
-            const uint32_t word = bits[w];
-            const int below = __popc(word & ((1u << (c & 31)) - 1u));
-            const int rank = sparse ? (int)wpre16[w] + below
-                                    : (int)gpre[w >> 3] + (int)wpre8[w] + below;
-            if (rank < cnt) {
-              if (sparse) atomicAdd(&vals[rank], prod[u]);
-              else atomicAdd(&c_vals[off + rank], prod[u]);
-            }
-          }
+    wide_walk<true>(A, B, pa, pe, ws, bad, [&](int c, double ab) {
+      if (c >= 0 && (unsigned)c < (unsigned)(words * 32)) {
+        const int w = c >> 5;
+        const uint32_t word = bits[w];
+        const int below = __popc(word & ((1u << (c & 31)) - 1u));
+        const int rank = sparse ? (int)wpre16[w] + below : (int)gpre[w >> 3] + (int)wpre8[w] + below;
+        if (rank < cnt) {
+          if (sparse) atomicAdd(&vals[rank], ab);
+          else atomicAdd(&c_vals[off + rank], ab);
         }
       }
-    }
-    __syncthreads();
+    });
     if (sparse) {
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) c_vals[off + e] = vals[e];
     }
@@ -363,7 +404,8 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
 // Dynamic shared memory available to the wide kernels (their static arrays
 // take the rest of the opt-in limit).
 size_t wide_budget(const LaunchCtx& ctx) {
-  return ctx.max_smem_optin > 1024 ? (size_t)ctx.max_smem_optin - 1024 : 0;
+  const size_t stat = sizeof(WalkSmem) + 33 * sizeof(int) + 512;
+  return (size_t)ctx.max_smem_optin > stat ? (size_t)ctx.max_smem_optin - stat : 0;
 }
 
 int wide_grid(const LaunchCtx& ctx, size_t smem, int nrows) {
