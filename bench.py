@@ -182,20 +182,14 @@ def _events_ms(fn, steps, stream):
     return a.elapsed_time(b) / steps
 
 
-def bench_learned(args, dA, dB, madds, plain_ms, ci, va):
-    """Learned form on the same workload: predictor trained on the GPU from the
-    training families (disjoint from this workload), then learned symbolic +
-    learned numeric per step, timed like the plain step."""
+def _learned_vs_plain(args, dA, dB, madds, plain_ms, ci, va, params, workload):
+    """Learned symbolic + learned numeric per step, with the trained network
+    and without it (rows sized by their flop bound), against the plain step."""
     import torch
-    from paper_2103_11991_gb300 import learned as L
     from paper_2103_11991_gb300 import spgemm as K
-    t0 = time.perf_counter()
-    X, y = L.make_training_set(L.training_pairs(small=False))
-    params, loss = L.train_predictor(X, y, epochs=30)
-    train_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
-    out = {"predictor": {"samples": int(X.shape[0]), "final_loss": loss, "train_s": train_s}}
-    del X, y
+    out = {"workload": workload, "plain": {"ms_per_step": plain_ms,
+                                           "value": 2.0 * madds / (plain_ms * 1e-3) / 1e9}}
     for label, p in (("with_network", params), ("without_network", None)):
         op = K.SpGEMM()
         if p is not None:
@@ -213,8 +207,47 @@ def bench_learned(args, dA, dB, madds, plain_ms, ci, va):
                       "overflow_rows": st["overflow_rows"], "heavy_rows": st["heavy_rows"],
                       "staging_entries": st["staging_entries"]}
         op.close()
-    out["unit"] = "GFLOP/s"
-    out["workload"] = WORKLOAD
+    return out
+
+
+def bench_learned(args, dA, dB, madds, plain_ms, ci, va):
+    """Learned form: predictor trained on the GPU from the training families
+    (disjoint from the evaluation matrices), then timed like the plain step on
+    the R-MAT power-law workload (scale 20, the learned form's own workload) and
+    on the benchmark's stencil workload."""
+    import torch
+    from paper_2103_11991_gb300 import inputs as I
+    from paper_2103_11991_gb300 import learned as L
+    from paper_2103_11991_gb300 import spgemm as K
+    t0 = time.perf_counter()
+    X, y = L.make_training_set(L.training_pairs(small=False))
+    params, loss = L.train_predictor(X, y, epochs=30)
+    train_s = time.perf_counter() - t0
+    out = {"predictor": {"samples": int(X.shape[0]), "final_loss": loss, "train_s": train_s},
+           "unit": "GFLOP/s"}
+    del X, y
+    out["stencil"] = _learned_vs_plain(args, dA, dB, madds, plain_ms, ci, va, params, WORKLOAD)
+    if args.scale == 100:
+        stream = torch.cuda.current_stream()
+        R = I.config_inputs("rmat20")["A"]
+        dR = K.DeviceCSR.from_host(R)
+        del R
+        op = K.SpGEMM()
+        rp, nnz = op.symbolic(dR, dR)
+        cR, vR = op.numeric(dR, dR, rp, nnz)
+        madds_r = op.stats()["flops"]
+
+        def plain_step():
+            r, n = op.symbolic(dR, dR)
+            op.numeric(dR, dR, r, n, cR, vR)
+
+        plain_r = _events_ms(plain_step, 3, stream)
+        op.close()
+        out["rmat20"] = _learned_vs_plain(args, dR, dR, madds_r, plain_r, cR, vR, params,
+                                          "rmat20: R-MAT scale 20, edge factor 16, A*A")
+        out["rmat20"]["nnz_c"] = int(nnz)
+        del cR, vR, dR
+        torch.cuda.empty_cache()
     return out
 
 

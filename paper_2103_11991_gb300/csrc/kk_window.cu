@@ -531,60 +531,76 @@ __device__ __forceinline__ int kept_rank(const u64* table, uint32_t o, bool ok, 
   return member ? min(r, kWindowMaxNnz) : kWindowMaxNnz;
 }
 
-// Value pass over one chunk of at most 32 A entries (ainfo: B row start and
-// length, A value as two 32-bit halves; entries past the chunk have length
-// 0).  Batches of kWinBatch entries: every lane loads its products of the
-// batch, ranks them, then the batch's updates go in entry order; lanes without
-// a product update the spare slot, so nothing branches per entry.
+// One batch of NB A entries of a chunk (ainfo: B row start and length, A
+// value as two 32-bit halves; entries past the chunk have length 0): every
+// lane loads its products of the batch and ranks them, then the batch's
+// updates go in entry order; lanes without a product update the spare slot,
+// so nothing branches per entry.
+template <int NB, bool DFM, bool PROBE>
+__device__ __forceinline__ void kept_batch(const int4* ainfo, int t0, int lo_c, const u64* table,
+                                           u64* vacc, const int32_t* __restrict__ bcol,
+                                           const float2* __restrict__ bspl,
+                                           const double* __restrict__ bval, int lane,
+                                           int& missing) {
+  float2 bv[NB];
+  int rk[NB];
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int2 in = *reinterpret_cast<const int2*>(&ainfo[t0 + u]);
+    const bool ok = lane < in.y;
+    const int q = in.x + lane;
+    int c = 0;
+    bv[u] = make_float2(0.f, 0.f);
+    if (ok) {
+      c = bcol[q];
+      if (DFM) {
+        bv[u] = bspl[q];
+      } else {
+        const long long bb = __double_as_longlong(bval[q]);
+        bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)), __int_as_float((int)(bb >> 32)));
+      }
+    }
+    rk[u] = kept_rank<PROBE>(table, (uint32_t)(c - lo_c), ok, missing);
+  }
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
+    if (DFM) {
+      DF a, b;
+      a.hi = __int_as_float(az.x);
+      a.lo = __int_as_float(az.y);
+      b.hi = bv[u].x;
+      b.lo = bv[u].y;
+      DF s = df_unpack(vacc[rk[u]]);
+      df_fma(s, a, b);
+      vacc[rk[u]] = df_pack(s);
+    } else {
+      const double x = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
+      const double y = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
+                                            (unsigned)__float_as_int(bv[u].x));
+      double* v = reinterpret_cast<double*>(&vacc[rk[u]]);
+      *v = fma(x, y, *v);
+    }
+    __syncwarp();  // this A entry's updates are visible before the next one's
+  }
+}
+
+// Value pass over one chunk of at most 32 A entries: batches of kWinBatch,
+// the tail in a batch of 4 or 8.
 template <bool DFM, bool PROBE>
 __device__ __forceinline__ void kept_chunk(const int4* ainfo, int nch, int lo_c, const u64* table,
                                            u64* vacc, const int32_t* __restrict__ bcol,
                                            const float2* __restrict__ bspl,
                                            const double* __restrict__ bval, int lane,
                                            int& missing) {
-  for (int t0 = 0; t0 < nch; t0 += kWinBatch) {
-    float2 bv[kWinBatch];
-    int rk[kWinBatch];
-#pragma unroll
-    for (int u = 0; u < kWinBatch; ++u) {
-      const int2 in = *reinterpret_cast<const int2*>(&ainfo[t0 + u]);
-      const bool ok = lane < in.y;
-      const int q = in.x + lane;
-      int c = 0;
-      bv[u] = make_float2(0.f, 0.f);
-      if (ok) {
-        c = bcol[q];
-        if (DFM) {
-          bv[u] = bspl[q];
-        } else {
-          const long long bb = __double_as_longlong(bval[q]);
-          bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)), __int_as_float((int)(bb >> 32)));
-        }
-      }
-      rk[u] = kept_rank<PROBE>(table, (uint32_t)(c - lo_c), ok, missing);
-    }
-#pragma unroll
-    for (int u = 0; u < kWinBatch; ++u) {
-      const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
-      if (DFM) {
-        DF a, b;
-        a.hi = __int_as_float(az.x);
-        a.lo = __int_as_float(az.y);
-        b.hi = bv[u].x;
-        b.lo = bv[u].y;
-        DF s = df_unpack(vacc[rk[u]]);
-        df_fma(s, a, b);
-        vacc[rk[u]] = df_pack(s);
-      } else {
-        const double x = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
-        const double y = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
-                                              (unsigned)__float_as_int(bv[u].x));
-        double* v = reinterpret_cast<double*>(&vacc[rk[u]]);
-        *v = fma(x, y, *v);
-      }
-      __syncwarp();  // this A entry's updates are visible before the next one's
-    }
-  }
+  int t0 = 0;
+  for (; t0 + kWinBatch <= nch; t0 += kWinBatch)
+    kept_batch<kWinBatch, DFM, PROBE>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+  const int rem = nch - t0;
+  if (rem > 4)
+    kept_batch<kWinBatch, DFM, PROBE>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+  else if (rem > 0)
+    kept_batch<4, DFM, PROBE>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
 }
 
 // Value pass for B rows longer than 32: one A entry at a time, lanes stride
@@ -623,42 +639,78 @@ __device__ __forceinline__ void kept_chunk_long(const int4* ainfo, int nch, int 
   }
 }
 
-template <bool DFM, bool PROBE>
-__device__ __forceinline__ void kept_values(int pa, int pe, const int32_t* __restrict__ acol,
+// Chunk setup: lane t holds A entry p0 + t (B row start, length, A value
+// split for DF32 or as raw float64 halves).  Returns 1 if the lane's value is
+// outside the DF32 window.
+__device__ __forceinline__ int kept_info(int p0, int pe, const int32_t* __restrict__ acol,
+                                         const double* __restrict__ aval,
+                                         const int32_t* __restrict__ brp, int lane, int4& info,
+                                         DF& ad, double& a) {
+  const int p = p0 + lane;
+  info = make_int4(0, 0, 0, 0);
+  a = 0.0;
+  if (p < pe) {
+    const int j = acol[p];
+    info.x = brp[j];
+    info.y = brp[j + 1] - info.x;
+    a = aval[p];
+  }
+  return df_split(a, ad) ? 0 : 1;
+}
+
+template <bool PROBE>
+__device__ __forceinline__ void kept_store_and_run(int4 info, const DF& ad, double a, bool df,
+                                                   int4* ainfo, int nch, int lo_c,
+                                                   const u64* table, u64* vacc,
+                                                   const int32_t* __restrict__ bcol,
+                                                   const float2* __restrict__ bspl,
+                                                   const double* __restrict__ bval, int lane,
+                                                   int& missing) {
+  if (df) {
+    info.z = __float_as_int(ad.hi);
+    info.w = __float_as_int(ad.lo);
+  } else {
+    const long long ab = __double_as_longlong(a);
+    info.z = (int)(ab & 0xffffffffll);
+    info.w = (int)(ab >> 32);
+  }
+  ainfo[lane] = info;
+  __syncwarp();
+  const bool shrt = __reduce_max_sync(kFull, (unsigned)info.y) <= 32u;
+  if (df) {
+    if (shrt) kept_chunk<true, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+    else kept_chunk_long<true, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+  } else {
+    if (shrt) kept_chunk<false, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+    else kept_chunk_long<false, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+  }
+  __syncwarp();
+}
+
+// Value pass of a row; returns whether it ran in DF32.  Rows of at most 32 A
+// entries decide the arithmetic from their own split values; longer rows
+// check all their values first.
+template <bool PROBE>
+__device__ __forceinline__ bool kept_values(int pa, int pe, bool df_all,
+                                            const int32_t* __restrict__ acol,
                                             const double* __restrict__ aval,
                                             const int32_t* __restrict__ brp, int4* ainfo, int lo_c,
                                             const u64* table, u64* vacc,
                                             const int32_t* __restrict__ bcol,
                                             const float2* __restrict__ bspl,
                                             const double* __restrict__ bval, int lane, int& missing) {
+  bool df = df_all;
+  if (df_all && pe - pa > 32) df = row_df_ok<32>(aval, pa, pe, lane, kFull);
   for (int p0 = pa; p0 < pe; p0 += 32) {
-    const int p = p0 + lane;
-    int4 info = make_int4(0, 0, 0, 0);
-    if (p < pe) {
-      const int j = acol[p];
-      info.x = brp[j];
-      info.y = brp[j + 1] - info.x;
-      const double a = aval[p];
-      if (DFM) {
-        DF ad;
-        df_split(a, ad);
-        info.z = __float_as_int(ad.hi);
-        info.w = __float_as_int(ad.lo);
-      } else {
-        const long long ab = __double_as_longlong(a);
-        info.z = (int)(ab & 0xffffffffll);
-        info.w = (int)(ab >> 32);
-      }
-    }
-    ainfo[lane] = info;
-    __syncwarp();
-    const int nch = min(32, pe - p0);
-    if (__reduce_max_sync(kFull, (unsigned)info.y) <= 32u)
-      kept_chunk<DFM, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
-    else
-      kept_chunk_long<DFM, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
-    __syncwarp();
+    int4 info;
+    DF ad;
+    double a;
+    const int bad = kept_info(p0, pe, acol, aval, brp, lane, info, ad, a);
+    if (df_all && pe - pa <= 32) df = __any_sync(kFull, bad) == 0;
+    kept_store_and_run<PROBE>(info, ad, a, df, ainfo, min(32, pe - p0), lo_c, table, vacc, bcol,
+                              bspl, bval, lane, missing);
   }
+  return df;
 }
 
 __global__ void __launch_bounds__(kKeptWarps * 32, 4)
@@ -674,6 +726,8 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
   u64* vacc = reinterpret_cast<u64*>(base + KeptGeom::kValOff);
   int4* ainfo = reinterpret_cast<int4*>(base + KeptGeom::kInfoOff);
   const bool df_all = arith == kArithDF32 && *b_range_bad == 0;
+  for (int s = lane; s < kKeptSlots; s += 32) table[s] = kKeptEmpty;
+  __syncwarp();
   const int per_cta = (nrows + gridDim.x - 1) / gridDim.x;
   const int r_begin = blockIdx.x * per_cta;
   const int r_end = min(nrows, r_begin + per_cta);
@@ -688,10 +742,10 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
     const int64_t off = c_rowptr[i];
     const int cnt = (int)(c_rowptr[i + 1] - off);
     const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
-    for (int s = lane; s < kKeptSlots; s += 32) table[s] = kKeptEmpty;
-    for (int e = lane; e < kWindowMaxNnz; e += 32) vacc[e] = 0ull;
+    for (int e = lane; e < cnt && e < kWindowMaxNnz; e += 32) vacc[e] = 0ull;
     __syncwarp();
     int run = 0, bad = 0, probe = 0;
+    uint32_t slot0 = kKeptSlots, slot1 = kKeptSlots;  // slots this lane filled
     for (int e0 = 0; e0 < L; e0 += 32) {
       const int e = e0 + lane;
       uint32_t w = 0u, m = 0u;
@@ -709,8 +763,13 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
         bool placed = false;
         for (int k = 0; k < kKeptSlots && !placed; ++k) {
           placed = atomicCAS(&table[s], kKeptEmpty, entry) == kKeptEmpty;
-          if (!placed) probe = 1;
-          s = (s + 1) & (kKeptSlots - 1);
+          if (placed) {
+            if (e0 == 0) slot0 = s;
+            else slot1 = s;
+          } else {
+            probe = 1;
+            s = (s + 1) & (kKeptSlots - 1);
+          }
         }
         if (!placed) bad = 1;
         while (m) {
@@ -725,21 +784,21 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
     probe = __any_sync(kFull, probe);
     __syncwarp();
     // arithmetic of this row: DF32 unless a value of the row is outside its window
-    const bool df = df_all && row_df_ok<32>(A.vals, pa, pe, lane, kFull);
     int missing = 0;
-    if (df) {
-      if (probe) kept_values<true, true>(pa, pe, A.colind, A.vals, B.rowptr, ainfo, lo_c, table, vacc, B.colind, bspl, B.vals, lane, missing);
-      else kept_values<true, false>(pa, pe, A.colind, A.vals, B.rowptr, ainfo, lo_c, table, vacc, B.colind, bspl, B.vals, lane, missing);
-    } else {
-      if (probe) kept_values<false, true>(pa, pe, A.colind, A.vals, B.rowptr, ainfo, lo_c, table, vacc, B.colind, bspl, B.vals, lane, missing);
-      else kept_values<false, false>(pa, pe, A.colind, A.vals, B.rowptr, ainfo, lo_c, table, vacc, B.colind, bspl, B.vals, lane, missing);
-    }
+    const bool df =
+        probe ? kept_values<true>(pa, pe, df_all, A.colind, A.vals, B.rowptr, ainfo, lo_c, table,
+                                  vacc, B.colind, bspl, B.vals, lane, missing)
+              : kept_values<false>(pa, pe, df_all, A.colind, A.vals, B.rowptr, ainfo, lo_c, table,
+                                   vacc, B.colind, bspl, B.vals, lane, missing);
     if (missing) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
     const int n = min(cnt, kWindowMaxNnz);
     for (int e = lane; e < n; e += 32) {
       const u64 v = vacc[e];
       c_vals[off + e] = df ? df_to_double(df_unpack(v)) : __longlong_as_double((long long)v);
     }
+    // empty the slots this row filled for the next row
+    if (slot0 < kKeptSlots) table[slot0] = kKeptEmpty;
+    if (slot1 < kKeptSlots) table[slot1] = kKeptEmpty;
     __syncwarp();
   }
 }
