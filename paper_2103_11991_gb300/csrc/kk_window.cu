@@ -67,25 +67,39 @@ struct NumWinGeom : WinWords<W> {
   static constexpr size_t kWarpBytes = kInfoOff + 32 * 16;
 };
 
+// Compressed row bounds of A entry p (0, 0 past the row's end).
+__device__ __forceinline__ void bc_bounds(int p, int pe, const int32_t* __restrict__ acol,
+                                          const int32_t* __restrict__ brp,
+                                          const int32_t* __restrict__ bclen, int& x, int& y) {
+  x = 0;
+  y = 0;
+  if (p < pe) {
+    const int j = acol[p];
+    x = brp[j];
+    y = bclen[j];
+  }
+}
+
 // OR the compressed rows B_C(j,:) of the entries [pa, pe) of A(i,:) into the
 // window whose word 0 is column word lo_w; the first setter of a word also sets
 // its summary bit.  Lanes take the pairs of 32 / G A entries at a time, G the
-// power of two that covers the longest compressed row of the chunk.
-template <int WORDS>
+// power of two that covers the longest compressed row of the chunk.  x0 / y0:
+// the lane's bounds for the first chunk, already loaded (PRE), else loaded here.
+template <int WORDS, bool PRE = false>
 __device__ __forceinline__ void bc_set_bits(uint32_t* bits, uint32_t* sum, int lo_w, int pa, int pe,
                                             const int32_t* __restrict__ acol,
                                             const int32_t* __restrict__ brp,
                                             const int2* __restrict__ bc,
                                             const int32_t* __restrict__ bclen, int lane,
-                                            int* status) {
+                                            int* status, int x0 = 0, int y0 = 0) {
   int bad = 0;
   for (int p0 = pa; p0 < pe; p0 += 32) {
-    const int p = p0 + lane;
-    int x = 0, y = 0;
-    if (p < pe) {
-      const int j = acol[p];
-      x = brp[j];
-      y = bclen[j];
+    int x, y;
+    if (PRE && p0 == pa) {
+      x = x0;
+      y = y0;
+    } else {
+      bc_bounds(p0 + lane, pe, acol, brp, bclen, x, y);
     }
     const int nch = min(32, pe - p0);
     const unsigned maxlen = __reduce_max_sync(kFull, (unsigned)y);
@@ -199,12 +213,38 @@ k_sym_window(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ row_
   const int r_begin = blockIdx.x * per_cta;
   const int r_end = min(nrows, r_begin + per_cta);
   int kept = 0;
-  for (int r = r_begin + warp; r < r_end; r += kWinWarps) {
-    const int i = rows[r];
-    const int lo_w = row_lo[i] >> 5;
-    bc_set_bits<WORDS>(bits, sum, lo_w, A.rowptr[i], A.rowptr[i + 1], A.colind, B.rowptr, bcomp.bc,
-                       bcomp.len, lane, status);
+  // Rows are software-pipelined: while a row is processed, the next row's
+  // bounds and then its first chunk of compressed-row bounds are loaded, so
+  // the chain row id -> A row -> A columns -> B_C bounds is off the critical
+  // path (the kernel is bound by those dependent loads otherwise).
+  int r = r_begin + warp;
+  int i = 0, pa = 0, pe = 0, lo = 0, x = 0, y = 0, i_n = -1;
+  if (r < r_end) {
+    i = rows[r];
+    pa = A.rowptr[i];
+    pe = A.rowptr[i + 1];
+    lo = row_lo[i];
+    bc_bounds(pa + lane, pe, A.colind, B.rowptr, bcomp.len, x, y);
+    if (r + kWinWarps < r_end) i_n = rows[r + kWinWarps];
+  }
+  for (; r < r_end; r += kWinWarps) {
+    int pa_n = 0, pe_n = 0, lo_n = 0;
+    if (i_n >= 0) {
+      pa_n = A.rowptr[i_n];
+      pe_n = A.rowptr[i_n + 1];
+      lo_n = row_lo[i_n];
+    }
+    const int i_nn = r + 2 * kWinWarps < r_end ? rows[r + 2 * kWinWarps] : -1;
+    bc_set_bits<WORDS, true>(bits, sum, lo >> 5, pa, pe, A.colind, B.rowptr, bcomp.bc, bcomp.len,
+                             lane, status, x, y);
+    int j_n = -1;
+    if (i_n >= 0 && pa_n + lane < pe_n) j_n = A.colind[pa_n + lane];
     const int L = window_list<SUMS>(sum, list, kCacheWords, lane);
+    int x_n = 0, y_n = 0;
+    if (j_n >= 0) {
+      x_n = B.rowptr[j_n];
+      y_n = bcomp.len[j_n];
+    }
     int c = 0;
     if (L <= kCacheWords) {
       for (int e = lane; e < L; e += 32) {
@@ -227,6 +267,13 @@ k_sym_window(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ row_
     }
     kept += (cache.n && L <= kCacheWords) ? 1 : 0;
     __syncwarp();
+    i = i_n;
+    pa = pa_n;
+    pe = pe_n;
+    lo = lo_n;
+    x = x_n;
+    y = y_n;
+    i_n = i_nn;
   }
   if (lane == 0 && kept) atomicAdd(cache.kept, (unsigned long long)kept);
 }
