@@ -206,3 +206,16 @@ def test_errors_reported():
         op.numeric(K.DeviceCSR.from_host(A2), dB, rp, nnz)
     assert e.value.status == 4
     op.close()
+
+
+@pytest.mark.parametrize("tier", [1, 2])
+def test_very_wide_k_uses_hash_and_chunk_tiers(tier):
+    # k beyond the wide tier's shared-memory bit vector: the CTA hash and the
+    # chunked dense kernels take the CTA and dense bins
+    k = 2_000_000
+    A = I.random_rows(40, 300, 20, 60, seed=21)
+    B = I.random_rows(300, k, 30, 90, seed=22)
+    rp, ci, va, _, st = run_gpu(A, B, force_tier=tier)
+    check_against_oracle(A, B, rp, ci, va)
+    key = "num_cta_rows" if tier == 1 else "num_dense_rows"
+    assert st[key] > 0
