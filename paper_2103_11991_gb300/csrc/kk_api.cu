@@ -1231,7 +1231,8 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
   if (m > 0) {
     if ((st = analyze_b(h, bv)) != KK_OK) return st;
     cudaError_t e = launch_learned_analyze(
-        ctx, av, bv, &dm->sorted, h->have_pred ? h->d_params.as<float>() : nullptr, h->quantile,
+        ctx, av, bv, &dm->sorted, h->opt.use_window, h->have_pred ? h->d_params.as<float>() : nullptr,
+        h->quantile,
         h->have_pred ? 1 : 0, h->d_flop.as<long long>(), h->d_rowlo.as<int32_t>(),
         h->d_span.as<int32_t>(), h->d_lbin.as<uint8_t>(), h->d_cap.as<int32_t>(), &dm->total_flop);
     if (e != cudaSuccess) return cuda_fail(h, e, "learned analyze");
@@ -1286,10 +1287,10 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
               ? launch_onepass(ctx, 5 + c, av, bv, h->d_bsplit.as<float2>(), &dm->range_bad, arith,
                                h->d_soff.as<int64_t>(), lrows, n, h->d_scol.as<int32_t>(),
                                h->d_sval.as<double>(), h->d_cnt.as<int32_t>())
-              : launch_onepass_window(ctx, c - kOnepassClasses, av, bv, bcomp, h->d_bsplit.as<float2>(),
-                                      &dm->range_bad, arith, h->d_soff.as<int64_t>(), h->d_cap.as<int32_t>(),
-                                      lrows, n, h->d_scol.as<int32_t>(), h->d_sval.as<double>(),
-                                      h->d_cnt.as<int32_t>());
+              : launch_onepass_table(ctx, av, bv, bcomp, h->d_bsplit.as<float2>(), &dm->range_bad,
+                                     arith, h->d_soff.as<int64_t>(), h->d_cap.as<int32_t>(), lrows, n,
+                                     h->d_scol.as<int32_t>(), h->d_sval.as<double>(),
+                                     h->d_cnt.as<int32_t>());
       if (e != cudaSuccess) return cuda_fail(h, e, "one-pass launch");
     }
     heavy = lstart[kLearnedHeavy + 1] - lstart[kLearnedHeavy];

@@ -145,8 +145,15 @@ cudaError_t launch_onepass_window(const LaunchCtx& ctx, int32_t wclass, const Cs
                                   const int32_t* b_range_bad, int32_t arith, const int64_t* soff,
                                   const int32_t* cap, const int32_t* rows, int32_t nrows,
                                   int32_t* scol, double* sval, int32_t* cnt_out);
+// Speculative one-pass for window rows through a word table (kk_onepass.cu).
+cudaError_t launch_onepass_table(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                                 const BComp& bcomp, const float2* b_split,
+                                 const int32_t* b_range_bad, int32_t arith, const int64_t* soff,
+                                 const int32_t* cap, const int32_t* rows, int32_t nrows,
+                                 int32_t* scol, double* sval, int32_t* cnt_out);
 cudaError_t launch_learned_analyze(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
-                                   const int32_t* b_sorted, const float* params, float quantile,
+                                   const int32_t* b_sorted, int32_t use_window,
+                                   const float* params, float quantile,
                                    int32_t use_pred, long long* flop, int32_t* row_lo,
                                    int32_t* row_span, uint8_t* lbin, int32_t* cap,
                                    unsigned long long* total_flop);

@@ -16,7 +16,7 @@ constexpr int kLearnedBlock = 128;
 // capacity class, [kOnepassClasses, kLearnedHeavy) = window one-pass of that
 // window class, kLearnedHeavy = heavy (plain path), 0xFF = no products.
 __global__ void __launch_bounds__(kLearnedBlock)
-k_learned_analyze(CsrView A, CsrView B, const int32_t* __restrict__ b_sorted,
+k_learned_analyze(CsrView A, CsrView B, const int32_t* __restrict__ b_sorted, int32_t use_window,
                   const float* __restrict__ params, float quantile, int32_t use_pred,
                   long long* __restrict__ flop, int32_t* __restrict__ row_lo,
                   int32_t* __restrict__ row_span, uint8_t* __restrict__ lbin,
@@ -112,7 +112,7 @@ k_learned_analyze(CsrView A, CsrView B, const int32_t* __restrict__ b_sorted,
     uint8_t lb = (uint8_t)kLearnedHeavy;
     if (sorted && c < kOnepassClasses) {
       lb = (uint8_t)c;  // warp hash one-pass
-      for (int w = 0; w < kNumWindowClasses; ++w) {
+      for (int w = 0; use_window && w < kNumWindowClasses; ++w) {  // needs B_C
         if (span <= window_bits(w) && (long long)window_bits(w) <= (long long)kWindowFlopRatio * f) {
           lb = (uint8_t)(kOnepassClasses + w);  // window one-pass
           break;
@@ -179,14 +179,16 @@ int grid1(long long n, int block, int cap) {
 }  // namespace
 
 cudaError_t launch_learned_analyze(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
-                                   const int32_t* b_sorted, const float* params, float quantile,
+                                   const int32_t* b_sorted, int32_t use_window,
+                                   const float* params, float quantile,
                                    int32_t use_pred, long long* flop, int32_t* row_lo,
                                    int32_t* row_span, uint8_t* lbin, int32_t* cap,
                                    unsigned long long* total_flop) {
   if (A.m <= 0) return cudaSuccess;
   timer_begin(ctx.timer, ctx.stream, "learned_analyze");
   k_learned_analyze<<<grid1(A.m, kLearnedBlock, ctx.num_sms * 16), kLearnedBlock, 0, ctx.stream>>>(
-      A, B, b_sorted, params, quantile, use_pred, flop, row_lo, row_span, lbin, cap, total_flop,
+      A, B, b_sorted, use_window, params, quantile, use_pred, flop, row_lo, row_span, lbin, cap,
+      total_flop,
       ctx.status);
   timer_end(ctx.timer, ctx.stream);
   return cudaGetLastError();

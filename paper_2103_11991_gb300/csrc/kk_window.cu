@@ -24,6 +24,7 @@
 #include "kk_internal.h"
 #include "kk_rowops.cuh"
 #include "kk_visit.cuh"
+#include "kk_kept.cuh"
 
 namespace kk {
 namespace {
@@ -209,15 +210,16 @@ k_sym_window(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ row_
     *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
   for (int w = lane; w < SUMS; w += 32) sum[w] = 0u;
   __syncwarp();
-  const int per_cta = (nrows + gridDim.x - 1) / gridDim.x;
-  const int r_begin = blockIdx.x * per_cta;
-  const int r_end = min(nrows, r_begin + per_cta);
+  // Rows are dealt to warps round-robin over the whole grid, so the rows in
+  // flight at any time are neighbours and the B rows they share stay in L2.
+  const int nw = gridDim.x * kWinWarps;
+  const int r_end = nrows;
   int kept = 0;
   // Rows are software-pipelined: while a row is processed, the next row's
   // bounds and then its first chunk of compressed-row bounds are loaded, so
   // the chain row id -> A row -> A columns -> B_C bounds is off the critical
   // path (the kernel is bound by those dependent loads otherwise).
-  int r = r_begin + warp;
+  int r = blockIdx.x * kWinWarps + warp;
   int i = 0, pa = 0, pe = 0, lo = 0, x = 0, y = 0, i_n = -1;
   if (r < r_end) {
     i = rows[r];
@@ -225,16 +227,16 @@ k_sym_window(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ row_
     pe = A.rowptr[i + 1];
     lo = row_lo[i];
     bc_bounds(pa + lane, pe, A.colind, B.rowptr, bcomp.len, x, y);
-    if (r + kWinWarps < r_end) i_n = rows[r + kWinWarps];
+    if (r + nw < r_end) i_n = rows[r + nw];
   }
-  for (; r < r_end; r += kWinWarps) {
+  for (; r < r_end; r += nw) {
     int pa_n = 0, pe_n = 0, lo_n = 0;
     if (i_n >= 0) {
       pa_n = A.rowptr[i_n];
       pe_n = A.rowptr[i_n + 1];
       lo_n = row_lo[i_n];
     }
-    const int i_nn = r + 2 * kWinWarps < r_end ? rows[r + 2 * kWinWarps] : -1;
+    const int i_nn = r + 2 * nw < r_end ? rows[r + 2 * nw] : -1;
     bc_set_bits<WORDS, true>(bits, sum, lo >> 5, pa, pe, A.colind, B.rowptr, bcomp.bc, bcomp.len,
                              lane, status, x, y);
     int j_n = -1;
@@ -323,15 +325,13 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
   const int32_t* __restrict__ bcol = B.colind;
   const double* __restrict__ bval = B.vals;
   if (nrows_dev) nrows = *nrows_dev;
-  const int per_cta = (nrows + gridDim.x - 1) / gridDim.x;
-  const int r_begin = blockIdx.x * per_cta;
-  const int r_end = min(nrows, r_begin + per_cta);
-  if (r_begin + warp >= r_end) return;  // warps share no shared memory or barrier
+  const int nw = gridDim.x * kWinWarps;  // rows dealt round-robin over the grid
+  if (blockIdx.x * kWinWarps + warp >= nrows) return;  // warps share no shared memory or barrier
   for (int w = lane * 4; w < WORDS; w += 128)
     *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
   for (int w = lane; w < SUMS; w += 32) sum[w] = 0u;
   __syncwarp();
-  for (int r = r_begin + warp; r < r_end; r += kWinWarps) {
+  for (int r = blockIdx.x * kWinWarps + warp; r < nrows; r += nw) {
     const int i = rows[r];
     const int lo_w = row_lo[i] >> 5;
     const int lo_c = lo_w * 32;
@@ -549,216 +549,12 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
 // 32..47) and the word index (48..63).  Rows without kept structure are
 // appended to `left` for k_num_window.
 constexpr int kKeptWarps = 8;
-constexpr int kKeptSlots = 256;
-constexpr u64 kKeptEmpty = ~0ull;
 struct KeptGeom {
   // table u64[kKeptSlots] | vacc u64[kWindowMaxNnz + 2] | ainfo int4[32]
   static constexpr size_t kValOff = (size_t)kKeptSlots * 8;
   static constexpr size_t kInfoOff = al16(kValOff + (size_t)(kWindowMaxNnz + 2) * 8);
   static constexpr size_t kWarpBytes = kInfoOff + 32 * 16;
 };
-
-// Rank of column o (relative to the row's first word) through the table, or
-// the spare slot kWindowMaxNnz when o is not a column of the row.
-template <bool PROBE>
-__device__ __forceinline__ int kept_rank(const u64* table, uint32_t o, bool ok, int& missing) {
-  const uint32_t w = o >> 5;
-  uint32_t s = w & (kKeptSlots - 1);
-  u64 e = table[s];
-  if (PROBE) {
-    for (int k = 0; k < kKeptSlots && e != kKeptEmpty && (uint32_t)(e >> 48) != w; ++k) {
-      s = (s + 1) & (kKeptSlots - 1);
-      e = table[s];
-    }
-  }
-  const uint32_t word = (uint32_t)e;
-  const bool member = ok && (uint32_t)(e >> 48) == w && ((word >> (o & 31)) & 1u);
-  if (ok && !member) missing = 1;
-  const int r = (int)((e >> 32) & 0xFFFFu) + __popc(word & ((1u << (o & 31)) - 1u));
-  return member ? min(r, kWindowMaxNnz) : kWindowMaxNnz;
-}
-
-// One batch of NB A entries of a chunk (ainfo: B row start and length, A
-// value as two 32-bit halves; entries past the chunk have length 0): every
-// lane loads its products of the batch and ranks them, then the batch's
-// updates go in entry order; lanes without a product update the spare slot,
-// so nothing branches per entry.
-template <int NB, bool DFM, bool PROBE>
-__device__ __forceinline__ void kept_batch(const int4* ainfo, int t0, int lo_c, const u64* table,
-                                           u64* vacc, const int32_t* __restrict__ bcol,
-                                           const float2* __restrict__ bspl,
-                                           const double* __restrict__ bval, int lane,
-                                           int& missing) {
-  float2 bv[NB];
-  int rk[NB];
-#pragma unroll
-  for (int u = 0; u < NB; ++u) {
-    const int2 in = *reinterpret_cast<const int2*>(&ainfo[t0 + u]);
-    const bool ok = lane < in.y;
-    const int q = in.x + lane;
-    int c = 0;
-    bv[u] = make_float2(0.f, 0.f);
-    if (ok) {
-      c = bcol[q];
-      if (DFM) {
-        bv[u] = bspl[q];
-      } else {
-        const long long bb = __double_as_longlong(bval[q]);
-        bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)), __int_as_float((int)(bb >> 32)));
-      }
-    }
-    rk[u] = kept_rank<PROBE>(table, (uint32_t)(c - lo_c), ok, missing);
-  }
-#pragma unroll
-  for (int u = 0; u < NB; ++u) {
-    const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
-    if (DFM) {
-      DF a, b;
-      a.hi = __int_as_float(az.x);
-      a.lo = __int_as_float(az.y);
-      b.hi = bv[u].x;
-      b.lo = bv[u].y;
-      DF s = df_unpack(vacc[rk[u]]);
-      df_fma(s, a, b);
-      vacc[rk[u]] = df_pack(s);
-    } else {
-      const double x = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
-      const double y = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
-                                            (unsigned)__float_as_int(bv[u].x));
-      double* v = reinterpret_cast<double*>(&vacc[rk[u]]);
-      *v = fma(x, y, *v);
-    }
-    __syncwarp();  // this A entry's updates are visible before the next one's
-  }
-}
-
-// Value pass over one chunk of at most 32 A entries: batches of kWinBatch,
-// the tail in a batch of 4 or 8.
-template <bool DFM, bool PROBE>
-__device__ __forceinline__ void kept_chunk(const int4* ainfo, int nch, int lo_c, const u64* table,
-                                           u64* vacc, const int32_t* __restrict__ bcol,
-                                           const float2* __restrict__ bspl,
-                                           const double* __restrict__ bval, int lane,
-                                           int& missing) {
-  int t0 = 0;
-  for (; t0 + kWinBatch <= nch; t0 += kWinBatch)
-    kept_batch<kWinBatch, DFM, PROBE>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
-  const int rem = nch - t0;
-  if (rem > 4)
-    kept_batch<kWinBatch, DFM, PROBE>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
-  else if (rem > 0)
-    kept_batch<4, DFM, PROBE>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
-}
-
-// Value pass for B rows longer than 32: one A entry at a time, lanes stride
-// the B row.
-template <bool DFM, bool PROBE>
-__device__ __forceinline__ void kept_chunk_long(const int4* ainfo, int nch, int lo_c,
-                                                const u64* table, u64* vacc,
-                                                const int32_t* __restrict__ bcol,
-                                                const float2* __restrict__ bspl,
-                                                const double* __restrict__ bval, int lane,
-                                                int& missing) {
-  for (int t = 0; t < nch; ++t) {
-    const int4 in = ainfo[t];
-    for (int q0 = 0; q0 < in.y; q0 += 32) {
-      const int q = in.x + q0 + lane;
-      const bool ok = q0 + lane < in.y;
-      const int c = ok ? bcol[q] : 0;
-      const int rank = kept_rank<PROBE>(table, (uint32_t)(c - lo_c), ok, missing);
-      if (DFM) {
-        DF a, b;
-        a.hi = __int_as_float(in.z);
-        a.lo = __int_as_float(in.w);
-        const float2 bb = ok ? bspl[q] : make_float2(0.f, 0.f);
-        b.hi = bb.x;
-        b.lo = bb.y;
-        DF s = df_unpack(vacc[rank]);
-        df_fma(s, a, b);
-        vacc[rank] = df_pack(s);
-      } else {
-        const double x = __longlong_as_double(((long long)in.w << 32) | (unsigned)in.z);
-        double* v = reinterpret_cast<double*>(&vacc[rank]);
-        *v = fma(x, ok ? bval[q] : 0.0, *v);
-      }
-      __syncwarp();
-    }
-  }
-}
-
-// Chunk setup: lane t holds A entry p0 + t (B row start, length, A value
-// split for DF32 or as raw float64 halves).  Returns 1 if the lane's value is
-// outside the DF32 window.
-__device__ __forceinline__ int kept_info(int p0, int pe, const int32_t* __restrict__ acol,
-                                         const double* __restrict__ aval,
-                                         const int32_t* __restrict__ brp, int lane, int4& info,
-                                         DF& ad, double& a) {
-  const int p = p0 + lane;
-  info = make_int4(0, 0, 0, 0);
-  a = 0.0;
-  if (p < pe) {
-    const int j = acol[p];
-    info.x = brp[j];
-    info.y = brp[j + 1] - info.x;
-    a = aval[p];
-  }
-  return df_split(a, ad) ? 0 : 1;
-}
-
-template <bool PROBE>
-__device__ __forceinline__ void kept_store_and_run(int4 info, const DF& ad, double a, bool df,
-                                                   int4* ainfo, int nch, int lo_c,
-                                                   const u64* table, u64* vacc,
-                                                   const int32_t* __restrict__ bcol,
-                                                   const float2* __restrict__ bspl,
-                                                   const double* __restrict__ bval, int lane,
-                                                   int& missing) {
-  if (df) {
-    info.z = __float_as_int(ad.hi);
-    info.w = __float_as_int(ad.lo);
-  } else {
-    const long long ab = __double_as_longlong(a);
-    info.z = (int)(ab & 0xffffffffll);
-    info.w = (int)(ab >> 32);
-  }
-  ainfo[lane] = info;
-  __syncwarp();
-  const bool shrt = __reduce_max_sync(kFull, (unsigned)info.y) <= 32u;
-  if (df) {
-    if (shrt) kept_chunk<true, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
-    else kept_chunk_long<true, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
-  } else {
-    if (shrt) kept_chunk<false, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
-    else kept_chunk_long<false, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
-  }
-  __syncwarp();
-}
-
-// Value pass of a row; returns whether it ran in DF32.  Rows of at most 32 A
-// entries decide the arithmetic from their own split values; longer rows
-// check all their values first.
-template <bool PROBE>
-__device__ __forceinline__ bool kept_values(int pa, int pe, bool df_all,
-                                            const int32_t* __restrict__ acol,
-                                            const double* __restrict__ aval,
-                                            const int32_t* __restrict__ brp, int4* ainfo, int lo_c,
-                                            const u64* table, u64* vacc,
-                                            const int32_t* __restrict__ bcol,
-                                            const float2* __restrict__ bspl,
-                                            const double* __restrict__ bval, int lane, int& missing) {
-  bool df = df_all;
-  if (df_all && pe - pa > 32) df = row_df_ok<32>(aval, pa, pe, lane, kFull);
-  for (int p0 = pa; p0 < pe; p0 += 32) {
-    int4 info;
-    DF ad;
-    double a;
-    const int bad = kept_info(p0, pe, acol, aval, brp, lane, info, ad, a);
-    if (df_all && pe - pa <= 32) df = __any_sync(kFull, bad) == 0;
-    kept_store_and_run<PROBE>(info, ad, a, df, ainfo, min(32, pe - p0), lo_c, table, vacc, bcol,
-                              bspl, bval, lane, missing);
-  }
-  return df;
-}
 
 __global__ void __launch_bounds__(kKeptWarps * 32, 4)
 k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__ row_lo,
@@ -775,10 +571,8 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
   const bool df_all = arith == kArithDF32 && *b_range_bad == 0;
   for (int s = lane; s < kKeptSlots; s += 32) table[s] = kKeptEmpty;
   __syncwarp();
-  const int per_cta = (nrows + gridDim.x - 1) / gridDim.x;
-  const int r_begin = blockIdx.x * per_cta;
-  const int r_end = min(nrows, r_begin + per_cta);
-  for (int r = r_begin + warp; r < r_end; r += kKeptWarps) {
+  const int nw = gridDim.x * kKeptWarps;  // rows dealt round-robin over the grid
+  for (int r = blockIdx.x * kKeptWarps + warp; r < nrows; r += nw) {
     const int i = rows[r];
     const int L = cache.n[i];
     if (L < 0 || L > kCacheWords) {
