@@ -134,7 +134,8 @@ constexpr uint8_t kSkipBin = 0xFF;
 struct BinTable {
   int32_t nb;
   long long hi[kMaxBins];
-  int32_t mode[kMaxBins];
+  int32_t mode[kMaxBins];  // 0 vector, 1 flattened, 2 either, 3 thread tier (flop capped too)
+  long long thread_flop;
   int32_t nwin;
   int32_t win_bits[kNumWindowClasses];
   int32_t win_bin[kNumWindowClasses];
@@ -149,8 +150,13 @@ __device__ __forceinline__ uint8_t classify(const BinTable& t, long long q, int 
       if (span <= t.win_bits[w] && (long long)t.win_bits[w] <= (long long)kWindowFlopRatio * flop)
         return (uint8_t)t.win_bin[w];
   }
-  for (int b = 0; b < t.nb; ++b)
+  for (int b = 0; b < t.nb; ++b) {
+    if (t.mode[b] == 3) {
+      if (q <= t.hi[b] && flop <= t.thread_flop) return (uint8_t)b;
+      continue;
+    }
     if (q <= t.hi[b] && (t.mode[b] == 2 || t.mode[b] == flat)) return (uint8_t)b;
+  }
   return (uint8_t)(t.nb - 1);
 }
 
@@ -470,7 +476,7 @@ __global__ void k_tier_sums(int32_t m, const uint8_t* __restrict__ nbin, const i
 TierOfBin tier_of_bins(const std::vector<BinSpec>& bins) {
   TierOfBin t{};
   t.nb = (int32_t)bins.size();
-  for (size_t b = 0; b < bins.size() && b < (size_t)kMaxBins; ++b) t.tier[b] = (int8_t)bins[b].tier;
+  for (size_t b = 0; b < bins.size() && b < (size_t)kMaxBins; ++b) t.tier[b] = (int8_t)stat_tier(bins[b].tier);
   return t;
 }
 
@@ -631,6 +637,9 @@ CsrView view(const kk_csr* M) {
 void build_bins(const kk_spgemm_options& o, bool numeric, std::vector<BinSpec>& out) {
   out.clear();
   const int force = o.force_tier;
+  // thread tier first (automatic tier choice only)
+  if (force == -1)
+    out.push_back(BinSpec{kTierThread, 1, 0, 0, 0, numeric ? kThreadNumMax : kThreadSymMax});
   if (!numeric) {
     if (force < 1) {
       for (int ls = 5; ls <= 12; ++ls) {
@@ -694,9 +703,10 @@ BinTable to_table(const std::vector<BinSpec>& bins) {
       t.nb = (int32_t)b + 1;
     }
   }
+  t.thread_flop = kThreadNumMaxFlop;
   for (int b = 0; b < t.nb; ++b) {
     t.hi[b] = bins[b].hi;
-    t.mode[b] = bins[b].tier == kTierTeam ? bins[b].flat : 2;
+    t.mode[b] = bins[b].tier == kTierThread ? 3 : bins[b].tier == kTierTeam ? bins[b].flat : 2;
   }
   return t;
 }
@@ -1007,7 +1017,7 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
     for (int b = 0; b < nbs; ++b) {
       const int cnt = h_start[b + 1] - h_start[b];
       if (cnt <= 0) continue;
-      tier_rows[h->sym_bins[b].tier] += cnt;
+      tier_rows[stat_tier(h->sym_bins[b].tier)] += cnt;
       const int32_t* rows = h->d_srows.as<int32_t>() + h_start[b];
       cudaError_t e = h->sym_bins[b].tier == kTierWindow
                           ? launch_symbolic_window(ctx, h->sym_bins[b], av, bv, bcomp, rows, cnt,
@@ -1048,7 +1058,7 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   h->nnz_c = m > 0 ? hm->grand : 0;
   h->num_start.assign(h_start, h_start + nbn + 1);
   int64_t ntier[4] = {0, 0, 0, 0};
-  for (int b = 0; b < nbn; ++b) ntier[h->num_bins[b].tier] += h_start[b + 1] - h_start[b];
+  for (int b = 0; b < nbn; ++b) ntier[stat_tier(h->num_bins[b].tier)] += h_start[b + 1] - h_start[b];
   for (int t = 0; t < 3; ++t) h->stats[3 + t] = ntier[t];
   h->stats[11] = ntier[kTierWindow];
   for (int t = 0; t < 4; ++t) {

@@ -30,8 +30,14 @@ struct CsrView {
   const double* vals;
 };
 
-// Accumulator tiers.
-enum Tier : int32_t { kTierTeam = 0, kTierCta = 1, kTierDense = 2, kTierWindow = 3 };
+// Accumulator tiers.  The thread tier counts as the team tier in statistics.
+enum Tier : int32_t { kTierTeam = 0, kTierCta = 1, kTierDense = 2, kTierWindow = 3, kTierThread = 4 };
+__host__ __device__ constexpr int32_t stat_tier(int32_t t) { return t == kTierThread ? kTierTeam : t; }
+
+// Thread tier (kk_thread.cu): one thread per row, accumulator in registers.
+constexpr int kThreadSymMax = 16;     // symbolic rows: flop bound <= this
+constexpr int kThreadNumMax = 8;      // numeric rows: nnz(C(i,:)) <= this ...
+constexpr int kThreadNumMaxFlop = 16; // ... and flop bound <= this
 
 // Window tier: a row whose columns of C all lie in [row_lo, row_lo + W) gets a
 // dense bit vector of W bits (plus per-word ranks in the numeric phase).
@@ -114,6 +120,12 @@ cudaError_t launch_symbolic_wide(const LaunchCtx& ctx, const CsrView& A, const C
 cudaError_t launch_numeric_wide(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
                                 const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
                                 int32_t* c_colind, double* c_vals);
+
+cudaError_t launch_symbolic_thread(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                                   const int32_t* rows, int32_t nrows, int32_t* cnt);
+cudaError_t launch_numeric_thread(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                                  const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
+                                  int32_t* c_colind, double* c_vals);
 
 // Window-tier launches (kk_window.cu).
 cudaError_t launch_symbolic_window(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,

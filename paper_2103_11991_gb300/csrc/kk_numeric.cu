@@ -696,6 +696,8 @@ cudaError_t launch_numeric_bin(const LaunchCtx& ctx, const BinSpec& bin, const C
                                const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
                                int32_t* c_colind, double* c_vals, int32_t) {
   if (nrows <= 0) return cudaSuccess;
+  if (bin.tier == kTierThread)
+    return launch_numeric_thread(ctx, A, B, c_rowptr, rows, nrows, c_colind, c_vals);
   NumArgs g{A, B, b_sorted, b_split, b_range_bad, arith, c_rowptr, rows, nrows,
             c_colind, c_vals, ctx.status, B.n, bin.slots, nullptr, nullptr, nullptr, nullptr};
   int log2s = 0;

@@ -303,6 +303,7 @@ cudaError_t launch_symbolic_bin(const LaunchCtx& ctx, const BinSpec& bin, const 
                                 const CsrView& B, int32_t b_sorted, const int32_t* rows,
                                 int32_t nrows, int32_t* cnt) {
   if (nrows <= 0) return cudaSuccess;
+  if (bin.tier == kTierThread) return launch_symbolic_thread(ctx, A, B, rows, nrows, cnt);
   int log2s = 0;
   while ((1 << log2s) < bin.slots) ++log2s;
   if (bin.tier == kTierTeam && !bin.flat && bin.team == 32 && log2s >= 5 && log2s <= 12) {

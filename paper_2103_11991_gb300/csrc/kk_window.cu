@@ -249,10 +249,17 @@ k_sym_window(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ row_
     }
     int c = 0;
     if (L <= kCacheWords) {
-      for (int e = lane; e < L; e += 32) {
-        const int w = list[e];
-        const uint32_t m = bits[w];
-        bits[w] = 0u;
+      // whole 32-entry rounds are written (zeros past L) so the kept structure
+      // is stored in full 32-byte sectors, not merged into partial ones
+      const int Lr = (L + 31) & ~31;
+      for (int e = lane; e < Lr; e += 32) {
+        int w = 0;
+        uint32_t m = 0u;
+        if (e < L) {
+          w = list[e];
+          m = bits[w];
+          bits[w] = 0u;
+        }
         c += __popc(m);
         if (cache.w) {
           cache.w[(size_t)i * kCacheWords + e] = (uint16_t)w;
