@@ -96,7 +96,11 @@ typedef struct {
                                  (its non-empty 32-column words, at most 64 per row, 6 bytes
                                  each) so that the numeric phase of the same A and B arrays
                                  writes C's columns without re-deriving them (default 1) */
-  int32_t reserved[2];
+  int32_t wide_cache_mb;      /* budget for the wide tier's kept bit vectors (rows whose values
+                                 go to C by atomics keep their k-bit column vector from the
+                                 symbolic phase): MiB, 0 = one eighth of the device memory,
+                                 -1 = none; only with structure_cache = 1 */
+  int32_t reserved[1];
 } kk_spgemm_options;
 
 typedef struct kk_spgemm_handle_s* kk_spgemm_handle;

@@ -578,6 +578,12 @@ struct kk_spgemm_handle_s {
   DevBuf d_cn;         // int32[m]
   DevBuf d_left;       // int32[1 + m]: count, then rows left to the window kernel
   bool cache_valid = false;
+  // wide-tier bit vectors kept by the symbolic phase
+  DevBuf d_wbits, d_wslot, d_wnext;
+  bool keep_valid = false;
+  const void* keep_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  WideKeep keep{nullptr, nullptr, nullptr, 0, 0};  // what the next launches use
+  size_t dev_total = 0;
   const void* cache_key[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -713,7 +719,7 @@ BinTable to_table(const std::vector<BinSpec>& bins) {
 
 LaunchCtx ctx_of(kk_spgemm_handle h) {
   return LaunchCtx{h->stream, h->timer, &h->d_misc.as<Misc>()->status, h->num_sms, h->max_smem,
-                   h->d_rowlo.as<int32_t>(), h->d_flop.as<long long>()};
+                   h->d_rowlo.as<int32_t>(), h->d_flop.as<long long>(), h->keep};
 }
 
 // Analysis of B at the start of a symbolic call; with the window tier on, the
@@ -791,6 +797,46 @@ kk_status cache_for_symbolic(kk_spgemm_handle h, int32_t m, bool any_window, con
   h->cache_key[2] = bv.rowptr;
   h->cache_key[3] = bv.colind;
   return KK_OK;
+}
+
+// Slots for the wide tier's kept bit vectors of this symbolic call (none when
+// the option is off, no row takes the wide tier or the budget is zero).
+kk_status keep_for_symbolic(kk_spgemm_handle h, int32_t m, int64_t wide_rows, const CsrView& av,
+                            const CsrView& bv) {
+  h->keep = WideKeep{nullptr, nullptr, nullptr, 0, 0};
+  h->keep_valid = false;
+  if (!h->opt.structure_cache || h->opt.wide_cache_mb < 0 || wide_rows <= 0 || m <= 0) return KK_OK;
+  const LaunchCtx probe = ctx_of(h);
+  if (!wide_symbolic_fits(probe, bv.n) || !wide_numeric_fits(probe, bv.n)) return KK_OK;
+  const size_t words = (size_t)wide_word_count(bv.n);
+  const size_t budget = h->opt.wide_cache_mb > 0 ? ((size_t)h->opt.wide_cache_mb << 20) : h->dev_total / 8;
+  long long slots = (long long)(budget / (words * 4));
+  if (slots > wide_rows) slots = wide_rows;
+  if (slots > 0x7fffffff) slots = 0x7fffffff;
+  if (slots <= 0) return KK_OK;
+  KK_CUDA(h, h->d_wbits.ensure(words * 4 * (size_t)slots), "alloc wide cache");
+  KK_CUDA(h, h->d_wslot.ensure(sizeof(int32_t) * (size_t)m), "alloc wide cache");
+  KK_CUDA(h, h->d_wnext.ensure(sizeof(int32_t)), "alloc wide cache");
+  KK_CUDA(h, cudaMemsetAsync(h->d_wslot.p, 0xFF, sizeof(int32_t) * (size_t)m, h->stream), "memset");
+  KK_CUDA(h, cudaMemsetAsync(h->d_wnext.p, 0, sizeof(int32_t), h->stream), "memset");
+  h->keep = WideKeep{h->d_wbits.as<uint32_t>(), h->d_wslot.as<int32_t>(), h->d_wnext.as<int32_t>(),
+                     (int32_t)slots, wide_keep_min_cnt(probe, bv.n)};
+  h->keep_valid = true;
+  h->keep_key[0] = av.rowptr;
+  h->keep_key[1] = av.colind;
+  h->keep_key[2] = bv.rowptr;
+  h->keep_key[3] = bv.colind;
+  return KK_OK;
+}
+
+// The kept wide bit vectors for a numeric call, if they belong to its arrays.
+void keep_for_numeric(kk_spgemm_handle h, const CsrView& av, const CsrView& bv) {
+  if (h->keep_valid && h->keep_key[0] == av.rowptr && h->keep_key[1] == av.colind &&
+      h->keep_key[2] == bv.rowptr && h->keep_key[3] == bv.colind) {
+    h->keep.next = nullptr;  // the numeric phase only reads
+  } else {
+    h->keep = WideKeep{nullptr, nullptr, nullptr, 0, 0};
+  }
 }
 
 // The kept structure, if it belongs to these index arrays, and the scratch
@@ -884,6 +930,7 @@ kk_status kk_spgemm_options_default(kk_spgemm_options* opt) {
   opt->sym_load_pct = 75;
   opt->num_load_pct = 50;
   opt->structure_cache = 1;
+  opt->wide_cache_mb = 0;
   return KK_OK;
 }
 
@@ -896,7 +943,7 @@ kk_status kk_spgemm_handle_create(kk_spgemm_handle* out, const kk_spgemm_options
   if (opt) h->opt = *opt; else kk_spgemm_options_default(&h->opt);
   if (h->opt.arith < 0 || h->opt.arith > 2 || h->opt.force_tier < -1 || h->opt.force_tier > 3 ||
       h->opt.sym_load_pct < 10 || h->opt.sym_load_pct > 100 || h->opt.num_load_pct < 10 ||
-      h->opt.num_load_pct > 50 || h->opt.structure_cache < 0 || h->opt.structure_cache > 1 ||
+      h->opt.num_load_pct > 50 || h->opt.structure_cache < 0 || h->opt.structure_cache > 1 || h->opt.wide_cache_mb < -1 ||
       h->opt.team_vec_min_len < 0) {
     delete h;
     return KK_ERR_INVALID_ARG;
@@ -906,6 +953,11 @@ kk_status kk_spgemm_handle_create(kk_spgemm_handle* out, const kk_spgemm_options
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&h->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (e == cudaSuccess) {
+    size_t fr = 0, tot = 0;
+    e = cudaMemGetInfo(&fr, &tot);
+    h->dev_total = tot;
+  }
   if (e == cudaSuccess) e = h->d_misc.ensure(sizeof(Misc));
   if (e == cudaSuccess) e = h->d_binstart.ensure(sizeof(int32_t) * 2 * (kMaxBins + 1));
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_pinned, 4096);
@@ -1004,6 +1056,11 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   // symbolic kernels per bin
   if (m > 0) {
     KK_CUDA(h, cudaMemsetAsync(h->d_cnt.p, 0, sizeof(int32_t) * (size_t)m, s), "memset counts");
+    int64_t wide_rows = 0;
+    for (int b = 0; b < nbs; ++b)
+      if (h->sym_bins[b].tier == kTierCta || h->sym_bins[b].tier == kTierDense)
+        wide_rows += h_start[b + 1] - h_start[b];
+    if ((st = keep_for_symbolic(h, m, wide_rows, av, bv)) != KK_OK) return st;
     LaunchCtx ctx = ctx_of(h);
     bool any_win = false;
     for (int b = 0; b < nbs; ++b)
@@ -1095,6 +1152,7 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
   h->last_arith = arith;
   if (h->am == 0 || h->nnz_c == 0) return KK_OK;
   const float2* bsplit = nullptr;
+  keep_for_numeric(h, av, bv);
   if (arith == kArithDF32) {
     KK_CUDA(h, h->d_bsplit.ensure(sizeof(float2) * (size_t)(bv.nnz > 0 ? bv.nnz : 1)), "alloc split");
     KK_CUDA(h, cudaMemsetAsync(&dm->range_bad, 0, sizeof(int32_t), s), "memset");
@@ -1208,6 +1266,8 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
   if (!c_rowptr || !nnz_c) return fail(h, KK_ERR_INVALID_ARG, "c_rowptr / nnz_c is NULL");
   h->have_symbolic = false;
   h->learned_valid = false;
+  h->keep = WideKeep{nullptr, nullptr, nullptr, 0, 0};
+  h->keep_valid = false;
   const int32_t m = A->m;
   const size_t mm1 = (size_t)(m > 0 ? m : 1);
   const CsrView av = view(A), bv = view(B);
@@ -1391,6 +1451,7 @@ kk_status kk_spgemm_learned_numeric(kk_spgemm_handle h, const kk_csr* A, const k
   if (h->am == 0 || h->nnz_c == 0) return KK_OK;
   const CsrView av = view(A), bv = view(B);
   Misc* dm = h->d_misc.as<Misc>();
+  keep_for_numeric(h, av, bv);
   LaunchCtx ctx = ctx_of(h);
   cudaError_t e = launch_copy_staged(ctx, h->am, h->d_lbin.as<uint8_t>(), h->d_plain.as<uint8_t>(),
                                      h->d_soff.as<int64_t>(), c_rowptr, h->d_scol.as<int32_t>(),
@@ -1721,7 +1782,8 @@ kk_status kk_spgemm_destroy(kk_spgemm_handle h) {
                     &h->d_sval, &h->d_sball, &h->d_nbin2, &h->d_lrows, &h->d_lrows2, &h->d_mm,
                     &h->d_bdesc, &h->d_rowpair, &h->d_bflop, &h->d_bsbin, &h->d_bnbin, &h->d_bsrows,
                     &h->d_bnrows, &h->d_bcnt, &h->d_btiles, &h->d_bstart, &h->d_bqueue, &h->d_bsplit2,
-                    &h->d_boff, &h->d_bc, &h->d_bclen, &h->d_cw, &h->d_cm, &h->d_cn, &h->d_left})
+                    &h->d_boff, &h->d_bc, &h->d_bclen, &h->d_cw, &h->d_cm, &h->d_cn, &h->d_left, &h->d_wbits,
+                    &h->d_wslot, &h->d_wnext})
     b->release();
   for (void* p : {h->h_bdesc, h->h_bdesc2, h->h_boff})
     if (p) cudaFreeHost(p);

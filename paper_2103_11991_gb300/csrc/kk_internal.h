@@ -13,6 +13,17 @@ struct KernelTimer;
 void timer_begin(KernelTimer* t, cudaStream_t s, const char* name);
 void timer_end(KernelTimer* t, cudaStream_t s);
 
+// Bit vectors of wide-tier rows kept by the symbolic phase for the numeric
+// phase of the same arrays: rows whose nnz(C(i,:)) exceeds min_cnt (their
+// values go to C with atomics) get a slot of `words` u32 when one is left.
+struct WideKeep {
+  uint32_t* bits;     // max_slots slots of `words` words
+  int32_t* slot;      // per row: slot or -1
+  int32_t* next;      // slot counter
+  int32_t max_slots;  // 0: nothing kept / nothing to use
+  int32_t min_cnt;
+};
+
 struct LaunchCtx {
   cudaStream_t stream;
   KernelTimer* timer;  // may be null
@@ -21,6 +32,7 @@ struct LaunchCtx {
   int max_smem_optin;
   const int32_t* row_lo;  // first column of each row's span window (window tier)
   const long long* flop;  // flop bound of each row (wide tier)
+  WideKeep keep;          // kept wide-tier bit vectors (wide tier)
 };
 
 struct CsrView {
@@ -113,6 +125,8 @@ cudaError_t launch_numeric_bin(const LaunchCtx& ctx, const BinSpec& bin, const C
 // Wide tier (kk_wide.cu): CTA-per-row bit vector over all k columns, used for
 // the CTA and dense bins when it fits in shared memory.
 bool wide_symbolic_fits(const LaunchCtx& ctx, int32_t k);
+int32_t wide_word_count(int32_t k);                           // words of a k-bit vector
+int32_t wide_keep_min_cnt(const LaunchCtx& ctx, int32_t k);  // rows above this go to C by atomics
 bool wide_numeric_fits(const LaunchCtx& ctx, int32_t k);
 cudaError_t launch_symbolic_wide(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
                                  const long long* flop, const int32_t* rows, int32_t nrows,

@@ -14,6 +14,10 @@
 //             values (zeroed first) with global float64 atomics.  The order of
 //             the additions is not fixed, so the values carry the float64 bound
 //             of an unordered sum.
+// Rows whose values go to C with atomics keep their bit vector from the
+// symbolic phase (a slot of ceil(k/32) words in global memory, while the
+// handle's budget lasts), so the numeric phase loads it instead of walking the
+// row's products a second time for the structure.
 // The CTA walks the row's products (the flattened (A entry, B entry) pairs in
 // storage order) in work items of kItem products that warps claim from a
 // shared counter, so one long B row does not leave the other warps waiting at
@@ -216,12 +220,14 @@ __device__ __forceinline__ void wide_set_bits(const CsrView& A, const CsrView& B
 
 __global__ void __launch_bounds__(kWideBlock, 1)
 k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long long* __restrict__ flop,
-           const int32_t* __restrict__ rows, int32_t nrows, int32_t* __restrict__ cnt, int* status) {
+           const int32_t* __restrict__ rows, int32_t nrows, int32_t* __restrict__ cnt,
+           WideKeep keep, int* status) {
   extern __shared__ __align__(16) unsigned char wsm[];
   uint32_t* bits = reinterpret_cast<uint32_t*>(wsm);
   uint32_t* sum = reinterpret_cast<uint32_t*>(wsm + sum_off);
   __shared__ WalkSmem ws;
   __shared__ int tmp[33];
+  __shared__ int s_slot;
   const int nsum = words >> 5;
   for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4)
     *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
@@ -233,6 +239,9 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
     const bool sparse = flop[i] < (long long)words;  // few words touched: walk the summary
     int c = 0;
     if (sparse) {
+      // few words touched: count and clear them through the summary (such rows
+      // keep nothing: walking their products again costs less than storing
+      // and reloading a k-bit vector)
       wide_set_bits<true>(A, B, A.rowptr[i], A.rowptr[i + 1], ws, bits, sum, words, bad);
       for (int s = threadIdx.x; s < nsum; s += blockDim.x) {
         uint32_t m = sum[s];
@@ -245,18 +254,39 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
           bits[w] = 0u;
         }
       }
+      int tot;
+      block_exscan<int>(c, tmp, &tot);
+      if (threadIdx.x == 0) cnt[i] = tot;
     } else {
       wide_set_bits<false>(A, B, A.rowptr[i], A.rowptr[i + 1], ws, bits, sum, words, bad);
       for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4) {
-        uint4* q = reinterpret_cast<uint4*>(&bits[w]);
-        const uint4 v = *q;
+        const uint4 v = *reinterpret_cast<const uint4*>(&bits[w]);
         c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+      }
+      int tot;
+      block_exscan<int>(c, tmp, &tot);
+      // rows whose values will go to C by atomics keep their bits for the
+      // numeric phase, while slots last
+      if (threadIdx.x == 0) {
+        int sl = -1;
+        if (keep.max_slots > 0 && tot > keep.min_cnt) {
+          sl = atomicAdd(keep.next, 1);
+          if (sl >= keep.max_slots) sl = -1;
+          if (sl >= 0) keep.slot[i] = sl;
+        }
+        s_slot = sl;
+      }
+      __syncthreads();
+      const int sl = s_slot;
+      uint32_t* dst = sl >= 0 ? keep.bits + (size_t)sl * words : nullptr;
+      for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4) {
+        uint4* q = reinterpret_cast<uint4*>(&bits[w]);
+        if (dst) *reinterpret_cast<uint4*>(&dst[w]) = *q;
         *q = make_uint4(0u, 0u, 0u, 0u);
       }
+      if (threadIdx.x == 0) cnt[i] = tot;
+      __syncthreads();
     }
-    int tot;
-    block_exscan<int>(c, tmp, &tot);
-    if (threadIdx.x == 0) cnt[i] = tot;
   }
   if (bad) set_status(status, KK_ERR_BAD_INDEX);
 }
@@ -264,7 +294,8 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
 __global__ void __launch_bounds__(kWideBlock, 1)
 k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, uint32_t reg_off,
            uint32_t val_off, const int64_t* __restrict__ c_rowptr, const int32_t* __restrict__ rows,
-           int32_t nrows, int32_t* __restrict__ c_colind, double* __restrict__ c_vals, int* status) {
+           int32_t nrows, int32_t* __restrict__ c_colind, double* __restrict__ c_vals, WideKeep keep,
+           int* status) {
   extern __shared__ __align__(16) unsigned char wsm[];
   uint32_t* bits = reinterpret_cast<uint32_t*>(wsm);
   uint32_t* sum = reinterpret_cast<uint32_t*>(wsm + sum_off);
@@ -340,7 +371,15 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
       // from C's columns when they are cleared
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) vals[e] = 0.0;
     } else {
-      wide_set_bits<false>(A, B, pa, pe, ws, bits, sum, words, bad);
+      const int sl = keep.max_slots > 0 ? keep.slot[i] : -1;
+      if (sl >= 0) {  // the symbolic phase kept this row's bits
+        const uint32_t* src = keep.bits + (size_t)sl * words;
+        for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4)
+          *reinterpret_cast<uint4*>(&bits[w]) = *reinterpret_cast<const uint4*>(&src[w]);
+        __syncthreads();
+      } else {
+        wide_set_bits<false>(A, B, pa, pe, ws, bits, sum, words, bad);
+      }
       const int gpt = (groups + blockDim.x - 1) / blockDim.x;
       const int g0 = threadIdx.x * gpt, g1 = min(groups, g0 + gpt);
       int mine = 0;
@@ -377,6 +416,10 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
       if (c >= 0 && (unsigned)c < (unsigned)(words * 32)) {
         const int w = c >> 5;
         const uint32_t word = bits[w];
+        if (!((word >> (c & 31)) & 1u)) {  // a column outside the (kept) structure
+          mismatch = 1;
+          return;
+        }
         const int below = __popc(word & ((1u << (c & 31)) - 1u));
         const int rank = sparse ? (int)wpre16[w] + below : (int)gpre[w >> 3] + (int)wpre8[w] + below;
         if (rank < cnt) {
@@ -419,6 +462,13 @@ int wide_grid(const LaunchCtx& ctx, size_t smem, int nrows) {
 
 }  // namespace
 
+int32_t wide_word_count(int32_t k) { return wide_words(k); }
+
+int32_t wide_keep_min_cnt(const LaunchCtx& ctx, int32_t k) {
+  const WideGeom g = wide_geom(wide_words(k), wide_budget(ctx), true);
+  return g.vcap < 65535 ? g.vcap : 65535;
+}
+
 bool wide_symbolic_fits(const LaunchCtx& ctx, int32_t k) {
   if (k <= 0) return false;
   return wide_geom(wide_words(k), wide_budget(ctx), false).bytes <= wide_budget(ctx);
@@ -439,7 +489,7 @@ cudaError_t launch_symbolic_wide(const LaunchCtx& ctx, const CsrView& A, const C
   cudaError_t e = cudaFuncSetAttribute(k_sym_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.bytes);
   if (e != cudaSuccess) return e;
   k_sym_wide<<<wide_grid(ctx, g.bytes, nrows), kWideBlock, g.bytes, ctx.stream>>>(
-      A, B, words, (uint32_t)g.sum_off, flop, rows, nrows, cnt, ctx.status);
+      A, B, words, (uint32_t)g.sum_off, flop, rows, nrows, cnt, ctx.keep, ctx.status);
   return cudaGetLastError();
 }
 
@@ -453,7 +503,7 @@ cudaError_t launch_numeric_wide(const LaunchCtx& ctx, const CsrView& A, const Cs
   if (e != cudaSuccess) return e;
   k_num_wide<<<wide_grid(ctx, g.bytes, nrows), kWideBlock, g.bytes, ctx.stream>>>(
       A, B, words, g.vcap, (uint32_t)g.sum_off, (uint32_t)g.reg_off, (uint32_t)g.val_off, c_rowptr,
-      rows, nrows, c_colind, c_vals, ctx.status);
+      rows, nrows, c_colind, c_vals, ctx.keep, ctx.status);
   return cudaGetLastError();
 }
 

@@ -103,3 +103,18 @@ def test_changed_structure_behind_same_arrays_is_reported(cache):
             op.numeric(dA, dB, rp, nnz)
             op.sync()
         assert e.value.status == 4
+
+
+def test_wide_kept_bits_match_rebuild():
+    # rows with more columns than the wide kernel holds as values in shared
+    # memory keep their bit vector from the symbolic phase; the result must be
+    # the one of a rebuild (structure bit-exact, values within the bound)
+    A = I.random_rows(60, 400, 250, 350, seed=31)
+    B = I.random_rows(400, 200000, 100, 140, seed=32)
+    kept = run_gpu(A, B, force_tier=2, structure_cache=1)
+    rebuilt = run_gpu(A, B, force_tier=2, structure_cache=0)
+    assert np.array_equal(kept[0], rebuilt[0]) and np.array_equal(kept[1], rebuilt[1])
+    check_against_oracle(A, B, *kept[:3])
+    check_against_oracle(A, B, *rebuilt[:3])
+    assert kept[4]["num_dense_rows"] > 0
+    assert np.diff(kept[0]).min() > 24000  # above the wide kernel's shared-memory value space
