@@ -1,7 +1,7 @@
 /*
  * kk_batched.h - C ABI of the batched form: many independent products
- * C_k = A_k * B_k (k = 0 .. count-1) in one persistent launch per phase
- * (include kk_spgemm.h first).
+ * C_k = A_k * B_k (k = 0 .. count-1) in one call per phase (include
+ * kk_spgemm.h first).
  *
  * The Kokkos Kernels paper runs many small dense problems inside one parallel
  * launch (Sec. "Dense Linear Algebra", batched BLAS: one launch over a batch,
@@ -18,13 +18,21 @@
  * total_nnz entries.  Row pointers of C_k are c_rowptr[R_k .. R_k + A_k.m];
  * c_rowptr[R_k] is the batch base of C_k.
  *
- * With options.batched_graph = 1 and a non-default stream, each phase is
- * captured into a CUDA graph on its first call and replayed by later calls
- * with the same pairs (same pointers and sizes).
- *
- * Limits: rows whose flop bound exceeds 24576 (symbolic) or whose nnz exceeds
- * 4096 (numeric) are outside the batched accumulators and return
- * KK_ERR_CAPACITY; use the plain form for such products.
+ * Two execution modes (options.batched_mode):
+ *   1 - persistent: the work-queue kernels above.  With options.batched_graph
+ *       = 1 and a non-default stream, each phase is captured into a CUDA graph
+ *       on its first call and replayed by later calls with the same pairs
+ *       (same pointers and sizes).  Rows whose flop bound exceeds 24576
+ *       (symbolic) or whose nnz exceeds 4096 (numeric) are outside the batched
+ *       accumulators and return KK_ERR_CAPACITY.
+ *   2 - packed (and 0, the default): the batch becomes one block-diagonal
+ *       product diag(A_k) * diag(B_k) in handle scratch (A's columns shifted to
+ *       the packed rows of B_k, B's columns kept local, so C's rows come out in
+ *       pair order with local columns) and runs through the plain two-phase
+ *       kernels, rows of all pairs binned together across every tier (thread,
+ *       window with kept structure, warp hash, wide); no capacity limits, no
+ *       graph capture (the symbolic phase reads its bin sizes on the host).
+ *       Needs the sums of A_k.nnz, B_k.nnz and B_k.m below 2^31.
  */
 #ifndef KK_BATCHED_H_
 #define KK_BATCHED_H_

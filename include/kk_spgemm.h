@@ -100,7 +100,9 @@ typedef struct {
                                  go to C by atomics keep their k-bit column vector from the
                                  symbolic phase): MiB, 0 = one eighth of the device memory,
                                  -1 = none; only with structure_cache = 1 */
-  int32_t reserved[1];
+  int32_t batched_mode;       /* batched form (kk_batched.h): 1 = persistent work-queue kernels
+                                 (graph-capturable), 2 = the batch as one block-diagonal product
+                                 through the plain two-phase kernels, 0 = automatic (2) */
 } kk_spgemm_options;
 
 typedef struct kk_spgemm_handle_s* kk_spgemm_handle;

@@ -584,6 +584,11 @@ struct kk_spgemm_handle_s {
   const void* keep_key[4] = {nullptr, nullptr, nullptr, nullptr};
   WideKeep keep{nullptr, nullptr, nullptr, 0, 0};  // what the next launches use
   size_t dev_total = 0;
+  // packed batch: block-diagonal A and B of the last batched symbolic call
+  DevBuf d_pa_rp, d_pa_ci, d_pa_v, d_pb_rp, d_pb_ci, d_pb_v, d_pbase;
+  long long p_RA = 0, p_NA = 0, p_RB = 0, p_NB = 0;
+  int32_t p_kmax = 0;
+  bool p_valid = false;
   const void* cache_key[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -931,6 +936,7 @@ kk_status kk_spgemm_options_default(kk_spgemm_options* opt) {
   opt->num_load_pct = 50;
   opt->structure_cache = 1;
   opt->wide_cache_mb = 0;
+  opt->batched_mode = 0;
   return KK_OK;
 }
 
@@ -943,7 +949,8 @@ kk_status kk_spgemm_handle_create(kk_spgemm_handle* out, const kk_spgemm_options
   if (opt) h->opt = *opt; else kk_spgemm_options_default(&h->opt);
   if (h->opt.arith < 0 || h->opt.arith > 2 || h->opt.force_tier < -1 || h->opt.force_tier > 3 ||
       h->opt.sym_load_pct < 10 || h->opt.sym_load_pct > 100 || h->opt.num_load_pct < 10 ||
-      h->opt.num_load_pct > 50 || h->opt.structure_cache < 0 || h->opt.structure_cache > 1 || h->opt.wide_cache_mb < -1 ||
+      h->opt.num_load_pct > 50 || h->opt.structure_cache < 0 || h->opt.structure_cache > 1 || h->opt.wide_cache_mb < -1 || h->opt.batched_mode < 0 ||
+      h->opt.batched_mode > 2 ||
       h->opt.team_vec_min_len < 0) {
     delete h;
     return KK_ERR_INVALID_ARG;
@@ -1554,6 +1561,111 @@ kk_status run_maybe_graph(kk_spgemm_handle h, bool use_graph, cudaGraphExec_t* e
 
 extern "C" {
 
+}  // extern "C"
+
+namespace {
+
+kk_csr packed_a(kk_spgemm_handle h) {
+  return kk_csr{(int32_t)h->p_RA, (int32_t)h->p_RB, (int32_t)h->p_NA, h->d_pa_rp.as<int32_t>(),
+                h->d_pa_ci.as<int32_t>(), h->d_pa_v.as<double>()};
+}
+kk_csr packed_b(kk_spgemm_handle h) {
+  return kk_csr{(int32_t)h->p_RB, h->p_kmax, (int32_t)h->p_NB, h->d_pb_rp.as<int32_t>(),
+                h->d_pb_ci.as<int32_t>(), h->d_pb_v.as<double>()};
+}
+
+// Packed batch, symbolic: the pairs become one block-diagonal product
+// diag(A_k) * diag(B_k) (A's columns shifted to their B rows, B's columns kept
+// local), whose rows are C's rows in pair order with local columns: the plain
+// two-phase path computes every product with all of its tiers, binning rows of
+// all pairs together.  The pair descriptors must already be in hd.
+kk_status batched_packed_symbolic(kk_spgemm_handle h, int32_t count, const kk_csr* A, const kk_csr* B,
+                                  PairDesc* hd, int64_t* c_rowptr, int64_t* c_offsets,
+                                  int64_t* total_nnz) {
+  long long RA = 0, NA = 0, RB = 0, NB = 0;
+  int32_t kmax = 0;
+  std::vector<long long> base(4 * (size_t)(count > 0 ? count : 1));
+  for (int k = 0; k < count; ++k) {
+    base[4 * k] = RA;
+    base[4 * k + 1] = NA;
+    base[4 * k + 2] = RB;
+    base[4 * k + 3] = NB;
+    RA += A[k].m;
+    NA += A[k].nnz;
+    RB += B[k].m;
+    NB += B[k].nnz;
+    if (B[k].n > kmax) kmax = B[k].n;
+  }
+  if (NA > 0x7fffffffll || NB > 0x7fffffffll || RB > 0x7fffffffll)
+    return fail(h, KK_ERR_INVALID_ARG, "packed batch exceeds int32 indices; use batched_mode = 1");
+  cudaStream_t s = h->stream;
+  KK_CUDA(h, h->d_pa_rp.ensure(sizeof(int32_t) * (size_t)(RA + 1)), "alloc packed batch");
+  KK_CUDA(h, h->d_pa_ci.ensure(sizeof(int32_t) * (size_t)(NA > 0 ? NA : 1)), "alloc packed batch");
+  KK_CUDA(h, h->d_pa_v.ensure(sizeof(double) * (size_t)(NA > 0 ? NA : 1)), "alloc packed batch");
+  KK_CUDA(h, h->d_pb_rp.ensure(sizeof(int32_t) * (size_t)(RB + 1)), "alloc packed batch");
+  KK_CUDA(h, h->d_pb_ci.ensure(sizeof(int32_t) * (size_t)(NB > 0 ? NB : 1)), "alloc packed batch");
+  KK_CUDA(h, h->d_pb_v.ensure(sizeof(double) * (size_t)(NB > 0 ? NB : 1)), "alloc packed batch");
+  KK_CUDA(h, h->d_pbase.ensure(sizeof(long long) * base.size()), "alloc packed batch");
+  KK_CUDA(h, h->d_bdesc.ensure(sizeof(PairDesc) * (size_t)(count > 0 ? count : 1)), "alloc batch");
+  KK_CUDA(h, h->d_boff.ensure(sizeof(int64_t) * ((size_t)count + 1)), "alloc batch");
+  PairDesc* dd = h->d_bdesc.as<PairDesc>();
+  if (count > 0) {
+    KK_CUDA(h, cudaMemcpyAsync(dd, hd, sizeof(PairDesc) * count, cudaMemcpyHostToDevice, s), "upload");
+    KK_CUDA(h, cudaMemcpyAsync(h->d_pbase.p, base.data(), sizeof(long long) * base.size(),
+                               cudaMemcpyHostToDevice, s), "upload");
+  }
+  // pageable sources above: staged before return, so base may go out of scope
+  KK_CUDA(h, launch_b_pack(s, h->num_sms, count, dd, h->d_pbase.as<long long>(), false,
+                           h->d_pa_rp.as<int32_t>(), h->d_pa_ci.as<int32_t>(), h->d_pa_v.as<double>(),
+                           h->d_pb_rp.as<int32_t>(), h->d_pb_ci.as<int32_t>(), h->d_pb_v.as<double>(),
+                           RA, NA, RB, NB), "pack");
+  if (count == 0) {
+    KK_CUDA(h, cudaMemsetAsync(h->d_pa_rp.p, 0, sizeof(int32_t), s), "memset");
+    KK_CUDA(h, cudaMemsetAsync(h->d_pb_rp.p, 0, sizeof(int32_t), s), "memset");
+  }
+  h->p_RA = RA;
+  h->p_NA = NA;
+  h->p_RB = RB;
+  h->p_NB = NB;
+  h->p_kmax = kmax;
+  const kk_csr Ap = packed_a(h), Bp = packed_b(h);
+  int64_t nnz = 0;
+  kk_status st = kk_spgemm_symbolic(h, &Ap, &Bp, c_rowptr, &nnz);
+  if (st != KK_OK) return st;
+  KK_CUDA(h, launch_b_offsets(s, count, dd, RA, c_rowptr, h->d_boff.as<int64_t>()), "offsets");
+  KK_CUDA(h, cudaMemcpyAsync(h->h_boff, h->d_boff.p, sizeof(int64_t) * ((size_t)count + 1),
+                             cudaMemcpyDeviceToHost, s), "readback");
+  KK_CUDA(h, cudaStreamSynchronize(s), "sync");
+  const int64_t* off = static_cast<const int64_t*>(h->h_boff);
+  if (c_offsets)
+    for (int k = 0; k <= count; ++k) c_offsets[k] = off[k];
+  h->b_total = nnz;
+  h->p_valid = true;
+  *total_nnz = nnz;
+  return KK_OK;
+}
+
+// Packed batch, numeric: values (and, when the caller's arrays moved, the
+// structure) packed again, then the plain numeric phase.
+kk_status batched_packed_numeric(kk_spgemm_handle h, int32_t count, bool moved, const int64_t* c_rowptr,
+                                 int32_t* c_colind, double* c_vals) {
+  cudaStream_t s = h->stream;
+  PairDesc* dd = h->d_bdesc.as<PairDesc>();
+  PairDesc* hd2 = static_cast<PairDesc*>(h->h_bdesc2);
+  if (count > 0)
+    KK_CUDA(h, cudaMemcpyAsync(dd, hd2, sizeof(PairDesc) * count, cudaMemcpyHostToDevice, s), "upload");
+  KK_CUDA(h, launch_b_pack(s, h->num_sms, count, dd, h->d_pbase.as<long long>(), !moved,
+                           h->d_pa_rp.as<int32_t>(), h->d_pa_ci.as<int32_t>(), h->d_pa_v.as<double>(),
+                           h->d_pb_rp.as<int32_t>(), h->d_pb_ci.as<int32_t>(), h->d_pb_v.as<double>(),
+                           h->p_RA, h->p_NA, h->p_RB, h->p_NB), "pack");
+  const kk_csr Ap = packed_a(h), Bp = packed_b(h);
+  return kk_spgemm_numeric(h, &Ap, &Bp, c_rowptr, c_colind, c_vals);
+}
+
+}  // namespace
+
+extern "C" {
+
 kk_status kk_spgemm_batched_symbolic(kk_spgemm_handle h, int32_t count, const kk_csr* A,
                                      const kk_csr* B, int64_t* c_rowptr, int64_t* c_offsets,
                                      int64_t* total_nnz) {
@@ -1581,6 +1693,17 @@ kk_status kk_spgemm_batched_symbolic(kk_spgemm_handle h, int32_t count, const kk
     hd[k] = PairDesc{view(&A[k]), view(&B[k]), rb, sb, 1, 0};
     rb += A[k].m;
     sb += B[k].nnz;
+  }
+  h->p_valid = false;
+  if (h->opt.batched_mode != 1) {
+    if ((st = batched_packed_symbolic(h, count, A, B, hd, c_rowptr, c_offsets, total_nnz)) != KK_OK)
+      return st;
+    std::memcpy(h->h_bdesc2, hd, sizeof(PairDesc) * (size_t)count);
+    h->b_count = count;
+    h->b_R = R;
+    h->b_nnzb = nnzb;
+    h->b_valid = true;
+    return KK_OK;
   }
   batched_bin_tables(h->b_sym, h->b_num, h->opt.sym_load_pct, h->opt.num_load_pct);
   const size_t R1 = (size_t)(R > 0 ? R : 1);
@@ -1692,6 +1815,13 @@ kk_status kk_spgemm_batched_numeric(kk_spgemm_handle h, int32_t count, const kk_
         b.colind != d.B.colind || b.vals != d.B.vals)
       changed = true;
   }
+  bool moved = false;  // index arrays at other addresses (values alone may move freely)
+  for (int k = 0; k < count && changed; ++k) {
+    const CsrView a = view(&A[k]), b = view(&B[k]);
+    if (a.rowptr != hd2[k].A.rowptr || a.colind != hd2[k].A.colind || b.rowptr != hd2[k].B.rowptr ||
+        b.colind != hd2[k].B.colind)
+      moved = true;
+  }
   if (changed) {
     KK_CUDA(h, cudaStreamSynchronize(h->stream), "sync");  // pending uploads read the pinned copy
     for (int k = 0; k < count; ++k) {
@@ -1700,6 +1830,7 @@ kk_status kk_spgemm_batched_numeric(kk_spgemm_handle h, int32_t count, const kk_
     }
   }
   if (h->b_R == 0 || h->b_total == 0) return KK_OK;
+  if (h->p_valid) return batched_packed_numeric(h, count, moved, c_rowptr, c_colind, c_vals);
   const int32_t arith = h->opt.arith == KK_ARITH_FP64 ? kArithF64 : kArithDF32;
   h->last_arith = arith;
   KK_CUDA(h, h->d_bsplit2.ensure(sizeof(float2) * (size_t)(h->b_nnzb > 0 ? h->b_nnzb : 1)), "alloc split");
@@ -1783,7 +1914,8 @@ kk_status kk_spgemm_destroy(kk_spgemm_handle h) {
                     &h->d_bdesc, &h->d_rowpair, &h->d_bflop, &h->d_bsbin, &h->d_bnbin, &h->d_bsrows,
                     &h->d_bnrows, &h->d_bcnt, &h->d_btiles, &h->d_bstart, &h->d_bqueue, &h->d_bsplit2,
                     &h->d_boff, &h->d_bc, &h->d_bclen, &h->d_cw, &h->d_cm, &h->d_cn, &h->d_left, &h->d_wbits,
-                    &h->d_wslot, &h->d_wnext})
+                    &h->d_wslot, &h->d_wnext, &h->d_pa_rp, &h->d_pa_ci, &h->d_pa_v, &h->d_pb_rp, &h->d_pb_ci,
+                    &h->d_pb_v, &h->d_pbase})
     b->release();
   for (void* p : {h->h_bdesc, h->h_bdesc2, h->h_boff})
     if (p) cudaFreeHost(p);

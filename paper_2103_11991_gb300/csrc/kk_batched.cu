@@ -553,3 +553,51 @@ cudaError_t launch_b_offsets(cudaStream_t s, int32_t count, const PairDesc* d, l
 }
 
 }  // namespace kk
+
+// --------------------------------------------------------------------------
+// Packed batch: the pairs as one block-diagonal product
+// --------------------------------------------------------------------------
+namespace kk {
+namespace {
+
+// One CTA per pair: A_k's rows go to packed rows [R_k, R_k + A_k.m) with
+// columns shifted to B_k's packed rows; B_k's rows go to [RB_k, RB_k + B_k.m)
+// with their columns unchanged (C_k's columns stay local to the pair).
+// vals_only: copy values only (numeric calls on the same structure).
+__global__ void k_b_pack(int32_t count, const PairDesc* __restrict__ d,
+                         const long long* __restrict__ base, int32_t vals_only, int32_t* pa_rp,
+                         int32_t* pa_ci, double* pa_v, int32_t* pb_rp, int32_t* pb_ci, double* pb_v,
+                         long long RA, long long NA, long long RB, long long NB) {
+  for (int k = blockIdx.x; k < count; k += gridDim.x) {
+    const CsrView A = d[k].A, B = d[k].B;
+    // base[4k ..]: A rows, A entries, B rows, B entries before pair k
+    const long long ra = base[4 * k], na = base[4 * k + 1], rb = base[4 * k + 2], nb = base[4 * k + 3];
+    if (!vals_only) {
+      for (int r = threadIdx.x; r < A.m; r += blockDim.x) pa_rp[ra + r] = (int32_t)(na + A.rowptr[r]);
+      for (int q = threadIdx.x; q < A.nnz; q += blockDim.x) pa_ci[na + q] = (int32_t)(rb + A.colind[q]);
+      for (int r = threadIdx.x; r < B.m; r += blockDim.x) pb_rp[rb + r] = (int32_t)(nb + B.rowptr[r]);
+      for (int q = threadIdx.x; q < B.nnz; q += blockDim.x) pb_ci[nb + q] = B.colind[q];
+    }
+    for (int q = threadIdx.x; q < A.nnz; q += blockDim.x) pa_v[na + q] = A.vals ? A.vals[q] : 0.0;
+    for (int q = threadIdx.x; q < B.nnz; q += blockDim.x) pb_v[nb + q] = B.vals ? B.vals[q] : 0.0;
+  }
+  if (!vals_only && blockIdx.x == 0 && threadIdx.x == 0) {
+    pa_rp[RA] = (int32_t)NA;
+    pb_rp[RB] = (int32_t)NB;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_b_pack(cudaStream_t s, int num_sms, int32_t count, const PairDesc* d,
+                          const long long* base, bool vals_only, int32_t* pa_rp, int32_t* pa_ci,
+                          double* pa_v, int32_t* pb_rp, int32_t* pb_ci, double* pb_v, long long RA,
+                          long long NA, long long RB, long long NB) {
+  if (count <= 0) return cudaSuccess;
+  const int grid = count < num_sms * 8 ? count : num_sms * 8;
+  k_b_pack<<<grid, 256, 0, s>>>(count, d, base, vals_only ? 1 : 0, pa_rp, pa_ci, pa_v, pb_rp, pb_ci,
+                                pb_v, RA, NA, RB, NB);
+  return cudaGetLastError();
+}
+
+}  // namespace kk

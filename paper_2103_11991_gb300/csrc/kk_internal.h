@@ -210,6 +210,12 @@ struct BBinTable {
   long long hi[kMaxBBins];
 };
 void batched_bin_tables(BBinTable& sym, BBinTable& num, int sym_load_pct, int num_load_pct);
+// Packed batch (block-diagonal A and B for the plain kernels); base holds per
+// pair the A rows, A entries, B rows and B entries that precede it.
+cudaError_t launch_b_pack(cudaStream_t s, int num_sms, int32_t count, const PairDesc* d,
+                          const long long* base, bool vals_only, int32_t* pa_rp, int32_t* pa_ci,
+                          double* pa_v, int32_t* pb_rp, int32_t* pb_ci, double* pb_v, long long RA,
+                          long long NA, long long RB, long long NB);
 cudaError_t launch_b_prepare(cudaStream_t s, int num_sms, int32_t count, PairDesc* d, long long R,
                              int32_t* row_pair, int* status);
 cudaError_t launch_b_analyze_a(cudaStream_t s, int num_sms, long long R, const PairDesc* d,

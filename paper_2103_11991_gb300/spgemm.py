@@ -51,7 +51,7 @@ class KkOptions(ctypes.Structure):
                 ("num_cta_max_nnz", ctypes.c_int32), ("use_window", ctypes.c_int32),
                 ("batched_graph", ctypes.c_int32), ("sym_load_pct", ctypes.c_int32),
                 ("num_load_pct", ctypes.c_int32), ("structure_cache", ctypes.c_int32),
-                ("wide_cache_mb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("wide_cache_mb", ctypes.c_int32), ("batched_mode", ctypes.c_int32)]
 
 
 # exported symbol -> (restype, argtypes)

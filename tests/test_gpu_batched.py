@@ -34,9 +34,10 @@ def _pairs(count, seed0, rows_hi=3000):
     return pairs
 
 
+@pytest.mark.parametrize("mode", [1, 2])  # persistent work queue / packed block-diagonal
 @pytest.mark.parametrize("graph", [0, 1])
 @pytest.mark.parametrize("arith", [1, 2])
-def test_batched_matches_oracle(graph, arith):
+def test_batched_matches_oracle(graph, arith, mode):
     import torch
     from paper_2103_11991_gb300 import spgemm as K
     pairs = _pairs(40, 7000)
@@ -45,7 +46,7 @@ def test_batched_matches_oracle(graph, arith):
     stream = torch.cuda.Stream() if graph else None
     ctx = torch.cuda.stream(stream) if stream is not None else torch.cuda.stream(torch.cuda.current_stream())
     with ctx:
-        with K.BatchedSpGEMM(stream=stream, batched_graph=graph, arith=arith) as op:
+        with K.BatchedSpGEMM(stream=stream, batched_graph=graph, arith=arith, batched_mode=mode) as op:
             for rep in range(2):  # second round replays the captured graphs
                 rowptr, off, total = op.symbolic(dA, dB)
                 colind, vals = op.numeric(dA, dB, rowptr, total)
@@ -70,3 +71,19 @@ def test_batched_empty_batch():
         rowptr = torch.zeros(1, dtype=torch.int64, device="cuda")
         off, total = K.kk_spgemm_batched_symbolic(op.h, [], [], rowptr)
         assert total == 0 and list(off) == [0]
+
+
+def test_batched_packed_moved_arrays():
+    # numeric with the same patterns in other arrays: the packed batch is rebuilt
+    import torch
+    from paper_2103_11991_gb300 import spgemm as K
+    pairs = _pairs(12, 7100)
+    dA = [K.DeviceCSR.from_host(A) for A, _ in pairs]
+    dB = [K.DeviceCSR.from_host(B) for _, B in pairs]
+    with K.BatchedSpGEMM(batched_mode=2) as op:
+        rowptr, off, total = op.symbolic(dA, dB)
+        dA2 = [K.DeviceCSR(d.m, d.n, d.rowptr.clone(), d.colind.clone(), d.vals.clone()) for d in dA]
+        colind, vals = op.numeric(dA2, dB, rowptr, total)
+        op.sync()
+        torch.cuda.synchronize()
+        _check_batch(pairs, rowptr, off, colind[:total], vals[:total])
