@@ -137,17 +137,18 @@ struct BinTable {
   int32_t mode[kMaxBins];  // 0 vector, 1 flattened, 2 either, 3 thread tier (flop capped too)
   long long thread_flop;
   int32_t nwin;
-  int32_t win_bits[kNumWindowClasses];
-  int32_t win_bin[kNumWindowClasses];
-  long long win_max_q;
+  int32_t win_bits[kMaxWindowBins];
+  int32_t win_bin[kMaxWindowBins];
+  long long win_q[kMaxWindowBins];      // largest binning quantity of each window bin
+  long long win_ratio[kMaxWindowBins];  // window W only when W <= ratio * flop
 };
 
 __device__ __forceinline__ uint8_t classify(const BinTable& t, long long q, int flat, int span,
                                             long long flop, int sorted) {
   if (q <= 0) return kSkipBin;
-  if (sorted && span > 0 && q <= t.win_max_q) {
+  if (sorted && span > 0) {
     for (int w = 0; w < t.nwin; ++w)
-      if (span <= t.win_bits[w] && (long long)t.win_bits[w] <= (long long)kWindowFlopRatio * flop)
+      if (q <= t.win_q[w] && span <= t.win_bits[w] && (long long)t.win_bits[w] <= t.win_ratio[w] * flop)
         return (uint8_t)t.win_bin[w];
   }
   for (int b = 0; b < t.nb; ++b) {
@@ -696,6 +697,10 @@ void build_bins(const kk_spgemm_options& o, bool numeric, std::vector<BinSpec>& 
     for (int w = 0; w < kNumWindowClasses; ++w)
       out.push_back(BinSpec{kTierWindow, 128, kWindowBits[w], 0, 0,
                             numeric ? kWindowMaxNnz : (long long)9e18});
+    // numeric rows of up to kWindowMaxNnzWide columns: large value arrays
+    if (numeric)
+      for (int w = 0; w < kNumWideWindowClasses; ++w)
+        out.push_back(BinSpec{kTierWindow, 128, kWideWindowBits[w], 0, 0, kWindowMaxNnzWide});
   }
 }
 
@@ -703,12 +708,15 @@ BinTable to_table(const std::vector<BinSpec>& bins) {
   BinTable t{};
   t.nb = 0;
   t.nwin = 0;
-  t.win_max_q = 0;
   for (size_t b = 0; b < bins.size(); ++b) {
     if (bins[b].tier == kTierWindow) {
       t.win_bits[t.nwin] = bins[b].slots;
       t.win_bin[t.nwin] = (int32_t)b;
-      t.win_max_q = bins[b].hi;
+      t.win_q[t.nwin] = bins[b].hi;
+      // large-value numeric bins admit sparser rows: their cost does not grow with W
+      t.win_ratio[t.nwin] = bins[b].hi > kWindowMaxNnz && bins[b].hi <= kWindowMaxNnzWide
+                                ? kWindowFlopRatioNum
+                                : kWindowFlopRatio;
       ++t.nwin;
     } else {
       t.nb = (int32_t)b + 1;

@@ -59,7 +59,13 @@ __host__ __device__ constexpr int32_t window_bits(int w) {
   return w == 0 ? 4096 : w == 1 ? 12288 : w == 2 ? 24576 : w == 3 ? 40960 : 65536;
 }
 constexpr int32_t kWindowMaxNnz = 256;   // numeric window rows: nnz(C(i,:)) <= this
-constexpr int32_t kWindowFlopRatio = 128;  // window used only when W <= ratio * flop
+constexpr int32_t kWindowMaxNnzWide = 1024;  // ... or this, in the large-value window bins
+constexpr int32_t kWindowFlopRatio = 128;  // symbolic window used only when W <= ratio * flop
+constexpr int32_t kWindowFlopRatioNum = 512;  // large-value numeric window bins
+// Large-value numeric window bins (nnz(C(i,:)) in (kWindowMaxNnz, kWindowMaxNnzWide]).
+constexpr int kNumWideWindowClasses = 3;
+constexpr int32_t kWideWindowBits[kNumWideWindowClasses] = {24576, 40960, 65536};
+constexpr int kMaxWindowBins = kNumWindowClasses + kNumWideWindowClasses;
 
 // Compressed B (the paper's B_C): row j of B as (column >> 5, 32-bit column
 // mask) pairs in column order, stored at B's own row offsets

@@ -54,17 +54,17 @@ struct SymWinGeom : WinWords<W> {
   static constexpr size_t kWarpBytes = al16(kListOff + (size_t)kCacheWords * 2);
 };
 
-template <int W>
+template <int W, int VMAX = kWindowMaxNnz>
 struct NumWinGeom : WinWords<W> {
   using WinWords<W>::WORDS;
   using WinWords<W>::SUMS;
-  // bits u32[WORDS] | sum u32[SUMS] | prefix u16[WORDS] | list u16[kWindowMaxNnz]
-  // | vacc u64[kWindowMaxNnz + 2] (the last ones: spare slot) | ainfo int4[32]
+  // bits u32[WORDS] | sum u32[SUMS] | prefix u16[WORDS] | list u16[VMAX]
+  // | vacc u64[VMAX + 2] (the last ones: spare slot) | ainfo int4[32]
   static constexpr size_t kSumOff = al16((size_t)WORDS * 4);
   static constexpr size_t kPreOff = al16(kSumOff + (size_t)SUMS * 4);
   static constexpr size_t kListOff = al16(kPreOff + (size_t)WORDS * 2);
-  static constexpr size_t kValOff = al16(kListOff + (size_t)kWindowMaxNnz * 2);
-  static constexpr size_t kInfoOff = al16(kValOff + (size_t)(kWindowMaxNnz + 2) * 8);
+  static constexpr size_t kValOff = al16(kListOff + (size_t)VMAX * 2);
+  static constexpr size_t kInfoOff = al16(kValOff + (size_t)(VMAX + 2) * 8);
   static constexpr size_t kWarpBytes = kInfoOff + 32 * 16;
 };
 
@@ -288,8 +288,8 @@ k_sym_window(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ row_
 }
 
 // Rank of column o (relative to the window) from the bits and prefixes, or
-// the spare slot kWindowMaxNnz when o is not a column of the row.
-template <int WORDS>
+// the spare slot VMAX when o is not a column of the row.
+template <int WORDS, int VMAX>
 __device__ __forceinline__ int window_rank(const uint32_t* bits, const uint16_t* pre, uint32_t o,
                                            bool ok, int& missing) {
   const uint32_t w = min(o >> 5, (uint32_t)(WORDS - 1));
@@ -297,14 +297,14 @@ __device__ __forceinline__ int window_rank(const uint32_t* bits, const uint16_t*
   const bool member = ok && o < (uint32_t)(WORDS * 32) && ((word >> (o & 31)) & 1u);
   if (ok && !member) missing = 1;
   const int r = (int)pre[w] + __popc(word & ((1u << (o & 31)) - 1u));
-  return member ? min(r, kWindowMaxNnz) : kWindowMaxNnz;
+  return member ? min(r, VMAX) : VMAX;
 }
 
 // SPEC = true: speculative one-pass of the learned form.  c_rowptr then holds
 // staging offsets, c_colind / c_vals the staging arrays, cap[i] the row's
 // predicted capacity; a row with more columns than its capacity overflows
 // (cnt_out[i] = -1, re-run by the plain path), otherwise cnt_out[i] = nnz.
-template <int W, bool SPEC>
+template <int W, bool SPEC, int VMAX = kWindowMaxNnz>
 __global__ void __launch_bounds__(kWinWarps * 32, 4)
 k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
              const int32_t* __restrict__ row_lo, const float2* __restrict__ bspl,
@@ -313,7 +313,7 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
              int32_t* __restrict__ c_colind, double* __restrict__ c_vals, int* status,
              const int32_t* __restrict__ cap, int32_t* __restrict__ cnt_out,
              const int32_t* __restrict__ nrows_dev) {
-  using G = NumWinGeom<W>;
+  using G = NumWinGeom<W, VMAX>;
   constexpr int WORDS = G::WORDS;
   constexpr int SUMS = G::SUMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -343,10 +343,10 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
     const int lo_w = row_lo[i] >> 5;
     const int lo_c = lo_w * 32;
     const int64_t off = c_rowptr[i];
-    const int cnt = SPEC ? min(cap[i], kWindowMaxNnz) : (int)(c_rowptr[i + 1] - off);
+    const int cnt = SPEC ? min(cap[i], VMAX) : (int)(c_rowptr[i + 1] - off);
     const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
     const int Lc = (!SPEC && cache.n) ? cache.n[i] : -1;
-    for (int e = lane; e < kWindowMaxNnz; e += 32) vacc[e] = 0ull;
+    for (int e = lane; e < VMAX; e += 32) vacc[e] = 0ull;
     int L, run = 0, bad = 0;
     if (Lc >= 0 && Lc <= kCacheWords) {
       // structure kept by the symbolic phase: words, bits, prefixes, columns
@@ -383,8 +383,8 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
     } else {
       // rebuild: bits from B_C, ordered word list, prefixes and columns
       bc_set_bits<WORDS>(bits, sum, lo_w, pa, pe, acol, brp, bcomp.bc, bcomp.len, lane, status);
-      L = window_list<SUMS>(sum, list, kWindowMaxNnz, lane);
-      if (L > kWindowMaxNnz) {  // more words than a window row has columns
+      L = window_list<SUMS>(sum, list, VMAX, lane);
+      if (L > VMAX) {  // more words than a window row has columns
         for (int w = lane * 4; w < WORDS; w += 128)
           *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
         if (lane == 0) {
@@ -479,7 +479,7 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
                 }
               }
             }
-            rk[u] = window_rank<WORDS>(bits, pre, (uint32_t)(c - lo_c), ok, missing);
+            rk[u] = window_rank<WORDS, VMAX>(bits, pre, (uint32_t)(c - lo_c), ok, missing);
           }
 #pragma unroll
           for (int u = 0; u < kWinBatch; ++u) {
@@ -512,7 +512,7 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
             const int q = in.x + q0 + lane;
             const bool ok = q0 + lane < in.y;
             const int c = ok ? bcol[q] : 0;
-            const int rank = window_rank<WORDS>(bits, pre, (uint32_t)(c - lo_c), ok, missing);
+            const int rank = window_rank<WORDS, VMAX>(bits, pre, (uint32_t)(c - lo_c), ok, missing);
             if (df) {
               DF av2, b2;
               av2.hi = __int_as_float(in.z);
@@ -535,7 +535,7 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
       __syncwarp();
     }
     if (missing) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
-    const int n = min(SPEC ? run : cnt, kWindowMaxNnz);
+    const int n = min(SPEC ? run : cnt, VMAX);
     for (int e = lane; e < n; e += 32) {
       const u64 v = vacc[e];
       c_vals[off + e] = df ? df_to_double(df_unpack(v)) : __longlong_as_double((long long)v);
@@ -765,15 +765,15 @@ cudaError_t sym_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
   return cudaGetLastError();
 }
 
-template <int W, bool SPEC = false>
+template <int W, bool SPEC = false, int VMAX = kWindowMaxNnz>
 cudaError_t num_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B, const BComp& bcomp,
                        const WinCacheView& cache, const float2* b_split,
                        const int32_t* b_range_bad, int32_t arith, const int64_t* c_rowptr,
                        const int32_t* rows, int32_t nrows, int32_t* c_colind, double* c_vals,
                        const int32_t* cap = nullptr, int32_t* cnt_out = nullptr,
                        const int32_t* nrows_dev = nullptr) {
-  const size_t smem = (size_t)kWinWarps * NumWinGeom<W>::kWarpBytes;
-  auto kern = k_num_window<W, SPEC>;
+  const size_t smem = (size_t)kWinWarps * NumWinGeom<W, VMAX>::kWarpBytes;
+  auto kern = k_num_window<W, SPEC, VMAX>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid_for_rows(ctx, nrows), kWinWarps * 32, smem, ctx.stream>>>(
@@ -836,6 +836,17 @@ cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, cons
                                   int32_t* c_colind, double* c_vals) {
   if (nrows <= 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
+  if (bin.hi > kWindowMaxNnz) {  // rows of up to kWindowMaxNnzWide columns: large value array
+    timer_begin(ctx.timer, ctx.stream, "num_window");
+    e = cudaErrorInvalidValue;
+    switch (bin.slots) {
+      case 24576: e = num_window<24576, false, kWindowMaxNnzWide>(ctx, A, B, bcomp, cache, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
+      case 40960: e = num_window<40960, false, kWindowMaxNnzWide>(ctx, A, B, bcomp, cache, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
+      case 65536: e = num_window<65536, false, kWindowMaxNnzWide>(ctx, A, B, bcomp, cache, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
+    }
+    timer_end(ctx.timer, ctx.stream);
+    return e;
+  }
   const int32_t* wrows = rows;
   const int32_t* wcount = nullptr;
   if (cache.n && scratch.rows) {
