@@ -1393,10 +1393,16 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
             "readback");
     KK_CUDA(h, cudaStreamSynchronize(s), "sync");
     bool any_win = false;
-    for (int b = 0; b < nbs; ++b)
+    int64_t wide_rows = 0;
+    for (int b = 0; b < nbs; ++b) {
       if (h->sym_bins[b].tier == kTierWindow && h_start[b + 1] > h_start[b]) any_win = true;
+      if (h->sym_bins[b].tier == kTierCta || h->sym_bins[b].tier == kTierDense)
+        wide_rows += h_start[b + 1] - h_start[b];
+    }
     WinCache wcache;
     if ((st = cache_for_symbolic(h, m, any_win, av, bv, &wcache)) != KK_OK) return st;
+    if ((st = keep_for_symbolic(h, m, wide_rows, av, bv)) != KK_OK) return st;
+    ctx = ctx_of(h);
     int64_t plain_rows = 0;
     for (int b = 0; b < nbs; ++b) {
       const int cnt = h_start[b + 1] - h_start[b];

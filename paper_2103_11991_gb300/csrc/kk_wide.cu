@@ -32,8 +32,9 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWideU = 4;      // warp steps whose loads are issued together
 constexpr int kWideBlock = 1024;
 
-// Words of the column bit vector: ceil(k / 32) rounded up to a multiple of 32.
-__host__ __device__ inline int wide_words(int k) { return (((k + 31) >> 5) + 31) & ~31; }
+// Words of the column bit vector: ceil(k / 32) rounded up to a multiple of
+// 1024 (one run of 32 words per lane of every warp of the CTA).
+__host__ __device__ inline int wide_words(int k) { return (((k + 31) >> 5) + 1023) & ~1023; }
 
 // Shared memory: bits u32[words] | sum u32[words / 32] | region u8[2 * words]
 // | values f64[vcap].  The region holds either per-word prefixes (u16, rows
@@ -307,7 +308,8 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
   __shared__ WalkSmem ws;
   __shared__ int tmp[33];
   const int nsum = words >> 5;
-  const int groups = words >> 3;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps_blk = blockDim.x >> 5;
   for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4)
     *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
   for (int s = threadIdx.x; s < nsum; s += blockDim.x) sum[s] = 0u;
@@ -380,31 +382,34 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
       } else {
         wide_set_bits<false>(A, B, pa, pe, ws, bits, sum, words, bad);
       }
-      const int gpt = (groups + blockDim.x - 1) / blockDim.x;
-      const int g0 = threadIdx.x * gpt, g1 = min(groups, g0 + gpt);
+      // Each warp owns a contiguous range of words, its lanes consecutive
+      // words in it (conflict-free shared loads, and consecutive lanes write
+      // consecutive columns of C): a warp sum, the block scan of the warp
+      // sums, then per round of 32 words a warp scan gives every word its
+      // prefix, kept as a u32 per 8-word group plus a byte per word.
+      const int wpw = words / nwarps_blk;  // words per warp (words is a multiple of 32 * 32)
+      const int w0 = warp * wpw;
       int mine = 0;
-      for (int g = g0; g < g1; ++g)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) mine += __popc(bits[g * 8 + k]);
-      int run = block_exscan<int>(mine, tmp, &total);
-      for (int g = g0; g < g1; ++g) {
-        gpre[g] = (uint32_t)run;
-        int in = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int w = g * 8 + k;
-          wpre8[w] = (uint8_t)in;
-          uint32_t m = bits[w];
-          int pos = run + in;
-          in += __popc(m);
-          while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            if (pos < cnt) c_colind[off + pos] = w * 32 + b;
-            ++pos;
-          }
+      for (int j = lane; j < wpw; j += 32) mine += __popc(bits[w0 + j]);
+      mine = team_sum<32>(mine, kFull);
+      int run = block_exscan<int>(lane == 0 ? mine : 0, tmp, &total);
+      run = __shfl_sync(kFull, run, 0);
+      for (int j0 = 0; j0 < wpw; j0 += 32) {
+        const int w = w0 + j0 + lane;
+        uint32_t m = bits[w];
+        const int c = __popc(m);
+        const int incl = team_inclusive_scan<32>(c, lane, kFull);
+        int pos = run + incl - c;
+        run += __shfl_sync(kFull, incl, 31);
+        const int gbase = __shfl_sync(kFull, pos, lane & ~7);
+        if ((lane & 7) == 0) gpre[w >> 3] = (uint32_t)pos;
+        wpre8[w] = (uint8_t)(pos - gbase);
+        while (m) {
+          const int b = __ffs(m) - 1;
+          m &= m - 1;
+          if (pos < cnt) c_colind[off + pos] = w * 32 + b;
+          ++pos;
         }
-        run += in;
       }
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) c_vals[off + e] = 0.0;
     }
