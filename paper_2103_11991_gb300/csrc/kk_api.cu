@@ -164,10 +164,14 @@ __device__ __forceinline__ uint8_t classify(const BinTable& t, long long q, int 
 // ---------------------------------------------------------------------------
 // Analysis kernels
 // ---------------------------------------------------------------------------
-constexpr int kAnaTeam = 8;
-
 // A rows: flop bound, column range, symbolic bin id; optional total flops.
-__global__ void k_analyze_a(CsrView A, const int32_t* __restrict__ brp,
+// One team of T lanes per row.  The kernel is bound by its dependent gathers
+// (A column -> B row bounds -> B's first and last column), so each lane issues
+// those of U entries together and the next row's bounds are loaded while a row
+// is processed; T and U follow A's mean row length.
+template <int T, int U>
+__global__ void __launch_bounds__(256, 6)
+k_analyze_a(CsrView A, const int32_t* __restrict__ brp,
                             const int32_t* __restrict__ bcol, int32_t nb_rows,
                             const int32_t* __restrict__ b_sorted, BinTable tab,
                             int32_t vec_min_len, long long* __restrict__ flop,
@@ -175,44 +179,67 @@ __global__ void k_analyze_a(CsrView A, const int32_t* __restrict__ brp,
                             int32_t* __restrict__ row_span, unsigned long long* total_flop,
                             int* status) {
   const int sorted = *b_sorted;
-  const int tl = threadIdx.x % kAnaTeam;
-  const unsigned mask = team_mask<kAnaTeam>();
-  const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kAnaTeam;
-  const long long nteams = (long long)gridDim.x * blockDim.x / kAnaTeam;
+  const int tl = threadIdx.x % T;
+  const unsigned mask = team_mask<T>();
+  const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / T;
+  const long long nteams = (long long)gridDim.x * blockDim.x / T;
   const long long iters = (A.m + nteams - 1) / nteams;
   unsigned long long acc = 0;
-  for (long long it = 0; it < iters; ++it) {
-    const long long r = team0 + it * nteams;
+  long long r = team0;
+  int pa_n = 0, pe_n = 0;
+  if (r < A.m) {
+    pa_n = A.rowptr[r];
+    pe_n = A.rowptr[r + 1];
+  }
+  for (long long it = 0; it < iters; ++it, r += nteams) {
+    int pa = pa_n, pe = pe_n;
+    if (r + nteams < A.m) {
+      pa_n = A.rowptr[r + nteams];
+      pe_n = A.rowptr[r + nteams + 1];
+    }
     long long f = 0;
     int bad = 0;
-    int pa = 0, pe = 0;
     int lo = 0x7fffffff, hi = -1;
     if (r < A.m) {
-      pa = A.rowptr[r];
-      pe = A.rowptr[r + 1];
       if (pa < 0 || pe < pa || pe > A.nnz || (r == 0 && pa != 0)) {
         bad = 1;
         pe = pa;
       }
-      for (int p = pa + tl; p < pe; p += kAnaTeam) {
-        const int j = A.colind[p];
-        if ((unsigned)j >= (unsigned)nb_rows) {
-          bad = 1;
-          continue;
+      for (int p0 = pa; p0 < pe; p0 += T * U) {
+        int j[U], bs[U], be[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int p = p0 + u * T + tl;
+          j[u] = p < pe ? A.colind[p] : -1;
+          if (p < pe && (unsigned)j[u] >= (unsigned)nb_rows) {
+            bad = 1;
+            j[u] = -1;
+          }
         }
-        const int bs = brp[j], be = brp[j + 1];
-        f += be - bs;
-        if (sorted && be > bs) {
-          lo = min(lo, bcol[bs]);
-          hi = max(hi, bcol[be - 1]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          bs[u] = 0;
+          be[u] = 0;
+          if (j[u] >= 0) {
+            bs[u] = brp[j[u]];
+            be[u] = brp[j[u] + 1];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          f += be[u] - bs[u];
+          if (sorted && be[u] > bs[u]) {
+            lo = min(lo, bcol[bs[u]]);
+            hi = max(hi, bcol[be[u] - 1]);
+          }
         }
       }
     }
 #pragma unroll
-    for (int o = kAnaTeam / 2; o > 0; o >>= 1) {
-      f += __shfl_xor_sync(mask, f, o, kAnaTeam);
-      lo = min(lo, __shfl_xor_sync(mask, lo, o, kAnaTeam));
-      hi = max(hi, __shfl_xor_sync(mask, hi, o, kAnaTeam));
+    for (int o = T / 2; o > 0; o >>= 1) {
+      f += __shfl_xor_sync(mask, f, o, T);
+      lo = min(lo, __shfl_xor_sync(mask, lo, o, T));
+      hi = max(hi, __shfl_xor_sync(mask, hi, o, T));
     }
     if (bad) set_status(status, KK_ERR_BAD_INDEX);
     if (r < A.m && tl == 0) {
@@ -482,16 +509,70 @@ TierOfBin tier_of_bins(const std::vector<BinSpec>& bins) {
 }
 
 // ---------------------------------------------------------------------------
+// Structure fingerprint: a 64-bit sum over the elements of the index arrays
+// (A's and B's row pointers and columns) of a mix of (value, position, array),
+// order-independent so blocks add their parts atomically.  The symbolic call
+// that keeps window structure records it; a numeric call that uses that
+// structure recomputes it, and a difference (index arrays changed in place
+// behind the same pointers) is reported as a structure mismatch.
+// ---------------------------------------------------------------------------
+struct FpArrays {
+  const int32_t* p[4];
+  long long n[4];
+};
+
+__device__ __forceinline__ unsigned long long fp_mix(uint32_t x, uint32_t i, uint32_t a) {
+  uint32_t h = x * 0x9E3779B1u + (i ^ (a << 29)) * 0x85EBCA77u + a;
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  return (unsigned long long)h * 0xD6E8FEB86659FD93ull;
+}
+
+__global__ void k_fingerprint(FpArrays arr, unsigned long long* out) {
+  const int a = blockIdx.y;
+  const int32_t* __restrict__ x = arr.p[a];
+  const long long n = arr.n[a];
+  unsigned long long acc = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; q0 < n; q0 += 4 * stride) {
+    int32_t v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = q0 + u * stride < n ? x[q0 + u * stride] : 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (q0 + u * stride < n) acc += fp_mix((uint32_t)v[u], (uint32_t)(q0 + u * stride), (uint32_t)a);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+// ---------------------------------------------------------------------------
 // DF32 split of B's values, with the window check.
 // ---------------------------------------------------------------------------
+// HBM-bound: each thread keeps kSplitUnroll coalesced loads in flight.
+constexpr int kSplitUnroll = 4;
 __global__ void k_split_values(long long n, const double* __restrict__ v, float2* __restrict__ out,
                                int32_t* range_bad) {
   int bad = 0;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x) {
-    DF d;
-    bad |= df_split(v[q], d) ? 0 : 1;
-    out[q] = make_float2(d.hi, d.lo);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; q0 < n;
+       q0 += stride * kSplitUnroll) {
+    double x[kSplitUnroll];
+#pragma unroll
+    for (int u = 0; u < kSplitUnroll; ++u) {
+      const long long q = q0 + u * stride;
+      x[u] = q < n ? v[q] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kSplitUnroll; ++u) {
+      const long long q = q0 + u * stride;
+      DF d;
+      bad |= df_split(x[u], d) ? 0 : 1;
+      if (q < n) out[q] = make_float2(d.hi, d.lo);
+    }
   }
   bad = __any_sync(0xffffffffu, bad);
   if (bad && (threadIdx.x & 31) == 0) atomicOr(range_bad, 1);
@@ -607,6 +688,7 @@ struct Misc {
   unsigned long long tier_a[4];  // numeric tiers: A entries of their rows
   unsigned long long kept;       // window rows whose structure was kept
   unsigned long long bc_pairs;   // pairs of the compressed B
+  unsigned long long fp[2];      // structure fingerprints: symbolic call, numeric call
 };
 
 kk_status fail(kk_spgemm_handle h, kk_status s, const std::string& msg) {
@@ -732,7 +814,8 @@ BinTable to_table(const std::vector<BinSpec>& bins) {
 
 LaunchCtx ctx_of(kk_spgemm_handle h) {
   return LaunchCtx{h->stream, h->timer, &h->d_misc.as<Misc>()->status, h->num_sms, h->max_smem,
-                   h->d_rowlo.as<int32_t>(), h->d_flop.as<long long>(), h->keep};
+                   h->d_rowlo.as<int32_t>(), h->d_flop.as<long long>(), h->keep, h->opt.debug_checks,
+                   nullptr};
 }
 
 // Analysis of B at the start of a symbolic call; with the window tier on, the
@@ -790,9 +873,40 @@ kk_status ensure_bcomp(kk_spgemm_handle h, const CsrView& bv, BComp* out, int* b
   return KK_OK;
 }
 
+int grid_for(long long work, int per_block, int cap);
+
+// Fingerprint of A's and B's index arrays into *out (device; B's arrays are
+// skipped when they are A's).
+kk_status fingerprint(kk_spgemm_handle h, const CsrView& av, const CsrView& bv,
+                      unsigned long long* out) {
+  FpArrays arr{};
+  int na = 0;
+  long long maxn = 0;
+  auto add = [&](const int32_t* p, long long n) {
+    if (!p || n <= 0) return;
+    arr.p[na] = p;
+    arr.n[na] = n;
+    maxn = n > maxn ? n : maxn;
+    ++na;
+  };
+  add(av.rowptr, (long long)av.m + 1);
+  add(av.colind, av.nnz);
+  if (bv.rowptr != av.rowptr) add(bv.rowptr, (long long)bv.m + 1);
+  if (bv.colind != av.colind) add(bv.colind, bv.nnz);
+  KK_CUDA(h, cudaMemsetAsync(out, 0, sizeof(unsigned long long), h->stream), "memset");
+  if (na == 0) return KK_OK;
+  timer_begin(h->timer, h->stream, "fingerprint");
+  const dim3 grid(grid_for((maxn + 3) / 4, 256, h->num_sms * 4), na);
+  k_fingerprint<<<grid, 256, 0, h->stream>>>(arr, out);
+  timer_end(h->timer, h->stream);
+  KK_CUDA(h, cudaGetLastError(), "fingerprint launch");
+  return KK_OK;
+}
+
 // Structure cache for the symbolic window kernel: every row starts without
 // kept structure (n = -1); null pointers when the option is off or no row of
-// the call takes the window tier.
+// the call takes the window tier.  The index arrays' fingerprint is recorded
+// with it.
 kk_status cache_for_symbolic(kk_spgemm_handle h, int32_t m, bool any_window, const CsrView& av,
                              const CsrView& bv, WinCache* out) {
   *out = WinCache{nullptr, nullptr, nullptr, nullptr};
@@ -804,6 +918,8 @@ kk_status cache_for_symbolic(kk_spgemm_handle h, int32_t m, bool any_window, con
   KK_CUDA(h, cudaMemsetAsync(h->d_cn.p, 0xFF, sizeof(int32_t) * (size_t)m, h->stream), "memset cache");
   *out = WinCache{h->d_cw.as<uint16_t>(), h->d_cm.as<uint32_t>(), h->d_cn.as<int32_t>(),
                   &h->d_misc.as<Misc>()->kept};
+  kk_status st = fingerprint(h, av, bv, &h->d_misc.as<Misc>()->fp[0]);
+  if (st != KK_OK) return st;
   h->cache_valid = true;
   h->cache_key[0] = av.rowptr;
   h->cache_key[1] = av.colind;
@@ -853,9 +969,11 @@ void keep_for_numeric(kk_spgemm_handle h, const CsrView& av, const CsrView& bv) 
 }
 
 // The kept structure, if it belongs to these index arrays, and the scratch
-// its numeric launches need.
+// its numeric launches need.  Unless options.debug_checks asks for a check of
+// every product, the arrays' fingerprint is taken again and ctx->fingerprint
+// points the numeric kernels at both fingerprints.
 kk_status cache_view(kk_spgemm_handle h, const CsrView& av, const CsrView& bv, WinCacheView* view,
-                     WinScratch* scratch) {
+                     WinScratch* scratch, LaunchCtx* ctx) {
   *view = WinCacheView{nullptr, nullptr, nullptr};
   *scratch = WinScratch{nullptr, nullptr};
   if (!h->cache_valid || h->cache_key[0] != av.rowptr || h->cache_key[1] != av.colind ||
@@ -864,6 +982,12 @@ kk_status cache_view(kk_spgemm_handle h, const CsrView& av, const CsrView& bv, W
   KK_CUDA(h, h->d_left.ensure(sizeof(int32_t) * ((size_t)av.m + 1)), "alloc window scratch");
   *view = WinCacheView{h->d_cw.as<uint16_t>(), h->d_cm.as<uint32_t>(), h->d_cn.as<int32_t>()};
   *scratch = WinScratch{h->d_left.as<int32_t>() + 1, h->d_left.as<int32_t>()};
+  if (!h->opt.debug_checks) {
+    Misc* dm = h->d_misc.as<Misc>();
+    kk_status st = fingerprint(h, av, bv, &dm->fp[1]);
+    if (st != KK_OK) return st;
+    ctx->fingerprint = dm->fp;
+  }
   return KK_OK;
 }
 
@@ -908,6 +1032,24 @@ kk_status check_device_status(kk_spgemm_handle h, int status) {
 }
 
 }  // namespace
+
+// Analysis of A with teams of T lanes, one resident wave of blocks (the kernel
+// strides over rows).
+template <int T, int U>
+static void launch_analyze_a(kk_spgemm_handle h, const CsrView& av, const CsrView& bv, Misc* dm,
+                             cudaStream_t s) {
+  static int per_sm = 0;
+  if (per_sm == 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_analyze_a<T, U>, 256, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    per_sm = 4;
+  }
+  const int64_t m = av.m;
+  k_analyze_a<T, U><<<grid_for(m * T, 256, h->num_sms * (per_sm > 0 ? per_sm : 1)), 256, 0, s>>>(
+      av, bv.rowptr, bv.colind, bv.m, &dm->sorted, to_table(h->sym_bins), h->opt.team_vec_min_len,
+      h->d_flop.as<long long>(), h->d_sbin.as<uint8_t>(), h->d_rowlo.as<int32_t>(),
+      h->d_span.as<int32_t>(), &dm->total_flop, &dm->status);
+}
 
 extern "C" {
 
@@ -1047,10 +1189,13 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   if (m > 0) {
     timer_begin(h->timer, s, "analyze");
     if ((st = analyze_b(h, bv)) != KK_OK) return st;
-    k_analyze_a<<<grid_for((long long)m * kAnaTeam, 256, h->num_sms * 8), 256, 0, s>>>(
-        av, bv.rowptr, bv.colind, bv.m, &dm->sorted, to_table(h->sym_bins), h->opt.team_vec_min_len,
-        h->d_flop.as<long long>(), h->d_sbin.as<uint8_t>(), h->d_rowlo.as<int32_t>(),
-        h->d_span.as<int32_t>(), &dm->total_flop, &dm->status);
+    const long long avg = m > 0 ? (long long)av.nnz / m : 0;
+    if (avg <= 2)
+      launch_analyze_a<1, 2>(h, av, bv, dm, s);
+    else if (avg <= 8)
+      launch_analyze_a<4, 2>(h, av, bv, dm, s);
+    else
+      launch_analyze_a<8, 4>(h, av, bv, dm, s);
     timer_end(h->timer, s);
     KK_CUDA(h, cudaGetLastError(), "analyze launch");
     if ((st = run_binning(h, m, h->d_sbin.as<uint8_t>(), nbs, h->d_srows.as<int32_t>(), sym_start)) != KK_OK)
@@ -1173,7 +1318,7 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
     KK_CUDA(h, cudaMemsetAsync(&dm->range_bad, 0, sizeof(int32_t), s), "memset");
     if (bv.nnz > 0) {
       timer_begin(h->timer, s, "split_b");
-      k_split_values<<<grid_for(bv.nnz, 256, h->num_sms * 16), 256, 0, s>>>(
+      k_split_values<<<grid_for(bv.nnz, 256, h->num_sms * 8), 256, 0, s>>>(
           bv.nnz, bv.vals, h->d_bsplit.as<float2>(), &dm->range_bad);
       timer_end(h->timer, s);
       KK_CUDA(h, cudaGetLastError(), "split launch");
@@ -1194,7 +1339,7 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
   }
   WinCacheView wview;
   WinScratch wscratch;
-  if ((st = cache_view(h, av, bv, &wview, &wscratch)) != KK_OK) return st;
+  if ((st = cache_view(h, av, bv, &wview, &wscratch, &ctx)) != KK_OK) return st;
   for (int b = 0; b < nbn; ++b) {
     const int cnt = h->num_start[b + 1] - h->num_start[b];
     if (cnt <= 0) continue;
@@ -1349,7 +1494,7 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
     KK_CUDA(h, h->d_bsplit.ensure(sizeof(float2) * (size_t)bv.nnz), "alloc split");
     KK_CUDA(h, cudaMemsetAsync(&dm->range_bad, 0, sizeof(int32_t), s), "memset");
     timer_begin(h->timer, s, "split_b");
-    k_split_values<<<grid_for(bv.nnz, 256, h->num_sms * 16), 256, 0, s>>>(
+    k_split_values<<<grid_for(bv.nnz, 256, h->num_sms * 8), 256, 0, s>>>(
         bv.nnz, bv.vals, h->d_bsplit.as<float2>(), &dm->range_bad);
     timer_end(h->timer, s);
   }
@@ -1491,7 +1636,7 @@ kk_status kk_spgemm_learned_numeric(kk_spgemm_handle h, const kk_csr* A, const k
   }
   WinCacheView wview;
   WinScratch wscratch;
-  if ((st = cache_view(h, av, bv, &wview, &wscratch)) != KK_OK) return st;
+  if ((st = cache_view(h, av, bv, &wview, &wscratch, &ctx)) != KK_OK) return st;
   for (int b = 0; b < nbn; ++b) {
     const int cnt = h->lnum_start[b + 1] - h->lnum_start[b];
     if (cnt <= 0) continue;

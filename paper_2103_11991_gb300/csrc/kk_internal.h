@@ -33,6 +33,10 @@ struct LaunchCtx {
   const int32_t* row_lo;  // first column of each row's span window (window tier)
   const long long* flop;  // flop bound of each row (wide tier)
   WideKeep keep;          // kept wide-tier bit vectors (wide tier)
+  int debug_checks;       // options.debug_checks
+  // structure fingerprints of the index arrays at the symbolic call ([0]) and
+  // at this numeric call ([1]); null when the kept structure is not in use
+  const unsigned long long* fingerprint;
 };
 
 struct CsrView {

@@ -17,11 +17,15 @@ namespace {
 
 constexpr int kKeptSlots = 256;
 constexpr unsigned long long kKeptEmpty = ~0ull;
-constexpr int kKeptBatch = 8;  // A entries whose B loads are issued together
+// A entries whose B loads are issued together; 4 keeps the kernel within 40
+// registers (six 256-thread CTAs per SM), which measured faster than 8 at 64.
+constexpr int kKeptBatch = 4;
 
 // Rank of column o (relative to the row's first word) through the table, or
-// the spare slot kWindowMaxNnz when o is not a column of the row.
-template <bool PROBE>
+// the spare slot kWindowMaxNnz when o is not a column of the row.  CHECK =
+// false trusts that o is a column of the row (the caller has verified the
+// structure otherwise); the rank is still clamped to the spare slot.
+template <bool PROBE, bool CHECK>
 __device__ __forceinline__ int kept_rank(const unsigned long long* table, uint32_t o, bool ok, int& missing) {
   const uint32_t w = o >> 5;
   uint32_t s = w & (kKeptSlots - 1);
@@ -33,8 +37,11 @@ __device__ __forceinline__ int kept_rank(const unsigned long long* table, uint32
     }
   }
   const uint32_t word = (uint32_t)e;
-  const bool member = ok && (uint32_t)(e >> 48) == w && ((word >> (o & 31)) & 1u);
-  if (ok && !member) missing = 1;
+  bool member = ok;
+  if (CHECK) {
+    member = ok && (uint32_t)(e >> 48) == w && ((word >> (o & 31)) & 1u);
+    if (ok && !member) missing = 1;
+  }
   const int r = (int)((e >> 32) & 0xFFFFu) + __popc(word & ((1u << (o & 31)) - 1u));
   return member ? min(r, kWindowMaxNnz) : kWindowMaxNnz;
 }
@@ -44,7 +51,7 @@ __device__ __forceinline__ int kept_rank(const unsigned long long* table, uint32
 // lane loads its products of the batch and ranks them, then the batch's
 // updates go in entry order; lanes without a product update the spare slot,
 // so nothing branches per entry.
-template <int NB, bool DFM, bool PROBE>
+template <int NB, bool DFM, bool PROBE, bool CHECK>
 __device__ __forceinline__ void kept_batch(const int4* ainfo, int t0, int lo_c, const unsigned long long* table,
                                            unsigned long long* vacc, const int32_t* __restrict__ bcol,
                                            const float2* __restrict__ bspl,
@@ -68,7 +75,7 @@ __device__ __forceinline__ void kept_batch(const int4* ainfo, int t0, int lo_c, 
         bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)), __int_as_float((int)(bb >> 32)));
       }
     }
-    rk[u] = kept_rank<PROBE>(table, (uint32_t)(c - lo_c), ok, missing);
+    rk[u] = kept_rank<PROBE, CHECK>(table, (uint32_t)(c - lo_c), ok, missing);
   }
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
@@ -94,8 +101,9 @@ __device__ __forceinline__ void kept_batch(const int4* ainfo, int t0, int lo_c, 
 }
 
 // Value pass over one chunk of at most 32 A entries: batches of kKeptBatch,
-// the tail in a batch of 4 or 8.
-template <bool DFM, bool PROBE>
+// a tail of 3 in one more (entries past the chunk have length 0), a tail of 1
+// or 2 in a batch of 2.
+template <bool DFM, bool PROBE, bool CHECK>
 __device__ __forceinline__ void kept_chunk(const int4* ainfo, int nch, int lo_c, const unsigned long long* table,
                                            unsigned long long* vacc, const int32_t* __restrict__ bcol,
                                            const float2* __restrict__ bspl,
@@ -103,17 +111,17 @@ __device__ __forceinline__ void kept_chunk(const int4* ainfo, int nch, int lo_c,
                                            int& missing) {
   int t0 = 0;
   for (; t0 + kKeptBatch <= nch; t0 += kKeptBatch)
-    kept_batch<kKeptBatch, DFM, PROBE>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+    kept_batch<kKeptBatch, DFM, PROBE, CHECK>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
   const int rem = nch - t0;
-  if (rem > 4)
-    kept_batch<kKeptBatch, DFM, PROBE>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+  if (rem > 2)
+    kept_batch<kKeptBatch, DFM, PROBE, CHECK>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
   else if (rem > 0)
-    kept_batch<4, DFM, PROBE>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+    kept_batch<2, DFM, PROBE, CHECK>(ainfo, t0, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
 }
 
 // Value pass for B rows longer than 32: one A entry at a time, lanes stride
 // the B row.
-template <bool DFM, bool PROBE>
+template <bool DFM, bool PROBE, bool CHECK>
 __device__ __forceinline__ void kept_chunk_long(const int4* ainfo, int nch, int lo_c,
                                                 const unsigned long long* table, unsigned long long* vacc,
                                                 const int32_t* __restrict__ bcol,
@@ -126,7 +134,7 @@ __device__ __forceinline__ void kept_chunk_long(const int4* ainfo, int nch, int 
       const int q = in.x + q0 + lane;
       const bool ok = q0 + lane < in.y;
       const int c = ok ? bcol[q] : 0;
-      const int rank = kept_rank<PROBE>(table, (uint32_t)(c - lo_c), ok, missing);
+      const int rank = kept_rank<PROBE, CHECK>(table, (uint32_t)(c - lo_c), ok, missing);
       if (DFM) {
         DF a, b;
         a.hi = __int_as_float(in.z);
@@ -166,7 +174,7 @@ __device__ __forceinline__ int kept_info(int p0, int pe, const int32_t* __restri
   return df_split(a, ad) ? 0 : 1;
 }
 
-template <bool PROBE>
+template <bool PROBE, bool CHECK>
 __device__ __forceinline__ void kept_store_and_run(int4 info, const DF& ad, double a, bool df,
                                                    int4* ainfo, int nch, int lo_c,
                                                    const unsigned long long* table, unsigned long long* vacc,
@@ -186,11 +194,11 @@ __device__ __forceinline__ void kept_store_and_run(int4 info, const DF& ad, doub
   __syncwarp();
   const bool shrt = __reduce_max_sync(0xffffffffu, (unsigned)info.y) <= 32u;
   if (df) {
-    if (shrt) kept_chunk<true, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
-    else kept_chunk_long<true, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+    if (shrt) kept_chunk<true, PROBE, CHECK>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+    else kept_chunk_long<true, PROBE, CHECK>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
   } else {
-    if (shrt) kept_chunk<false, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
-    else kept_chunk_long<false, PROBE>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+    if (shrt) kept_chunk<false, PROBE, CHECK>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
+    else kept_chunk_long<false, PROBE, CHECK>(ainfo, nch, lo_c, table, vacc, bcol, bspl, bval, lane, missing);
   }
   __syncwarp();
 }
@@ -198,7 +206,7 @@ __device__ __forceinline__ void kept_store_and_run(int4 info, const DF& ad, doub
 // Value pass of a row; returns whether it ran in DF32.  Rows of at most 32 A
 // entries decide the arithmetic from their own split values; longer rows
 // check all their values first.
-template <bool PROBE>
+template <bool PROBE, bool CHECK>
 __device__ __forceinline__ bool kept_values(int pa, int pe, bool df_all,
                                             const int32_t* __restrict__ acol,
                                             const double* __restrict__ aval,
@@ -215,7 +223,7 @@ __device__ __forceinline__ bool kept_values(int pa, int pe, bool df_all,
     double a;
     const int bad = kept_info(p0, pe, acol, aval, brp, lane, info, ad, a);
     if (df_all && pe - pa <= 32) df = __any_sync(0xffffffffu, bad) == 0;
-    kept_store_and_run<PROBE>(info, ad, a, df, ainfo, min(32, pe - p0), lo_c, table, vacc, bcol,
+    kept_store_and_run<PROBE, CHECK>(info, ad, a, df, ainfo, min(32, pe - p0), lo_c, table, vacc, bcol,
                               bspl, bval, lane, missing);
   }
   return df;

@@ -563,12 +563,17 @@ struct KeptGeom {
   static constexpr size_t kWarpBytes = kInfoOff + 32 * 16;
 };
 
-__global__ void __launch_bounds__(kKeptWarps * 32, 4)
+// CHECK = false: the index arrays were verified against the symbolic call by
+// their fingerprints fp[0] (symbolic) and fp[1] (this call), so products are
+// not checked one by one against the kept structure.
+template <bool CHECK>
+__global__ void __launch_bounds__(kKeptWarps * 32, 6)
 k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__ row_lo,
            const float2* __restrict__ bspl, const int32_t* __restrict__ b_range_bad, int32_t arith,
            const int64_t* __restrict__ c_rowptr, const int32_t* __restrict__ rows, int32_t nrows,
            int32_t* __restrict__ c_colind, double* __restrict__ c_vals, int* status,
-           int32_t* __restrict__ left_rows, int32_t* __restrict__ left_count) {
+           int32_t* __restrict__ left_rows, int32_t* __restrict__ left_count,
+           const unsigned long long* __restrict__ fp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* base = smem_raw + (size_t)warp * KeptGeom::kWarpBytes;
@@ -576,6 +581,8 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
   u64* vacc = reinterpret_cast<u64*>(base + KeptGeom::kValOff);
   int4* ainfo = reinterpret_cast<int4*>(base + KeptGeom::kInfoOff);
   const bool df_all = arith == kArithDF32 && *b_range_bad == 0;
+  if (!CHECK && blockIdx.x == 0 && threadIdx.x == 0 && fp[0] != fp[1])
+    set_status(status, KK_ERR_STRUCTURE_MISMATCH);
   for (int s = lane; s < kKeptSlots; s += 32) table[s] = kKeptEmpty;
   __syncwarp();
   const int nw = gridDim.x * kKeptWarps;  // rows dealt round-robin over the grid
@@ -634,10 +641,10 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
     // arithmetic of this row: DF32 unless a value of the row is outside its window
     int missing = 0;
     const bool df =
-        probe ? kept_values<true>(pa, pe, df_all, A.colind, A.vals, B.rowptr, ainfo, lo_c, table,
-                                  vacc, B.colind, bspl, B.vals, lane, missing)
-              : kept_values<false>(pa, pe, df_all, A.colind, A.vals, B.rowptr, ainfo, lo_c, table,
-                                   vacc, B.colind, bspl, B.vals, lane, missing);
+        probe ? kept_values<true, CHECK>(pa, pe, df_all, A.colind, A.vals, B.rowptr, ainfo, lo_c, table,
+                                         vacc, B.colind, bspl, B.vals, lane, missing)
+              : kept_values<false, CHECK>(pa, pe, df_all, A.colind, A.vals, B.rowptr, ainfo, lo_c,
+                                          table, vacc, B.colind, bspl, B.vals, lane, missing);
     if (missing) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
     const int n = min(cnt, kWindowMaxNnz);
     for (int e = lane; e < n; e += 32) {
@@ -648,95 +655,6 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
     if (slot0 < kKeptSlots) table[slot0] = kKeptEmpty;
     if (slot1 < kKeptSlots) table[slot1] = kKeptEmpty;
     __syncwarp();
-  }
-}
-
-// Analysis of B, one team of 8 lanes per row: rows strictly ascending?
-// columns inside [0, k)?  And, when bc is given, the compressed rows B_C:
-// row j as (column >> 5, OR of 1 << (column & 31)) pairs in column order at
-// B's own row offsets, len[j] = number of pairs (meaningful only if B turns
-// out sorted).  The team walks the row in chunks of 8 entries; the word being
-// built when a chunk ends is carried into the next chunk, so every word of a
-// sorted row gives exactly one pair.
-constexpr int kAnaBTeam = 8;
-__global__ void k_analyze_b(CsrView B, int32_t* sorted_flag, int* status, int2* __restrict__ bc,
-                            int32_t* __restrict__ len, unsigned long long* pairs) {
-  constexpr int T = kAnaBTeam;
-  const int lane = threadIdx.x & 31;
-  const int tl = lane & (T - 1);
-  const int tbase = lane & ~(T - 1);
-  const unsigned mask = team_mask<T>();
-  const unsigned lt = (1u << tl) - 1u;
-  const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / T;
-  const long long nteams = (long long)gridDim.x * blockDim.x / T;
-  int unsorted = 0, bad = 0;
-  unsigned long long tot = 0;
-  if (team0 == 0 && tl == 0 && B.rowptr[0] != 0) bad = 1;
-  for (long long r = team0; r < B.m; r += nteams) {
-    const int bs = B.rowptr[r], be = B.rowptr[r + 1];
-    if (bs < 0 || be < bs || be > B.nnz) {
-      bad = 1;
-      continue;
-    }
-    int cw = -1, n = 0;
-    uint32_t cm = 0u;
-    for (int q0 = bs; q0 < be; q0 += T) {
-      const int q = q0 + tl;
-      const bool valid = q < be;
-      const int c = valid ? B.colind[q] : 0;
-      if (valid) {
-        if ((unsigned)c >= (unsigned)B.n) bad = 1;
-        if (q > bs && B.colind[q - 1] >= c) unsorted = 1;
-      }
-      if (!bc) continue;
-      const int w = valid ? (c >> 5) : (-2 - tl);  // invalid lanes match nothing
-      uint32_t acc = valid ? (1u << (c & 31)) : 0u;
-      int pw = __shfl_up_sync(mask, w, 1, T);
-      if (tl == 0) pw = cw;
-      const bool head = valid && w != pw;
-#pragma unroll
-      for (int d = 1; d < T; d <<= 1) {
-        const uint32_t v = __shfl_down_sync(mask, acc, d, T);
-        const int w2 = __shfl_down_sync(mask, w, d, T);
-        if (tl + d < T && w2 == w) acc |= v;
-      }
-      // a chunk that starts inside the carried word adds its first segment to it
-      const uint32_t acc0 = __shfl_sync(mask, acc, 0, T);
-      const bool cont0 = __shfl_sync(mask, (int)(valid && !head), 0, T) != 0;
-      if (cont0) cm |= acc0;
-      const unsigned hm = (__ballot_sync(mask, head) >> tbase) & ((1u << T) - 1u);
-      if (hm) {
-        // a new word started: the carried pair is complete
-        if (cm) {
-          if (tl == 0) bc[bs + n] = make_int2(cw, (int)cm);
-          ++n;
-        }
-        const int last = 31 - __clz(hm);
-        if (head && tl != last) bc[bs + n + __popc(hm & lt)] = make_int2(w, (int)acc);
-        n += __popc(hm) - 1;
-        cw = __shfl_sync(mask, w, last, T);
-        cm = __shfl_sync(mask, acc, last, T);
-      }
-    }
-    if (bc) {
-      if (cm) {
-        if (tl == 0) bc[bs + n] = make_int2(cw, (int)cm);
-        ++n;
-      }
-      if (tl == 0) {
-        len[r] = n;
-        tot += (unsigned long long)n;
-      }
-    }
-  }
-  unsorted = __any_sync(kFull, unsorted);
-  bad = __any_sync(kFull, bad);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(kFull, tot, o);
-  if (lane == 0) {
-    if (unsorted) atomicAnd(sorted_flag, 0);
-    if (bad) set_status(status, KK_ERR_BAD_INDEX);
-    if (tot && pairs) atomicAdd(pairs, tot);
   }
 }
 
@@ -776,7 +694,11 @@ cudaError_t num_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
   auto kern = k_num_window<W, SPEC, VMAX>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid_for_rows(ctx, nrows), kWinWarps * 32, smem, ctx.stream>>>(
+  int grid = grid_for_rows(ctx, nrows);
+  // a device-side row count (the leftover pass) is usually small or zero:
+  // one wave of the kernel's minimum residency strides over it
+  if (nrows_dev && grid > ctx.num_sms * 4) grid = ctx.num_sms * 4;
+  kern<<<grid, kWinWarps * 32, smem, ctx.stream>>>(
       A, B, bcomp, cache, ctx.row_lo, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind,
       c_vals, ctx.status, cap, cnt_out, nrows_dev);
   return cudaGetLastError();
@@ -787,29 +709,22 @@ cudaError_t num_kept(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
                      int32_t arith, const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
                      int32_t* c_colind, double* c_vals, int32_t* left_rows, int32_t* left_count) {
   const size_t smem = (size_t)kKeptWarps * KeptGeom::kWarpBytes;
-  cudaError_t e = set_smem(k_num_kept, smem);
+  const bool check = ctx.fingerprint == nullptr;
+  auto kern = check ? k_num_kept<true> : k_num_kept<false>;
+  cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   long long blocks = (nrows + kKeptWarps * 4 - 1) / (kKeptWarps * 4);
   const long long capb = (long long)ctx.num_sms * 16;
   if (blocks > capb) blocks = capb;
   if (blocks < 1) blocks = 1;
-  k_num_kept<<<(int)blocks, kKeptWarps * 32, smem, ctx.stream>>>(
+  kern<<<(int)blocks, kKeptWarps * 32, smem, ctx.stream>>>(
       A, B, cache, ctx.row_lo, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals,
-      ctx.status, left_rows, left_count);
+      ctx.status, left_rows, left_count, ctx.fingerprint);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_analyze_b(const LaunchCtx& ctx, const CsrView& B, int32_t* sorted_flag,
-                             int2* bc, int32_t* len, unsigned long long* pairs) {
-  if (B.m <= 0) return cudaSuccess;
-  long long blocks = ((long long)B.m * kAnaBTeam + 255) / 256;
-  const long long cap = (long long)ctx.num_sms * 8;
-  if (blocks > cap) blocks = cap;
-  k_analyze_b<<<(int)blocks, 256, 0, ctx.stream>>>(B, sorted_flag, ctx.status, bc, len, pairs);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_symbolic_window(const LaunchCtx& ctx, const BinSpec& bin, const CsrView& A,
                                    const CsrView& B, const BComp& bcomp, const int32_t* rows,

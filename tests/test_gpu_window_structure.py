@@ -77,13 +77,36 @@ def test_kept_structure_only_for_its_arrays():
         check_against_oracle(A, A, rp.cpu().numpy(), c1.cpu().numpy(), v1.cpu().numpy())
 
 
-@pytest.mark.parametrize("cache", [0, 1])
-def test_changed_structure_behind_same_arrays_is_reported(cache):
+def test_kept_structure_with_new_values_in_place():
+    # symbolic reuse: new values written into the same arrays keep the
+    # fingerprint, so the kept structure is used and C follows the new values
+    import torch
+    from paper_2103_11991_gb300 import spgemm as K
+    A = _stencil_random(12, 31)
+    dA = K.DeviceCSR.from_host(A)
+    with K.SpGEMM() as op:
+        rp, nnz = op.symbolic(dA, dA)
+        assert op.stats()["kept_structure_rows"] > 0
+        ci, va = op.numeric(dA, dA, rp, nnz)
+        for seed in (32, 33):
+            vals = I.uniform01(seed, "ws", A.nnz) * 2 - 1
+            dA.vals.copy_(torch.from_numpy(vals).cuda())
+            op.numeric(dA, dA, rp, nnz, ci, va)
+            op.sync()
+            A2 = I.CSR(A.m, A.n, A.rowptr, A.colind, vals)
+            check_against_oracle(A2, A2, rp.cpu().numpy(), ci.cpu().numpy(), va.cpu().numpy())
+
+
+@pytest.mark.parametrize("cache,debug", [(0, 0), (1, 0), (1, 1)])
+def test_changed_structure_behind_same_arrays_is_reported(cache, debug):
+    # cache 0: the rebuilt structure misses products of the new B; cache 1: the
+    # index arrays' fingerprint differs from the symbolic call's (debug 0) or a
+    # product falls outside the kept structure (debug 1, checked one by one)
     import torch
     from paper_2103_11991_gb300 import spgemm as K
     A = I.config_inputs("stencil3d27_100", scale=10)["A"]
     dA, dB = K.DeviceCSR.from_host(A), K.DeviceCSR.from_host(A)
-    with K.SpGEMM(structure_cache=cache) as op:
+    with K.SpGEMM(structure_cache=cache, debug_checks=debug) as op:
         rp, nnz = op.symbolic(dA, dB)
         st = op.stats()
         assert st["sym_window_rows"] == A.m and st["num_window_rows"] == A.m
