@@ -140,6 +140,7 @@ struct BinTable {
   int32_t win_bits[kMaxWindowBins];
   int32_t win_bin[kMaxWindowBins];
   long long win_q[kMaxWindowBins];      // largest binning quantity of each window bin
+  long long win_qlo[kMaxWindowBins];    // binning quantity must exceed this
   long long win_ratio[kMaxWindowBins];  // window W only when W <= ratio * flop
 };
 
@@ -148,7 +149,8 @@ __device__ __forceinline__ uint8_t classify(const BinTable& t, long long q, int 
   if (q <= 0) return kSkipBin;
   if (sorted && span > 0) {
     for (int w = 0; w < t.nwin; ++w)
-      if (q <= t.win_q[w] && span <= t.win_bits[w] && (long long)t.win_bits[w] <= t.win_ratio[w] * flop)
+      if (q > t.win_qlo[w] && q <= t.win_q[w] && span <= t.win_bits[w] &&
+          (long long)t.win_bits[w] <= t.win_ratio[w] * flop)
         return (uint8_t)t.win_bin[w];
   }
   for (int b = 0; b < t.nb; ++b) {
@@ -531,22 +533,52 @@ __device__ __forceinline__ unsigned long long fp_mix(uint32_t x, uint32_t i, uin
   return (unsigned long long)h * 0xD6E8FEB86659FD93ull;
 }
 
-__global__ void k_fingerprint(FpArrays arr, unsigned long long* out) {
+// blockIdx.y = the array.  The aligned middle of the array is read as int4 with
+// kFpUnroll loads in flight per thread (the pass is bound by HBM latency and
+// bandwidth); block 0 takes the few elements before the first and after the
+// last 16-byte boundary.  One atomic per block.
+constexpr int kFpUnroll = 4;
+constexpr int kFpThreads = 256;
+__global__ void __launch_bounds__(kFpThreads) k_fingerprint(FpArrays arr, unsigned long long* out) {
   const int a = blockIdx.y;
-  const int32_t* __restrict__ x = arr.p[a];
-  const long long n = arr.n[a];
-  unsigned long long acc = 0;
+  // selects instead of indexing the parameter arrays (which would go through
+  // local memory)
+  const int32_t* __restrict__ x = a == 0 ? arr.p[0] : a == 1 ? arr.p[1] : a == 2 ? arr.p[2] : arr.p[3];
+  const long long n = a == 0 ? arr.n[0] : a == 1 ? arr.n[1] : a == 2 ? arr.n[2] : arr.n[3];
+  long long head = (long long)(((16u - (unsigned)((uintptr_t)x & 15u)) & 15u) / 4u);
+  if (head > n) head = n;
+  const long long nv = (n - head) / 4;
+  const int4* __restrict__ xv = reinterpret_cast<const int4*>(x + head);
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; q0 < n; q0 += 4 * stride) {
-    int32_t v[4];
+  unsigned long long acc = 0;
+  for (long long v0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; v0 < nv; v0 += kFpUnroll * stride) {
+    int4 w[kFpUnroll];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = q0 + u * stride < n ? x[q0 + u * stride] : 0;
+    for (int u = 0; u < kFpUnroll; ++u)
+      w[u] = v0 + u * stride < nv ? xv[v0 + u * stride] : make_int4(0, 0, 0, 0);
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (q0 + u * stride < n) acc += fp_mix((uint32_t)v[u], (uint32_t)(q0 + u * stride), (uint32_t)a);
+    for (int u = 0; u < kFpUnroll; ++u) {
+      if (v0 + u * stride < nv) {
+        const uint32_t i = (uint32_t)(head + (v0 + u * stride) * 4);
+        acc += fp_mix((uint32_t)w[u].x, i, a) + fp_mix((uint32_t)w[u].y, i + 1, a) +
+               fp_mix((uint32_t)w[u].z, i + 2, a) + fp_mix((uint32_t)w[u].w, i + 3, a);
+      }
+    }
   }
+  if (blockIdx.x == 0) {
+    for (long long q = threadIdx.x; q < head; q += blockDim.x) acc += fp_mix((uint32_t)x[q], (uint32_t)q, a);
+    for (long long q = head + nv * 4 + threadIdx.x; q < n; q += blockDim.x)
+      acc += fp_mix((uint32_t)x[q], (uint32_t)q, a);
+  }
+  __shared__ unsigned long long part[kFpThreads / 32];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int k = 0; k < kFpThreads / 32; ++k) t += part[k];
+    if (t) atomicAdd(out, t);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -795,10 +827,13 @@ BinTable to_table(const std::vector<BinSpec>& bins) {
       t.win_bits[t.nwin] = bins[b].slots;
       t.win_bin[t.nwin] = (int32_t)b;
       t.win_q[t.nwin] = bins[b].hi;
-      // large-value numeric bins admit sparser rows: their cost does not grow with W
-      t.win_ratio[t.nwin] = bins[b].hi > kWindowMaxNnz && bins[b].hi <= kWindowMaxNnzWide
-                                ? kWindowFlopRatioNum
-                                : kWindowFlopRatio;
+      // large-value numeric bins take only rows of more than kWindowMaxNnz
+      // columns (sparser rows than the ratio of the others admits: their cost
+      // follows the touched words rather than W); rows of fewer columns that
+      // miss the other window bins go to the hash tiers
+      const bool large = bins[b].hi > kWindowMaxNnz && bins[b].hi <= kWindowMaxNnzWide;
+      t.win_ratio[t.nwin] = large ? kWindowFlopRatioNum : kWindowFlopRatio;
+      t.win_qlo[t.nwin] = large ? kWindowMaxNnz : 0;
       ++t.nwin;
     } else {
       t.nb = (int32_t)b + 1;
@@ -896,8 +931,8 @@ kk_status fingerprint(kk_spgemm_handle h, const CsrView& av, const CsrView& bv,
   KK_CUDA(h, cudaMemsetAsync(out, 0, sizeof(unsigned long long), h->stream), "memset");
   if (na == 0) return KK_OK;
   timer_begin(h->timer, h->stream, "fingerprint");
-  const dim3 grid(grid_for((maxn + 3) / 4, 256, h->num_sms * 4), na);
-  k_fingerprint<<<grid, 256, 0, h->stream>>>(arr, out);
+  const dim3 grid(grid_for((maxn + 4 * kFpUnroll - 1) / (4 * kFpUnroll), kFpThreads, h->num_sms * 4), na);
+  k_fingerprint<<<grid, kFpThreads, 0, h->stream>>>(arr, out);
   timer_end(h->timer, h->stream);
   KK_CUDA(h, cudaGetLastError(), "fingerprint launch");
   return KK_OK;
