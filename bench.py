@@ -443,62 +443,39 @@ def run_ours(args, rank, world, local_rank):
     kernels = {k: {"ms_per_step": v[0] / reps, "launches_per_step": v[1] / reps} for k, v in kt.items()}
 
     # end to end through the API with host buffers: H2D of A (pinned), both
-    # phases, D2H of C (row pointers, columns, values) every step.  Measured
-    # twice: serially on one stream, and pipelined over two handles on two
-    # streams (step k's D2H of C runs while step k+1 copies its A in and
-    # computes), which is how a stream of independent products is served.
+    # phases, D2H of C (row pointers, columns, values) every step, on one
+    # stream.  (Overlapping step k's D2H of C with step k+1 on a second stream
+    # does not pay: the symbolic phase's small nnz read-back queues behind the
+    # large D2H on the copy engine.)
     hA = {k: torch.from_numpy(np.ascontiguousarray(getattr(A, k))).pin_memory()
           for k in ("rowptr", "colind", "vals")}
+    hC_rp = torch.empty(A.m + 1, dtype=torch.int64).pin_memory()
+    hC_ci = torch.empty(nnz, dtype=torch.int32).pin_memory()
+    hC_va = torch.empty(nnz, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 5))
     h2d = sum(t.numel() * t.element_size() for t in hA.values())
-    d2h = ((A.m + 1) * 8) + nnz * 12
+    d2h = (hC_rp.numel() * 8) + nnz * 12
 
-    def host_out():
-        return (torch.empty(A.m + 1, dtype=torch.int64).pin_memory(),
-                torch.empty(nnz, dtype=torch.int32).pin_memory(),
-                torch.empty(nnz, dtype=torch.float64).pin_memory())
-
-    def e2e_step(h, dci, dva, hout):
+    def e2e_step():
         gA = K.DeviceCSR(A.m, A.n, hA["rowptr"].cuda(non_blocking=True),
                          hA["colind"].cuda(non_blocking=True), hA["vals"].cuda(non_blocking=True))
-        grp, gnnz = h.symbolic(gA, gA)
-        gci, gva = h.numeric(gA, gA, grp, gnnz, dci, dva)
-        hout[0].copy_(grp, non_blocking=True)
-        hout[1].copy_(gci, non_blocking=True)
-        hout[2].copy_(gva, non_blocking=True)
+        grp, gnnz = op.symbolic(gA, gA)
+        gci, gva = op.numeric(gA, gA, grp, gnnz, ci, va)
+        hC_rp.copy_(grp, non_blocking=True)
+        hC_ci.copy_(gci, non_blocking=True)
+        hC_va.copy_(gva, non_blocking=True)
 
-    def timed(fn):
-        fn(0)  # warm-up of both slots (handle scratch, host buffers)
-        fn(1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(e2e_steps):
-            fn(k)
-        torch.cuda.synchronize()
-        t = (time.perf_counter() - t0) * 1e3 / e2e_steps
-        if dist:
-            tt = torch.tensor([t], device="cuda")
-            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-            t = float(tt.item())
-        return t
-
-    hout0 = host_out()
-    e2e_serial_ms = timed(lambda k: e2e_step(op, ci, va, hout0))
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    pops = [K.SpGEMM(stream=st_) for st_ in streams]
-    pbuf = [(torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda"),
-             torch.empty(max(nnz, 1), dtype=torch.float64, device="cuda")) for _ in streams]
-    houts = [hout0, host_out()]
+    e2e_step()
     torch.cuda.synchronize()
-
-    def piped(k):
-        with torch.cuda.stream(streams[k % 2]):
-            e2e_step(pops[k % 2], pbuf[k % 2][0], pbuf[k % 2][1], houts[k % 2])
-
-    e2e_ms = timed(piped)
-    for h_ in pops:
-        h_.close()
-    del pbuf, houts, hout0
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
     e2e_value = 2.0 * madds * world / (e2e_ms * 1e-3) / 1e9
 
     forms = {}
@@ -529,9 +506,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "streams": 2,
-                    "serial_ms_per_step": e2e_serial_ms,
-                    "serial_value": 2.0 * madds * world / (e2e_serial_ms * 1e-3) / 1e9},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": int(round(launches_per_step)) * args.steps,
             "clocks": clk,
             "kernels": kernels,
