@@ -813,8 +813,9 @@ void build_bins(const kk_spgemm_options& o, bool numeric, std::vector<BinSpec>& 
                             numeric ? kWindowMaxNnz : (long long)9e18});
     // numeric rows of up to kWindowMaxNnzWide columns: large value arrays
     if (numeric)
-      for (int w = 0; w < kNumWideWindowClasses; ++w)
-        out.push_back(BinSpec{kTierWindow, 128, kWideWindowBits[w], 0, 0, kWindowMaxNnzWide});
+      for (const int32_t vmax : {kWindowMidNnz, kWindowMaxNnzWide})
+        for (int w = 0; w < kNumWideWindowClasses; ++w)
+          out.push_back(BinSpec{kTierWindow, 128, kWideWindowBits[w], 0, 0, vmax});
   }
 }
 

@@ -66,10 +66,13 @@ constexpr int32_t kWindowMaxNnz = 256;   // numeric window rows: nnz(C(i,:)) <= 
 constexpr int32_t kWindowMaxNnzWide = 1024;  // ... or this, in the large-value window bins
 constexpr int32_t kWindowFlopRatio = 128;  // symbolic window used only when W <= ratio * flop
 constexpr int32_t kWindowFlopRatioNum = 512;  // large-value numeric window bins
-// Large-value numeric window bins (nnz(C(i,:)) in (kWindowMaxNnz, kWindowMaxNnzWide]).
+// Large-value numeric window bins (nnz(C(i,:)) in (kWindowMaxNnz, kWindowMaxNnzWide]),
+// with value arrays of kWindowMidNnz or kWindowMaxNnzWide slots (the smaller
+// array leaves room for more warps per SM).
+constexpr int32_t kWindowMidNnz = 512;
 constexpr int kNumWideWindowClasses = 3;
 constexpr int32_t kWideWindowBits[kNumWideWindowClasses] = {24576, 40960, 65536};
-constexpr int kMaxWindowBins = kNumWindowClasses + kNumWideWindowClasses;
+constexpr int kMaxWindowBins = kNumWindowClasses + 2 * kNumWideWindowClasses;
 
 // Compressed B (the paper's B_C): row j of B as (column >> 5, 32-bit column
 // mask) pairs in column order, stored at B's own row offsets

@@ -346,7 +346,9 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
     const int cnt = SPEC ? min(cap[i], VMAX) : (int)(c_rowptr[i + 1] - off);
     const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
     const int Lc = (!SPEC && cache.n) ? cache.n[i] : -1;
-    for (int e = lane; e < VMAX; e += 32) vacc[e] = 0ull;
+    // value slots of the row's columns (a rank past cnt goes to the spare slot
+    // VMAX, which is never read)
+    for (int e = lane; e < min(cnt, VMAX); e += 32) vacc[e] = 0ull;
     int L, run = 0, bad = 0;
     if (Lc >= 0 && Lc <= kCacheWords) {
       // structure kept by the symbolic phase: words, bits, prefixes, columns
@@ -754,11 +756,25 @@ cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, cons
   if (bin.hi > kWindowMaxNnz) {  // rows of up to kWindowMaxNnzWide columns: large value array
     timer_begin(ctx.timer, ctx.stream, "num_window");
     e = cudaErrorInvalidValue;
-    switch (bin.slots) {
-      case 24576: e = num_window<24576, false, kWindowMaxNnzWide>(ctx, A, B, bcomp, cache, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
-      case 40960: e = num_window<40960, false, kWindowMaxNnzWide>(ctx, A, B, bcomp, cache, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
-      case 65536: e = num_window<65536, false, kWindowMaxNnzWide>(ctx, A, B, bcomp, cache, b_split, b_range_bad, arith, c_rowptr, rows, nrows, c_colind, c_vals); break;
+#define KK_NUM_WIN_LARGE(WB, VM)                                                               \
+  case WB:                                                                                     \
+    e = num_window<WB, false, VM>(ctx, A, B, bcomp, cache, b_split, b_range_bad, arith, c_rowptr, \
+                                  rows, nrows, c_colind, c_vals);                              \
+    break;
+    if (bin.hi <= kWindowMidNnz) {
+      switch (bin.slots) {
+        KK_NUM_WIN_LARGE(24576, kWindowMidNnz)
+        KK_NUM_WIN_LARGE(40960, kWindowMidNnz)
+        KK_NUM_WIN_LARGE(65536, kWindowMidNnz)
+      }
+    } else {
+      switch (bin.slots) {
+        KK_NUM_WIN_LARGE(24576, kWindowMaxNnzWide)
+        KK_NUM_WIN_LARGE(40960, kWindowMaxNnzWide)
+        KK_NUM_WIN_LARGE(65536, kWindowMaxNnzWide)
+      }
     }
+#undef KK_NUM_WIN_LARGE
     timer_end(ctx.timer, ctx.stream);
     return e;
   }

@@ -141,3 +141,21 @@ def test_wide_kept_bits_match_rebuild():
     check_against_oracle(A, B, *rebuilt[:3])
     assert kept[4]["num_dense_rows"] > 0
     assert np.diff(kept[0]).min() > 24000  # above the wide kernel's shared-memory value space
+
+
+@pytest.mark.parametrize("n", [20000, 36000, 60000])
+@pytest.mark.parametrize("lens", [(14, 22), (24, 34)])
+@pytest.mark.parametrize("arith", [1, 2])
+def test_large_value_window_bins(n, lens, arith):
+    # rows of 257..1024 columns spread over the whole width of a matrix whose
+    # width picks the 24576 / 40960 / 65536-bit window: random rows times random
+    # rows give about lens^2 distinct columns per row of C, which lands in the
+    # 512-slot (first lens) or 1024-slot (second lens) value array
+    A = I.random_rows(600, n, lens[0], lens[1], seed=n + lens[0], purpose="lvA")
+    B = I.random_rows(n, n, lens[0], lens[1], seed=n + lens[1], purpose="lvB")
+    rp, ci, va, _, st = run_gpu(A, B, arith=arith)
+    per_row = np.diff(rp)
+    assert per_row.max() > 256 and st["num_window_rows"] > 0
+    if lens[0] >= 24:
+        assert (per_row > 512).any()
+    check_against_oracle(A, B, rp, ci, va)
