@@ -548,6 +548,277 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
   }
 }
 
+// DF32 s += b (two-sum of the high parts, renormalised).
+__device__ __forceinline__ void df_add(DF& s, const DF b) {
+  const float sh = s.hi + b.hi;
+  const float bb = sh - s.hi;
+  const float err = (s.hi - (sh - bb)) + (b.hi - bb);
+  const float lo = s.lo + (b.lo + err);
+  const float hi = sh + lo;
+  s.lo = lo - (hi - sh);
+  s.hi = hi;
+}
+
+// Value pass over the A entries [p_lo, p_hi) of a window row into vacc: DF32
+// pairs when df, else float64 in storage order; ranks from the window's bits
+// and prefix counts.  One warp.
+template <int WORDS, int VMAX>
+__device__ __forceinline__ void window_values(int p_lo, int p_hi, bool df, const int32_t* __restrict__ acol,
+                                              const double* __restrict__ aval,
+                                              const int32_t* __restrict__ brp,
+                                              const int32_t* __restrict__ bcol,
+                                              const float2* __restrict__ bspl,
+                                              const double* __restrict__ bval, const uint32_t* bits,
+                                              const uint16_t* pre, int lo_c, u64* vacc, int4* ainfo,
+                                              int lane, int& missing) {
+  for (int p0 = p_lo; p0 < p_hi; p0 += 32) {
+    const int p = p0 + lane;
+    int4 info = make_int4(0, 0, 0, 0);
+    double a = 0.0;
+    if (p < p_hi) {
+      const int j = acol[p];
+      info.x = brp[j];
+      info.y = brp[j + 1] - info.x;
+      a = aval[p];
+    }
+    if (df) {
+      DF ad;
+      df_split(a, ad);
+      info.z = __float_as_int(ad.hi);
+      info.w = __float_as_int(ad.lo);
+    } else {
+      const long long ab = __double_as_longlong(a);
+      info.z = (int)(ab & 0xffffffffll);
+      info.w = (int)(ab >> 32);
+    }
+    ainfo[lane] = info;
+    __syncwarp();
+    const int nch = min(32, p_hi - p0);
+    const unsigned maxlen = __reduce_max_sync(kFull, (unsigned)info.y);
+    if (maxlen <= 32u) {
+      // B rows of at most 32 entries: the loads of kWinBatch A entries in flight
+      for (int t0 = 0; t0 < nch; t0 += kWinBatch) {
+        float2 bv[kWinBatch];
+        int rk[kWinBatch];
+#pragma unroll
+        for (int u = 0; u < kWinBatch; ++u) {
+          int c = 0;
+          bool ok = false;
+          bv[u] = make_float2(0.f, 0.f);
+          if (t0 + u < nch) {
+            const int2 in = *reinterpret_cast<const int2*>(&ainfo[t0 + u]);
+            if (lane < in.y) {
+              const int q = in.x + lane;
+              ok = true;
+              c = bcol[q];
+              if (df) {
+                bv[u] = bspl[q];
+              } else {
+                const long long bb = __double_as_longlong(bval[q]);
+                bv[u] = make_float2(__int_as_float((int)(bb & 0xffffffffll)),
+                                    __int_as_float((int)(bb >> 32)));
+              }
+            }
+          }
+          rk[u] = window_rank<WORDS, VMAX>(bits, pre, (uint32_t)(c - lo_c), ok, missing);
+        }
+#pragma unroll
+        for (int u = 0; u < kWinBatch; ++u) {
+          if (t0 + u < nch) {
+            const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
+            if (df) {
+              DF av2, b2;
+              av2.hi = __int_as_float(az.x);
+              av2.lo = __int_as_float(az.y);
+              b2.hi = bv[u].x;
+              b2.lo = bv[u].y;
+              DF sv = df_unpack(vacc[rk[u]]);
+              df_fma(sv, av2, b2);
+              vacc[rk[u]] = df_pack(sv);
+            } else {
+              const double x = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
+              const double y = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
+                                                    (unsigned)__float_as_int(bv[u].x));
+              double* v = reinterpret_cast<double*>(&vacc[rk[u]]);
+              *v = fma(x, y, *v);
+            }
+            __syncwarp();  // this A entry's updates are visible before the next one's
+          }
+        }
+      }
+      __syncwarp();
+      continue;
+    }
+    for (int t = 0; t < nch; ++t) {
+      const int4 in = ainfo[t];
+      for (int q0 = 0; q0 < in.y; q0 += 32) {
+        const int q = in.x + q0 + lane;
+        const bool ok = q0 + lane < in.y;
+        const int c = ok ? bcol[q] : 0;
+        const int rank = window_rank<WORDS, VMAX>(bits, pre, (uint32_t)(c - lo_c), ok, missing);
+        if (df) {
+          DF av2, b2;
+          av2.hi = __int_as_float(in.z);
+          av2.lo = __int_as_float(in.w);
+          const float2 bb = ok ? bspl[q] : make_float2(0.f, 0.f);
+          b2.hi = bb.x;
+          b2.lo = bb.y;
+          DF sv = df_unpack(vacc[rank]);
+          df_fma(sv, av2, b2);
+          vacc[rank] = df_pack(sv);
+        } else {
+          const double x = __longlong_as_double(((long long)in.w << 32) | (unsigned)in.z);
+          double* v = reinterpret_cast<double*>(&vacc[rank]);
+          *v = fma(x, ok ? bval[q] : 0.0, *v);
+        }
+        __syncwarp();  // this B entry set's updates are visible before the next one's
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Large-value window rows (more than kWindowMaxNnz columns), one CTA of
+// kWinCtaWarps warps per row.  The window (bits, summary bits, prefix counts,
+// word list) is shared by the CTA instead of one per warp, so an SM holds
+// about twice as many warps of these rows; the warps split the row's A entries
+// into contiguous shares, OR their compressed rows into the shared window,
+// and add their products into a value array of their own; the arrays are
+// summed in warp order, so the result does not depend on scheduling.  A row
+// whose values leave the DF32 window is added by warp 0 alone, in float64 and
+// storage order.  The structure is always rebuilt from B_C.
+constexpr int kWinCtaWarps = 4;
+template <int W, int VMAX>
+struct CtaWinGeom : WinWords<W> {
+  using WinWords<W>::WORDS;
+  using WinWords<W>::SUMS;
+  // bits u32[WORDS] | sum u32[SUMS] | prefix u16[WORDS] | list u16[VMAX]
+  // | vacc u64[kWinCtaWarps][VMAX + 2] | ainfo int4[kWinCtaWarps][32] | int[8]
+  static constexpr size_t kSumOff = al16((size_t)WORDS * 4);
+  static constexpr size_t kPreOff = al16(kSumOff + (size_t)SUMS * 4);
+  static constexpr size_t kListOff = al16(kPreOff + (size_t)WORDS * 2);
+  static constexpr size_t kValOff = al16(kListOff + (size_t)VMAX * 2);
+  static constexpr size_t kValStride = (size_t)(VMAX + 2);
+  static constexpr size_t kInfoOff = al16(kValOff + kWinCtaWarps * kValStride * 8);
+  static constexpr size_t kShOff = kInfoOff + (size_t)kWinCtaWarps * 32 * 16;
+  static constexpr size_t kBytes = kShOff + 8 * 4;
+};
+
+template <int W, int VMAX>
+__global__ void __launch_bounds__(kWinCtaWarps * 32)
+k_num_window_cta(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ row_lo,
+                 const float2* __restrict__ bspl, const int32_t* __restrict__ b_range_bad,
+                 int32_t arith, const int64_t* __restrict__ c_rowptr, const int32_t* __restrict__ rows,
+                 int32_t nrows, int32_t* __restrict__ c_colind, double* __restrict__ c_vals, int* status) {
+  using G = CtaWinGeom<W, VMAX>;
+  constexpr int WORDS = G::WORDS;
+  constexpr int SUMS = G::SUMS;
+  constexpr int NT = kWinCtaWarps * 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* sum = reinterpret_cast<uint32_t*>(smem_raw + G::kSumOff);
+  uint16_t* pre = reinterpret_cast<uint16_t*>(smem_raw + G::kPreOff);
+  uint16_t* list = reinterpret_cast<uint16_t*>(smem_raw + G::kListOff);
+  u64* vacc_all = reinterpret_cast<u64*>(smem_raw + G::kValOff);
+  u64* vacc = vacc_all + warp * G::kValStride;
+  int4* ainfo = reinterpret_cast<int4*>(smem_raw + G::kInfoOff) + warp * 32;
+  int* sh = reinterpret_cast<int*>(smem_raw + G::kShOff);
+  const bool df_all = arith == kArithDF32 && *b_range_bad == 0;
+  const int32_t* __restrict__ acol = A.colind;
+  const double* __restrict__ aval = A.vals;
+  for (int w = tid * 4; w < WORDS; w += NT * 4)
+    *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
+  for (int w = tid; w < SUMS; w += NT) sum[w] = 0u;
+  __syncthreads();
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int i = rows[r];
+    const int lo_w = row_lo[i] >> 5;
+    const int lo_c = lo_w * 32;
+    const int64_t off = c_rowptr[i];
+    const int cnt = (int)(c_rowptr[i + 1] - off);
+    const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
+    for (int e = lane; e < min(cnt, VMAX); e += 32) vacc[e] = 0ull;
+    // this warp's share of the A entries
+    const int na = pe - pa;
+    const int qa = (na + kWinCtaWarps - 1) / kWinCtaWarps;
+    const int p_lo = pa + min(na, warp * qa), p_hi = pa + min(na, (warp + 1) * qa);
+    bc_set_bits<WORDS>(bits, sum, lo_w, p_lo, p_hi, acol, B.rowptr, bcomp.bc, bcomp.len, lane, status);
+    __syncthreads();
+    if (warp == 0) {
+      const int L0 = window_list<SUMS>(sum, list, VMAX, lane);
+      if (lane == 0) sh[0] = L0;
+    }
+    __syncthreads();
+    const int L = sh[0];
+    if (L > VMAX) {  // more words than a window row has columns
+      for (int w = tid * 4; w < WORDS; w += NT * 4)
+        *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
+      if (tid == 0) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+      __syncthreads();
+      continue;
+    }
+    // prefix counts and columns: warp w takes a contiguous part of the list
+    const int lq = (L + NT - 1) / NT * 32;
+    const int e_lo = min(L, warp * lq), e_hi = min(L, (warp + 1) * lq);
+    int part = 0;
+    for (int e = e_lo + lane; e < e_hi; e += 32) part += __popc(bits[list[e]]);
+    part = team_sum<32>(part, kFull);
+    if (lane == 0) sh[1 + warp] = part;
+    __syncthreads();
+    int run = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < kWinCtaWarps; ++k) {
+      run += k < warp ? sh[1 + k] : 0;
+      total += sh[1 + k];
+    }
+    for (int e0 = e_lo; e0 < e_hi; e0 += 32) {
+      const int e = e0 + lane;
+      const int w = e < e_hi ? (int)list[e] : 0;
+      uint32_t m = e < e_hi ? bits[w] : 0u;
+      const int c = __popc(m);
+      const int incl = team_inclusive_scan<32>(c, lane, kFull);
+      int pos = run + incl - c;
+      run += __shfl_sync(kFull, incl, 31);
+      if (e < e_hi) {
+        pre[w] = (uint16_t)pos;
+        while (m) {
+          const int b = __ffs(m) - 1;
+          m &= m - 1;
+          if (pos < cnt) c_colind[off + pos] = lo_c + w * 32 + b;
+          ++pos;
+        }
+      }
+    }
+    if (tid == 0 && total != cnt) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    __syncthreads();
+    // arithmetic of this row: DF32 unless one of its A values is outside the window
+    const bool df = df_all && row_df_ok<32>(aval, pa, pe, lane, kFull);
+    int missing = 0;
+    if (df)
+      window_values<WORDS, VMAX>(p_lo, p_hi, true, acol, aval, B.rowptr, B.colind, bspl, B.vals, bits, pre,
+                                 lo_c, vacc, ainfo, lane, missing);
+    else if (warp == 0)
+      window_values<WORDS, VMAX>(pa, pe, false, acol, aval, B.rowptr, B.colind, bspl, B.vals, bits, pre,
+                                 lo_c, vacc, ainfo, lane, missing);
+    if (missing) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+    __syncthreads();
+    const int n = min(cnt, VMAX);
+    for (int e = tid; e < n; e += NT) {
+      if (df) {
+        DF v = df_unpack(vacc_all[e]);
+#pragma unroll
+        for (int k = 1; k < kWinCtaWarps; ++k) df_add(v, df_unpack(vacc_all[k * G::kValStride + e]));
+        c_vals[off + e] = df_to_double(v);
+      } else {
+        c_vals[off + e] = __longlong_as_double((long long)vacc_all[e]);
+      }
+    }
+    for (int e = tid; e < L; e += NT) bits[list[e]] = 0u;
+    __syncthreads();
+  }
+}
+
 // Numeric phase of the rows whose structure the symbolic phase kept: the
 // row's words go into a small open-addressing table (slot = word mod 256,
 // linear probing; at most kCacheWords words in 256 slots) instead of a W-bit
@@ -706,6 +977,31 @@ cudaError_t num_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
   return cudaGetLastError();
 }
 
+template <int W, int VMAX>
+cudaError_t num_window_cta(const LaunchCtx& ctx, const CsrView& A, const CsrView& B, const BComp& bcomp,
+                           const float2* b_split, const int32_t* b_range_bad, int32_t arith,
+                           const int64_t* c_rowptr, const int32_t* rows, int32_t nrows, int32_t* c_colind,
+                           double* c_vals) {
+  const size_t smem = CtaWinGeom<W, VMAX>::kBytes;
+  auto kern = k_num_window_cta<W, VMAX>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  // persistent: one resident wave strides over the rows
+  static int per_sm = 0;
+  if (per_sm == 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWinCtaWarps * 32, smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    per_sm = 1;
+  }
+  long long grid = (long long)ctx.num_sms * (per_sm > 0 ? per_sm : 1);
+  if (grid > nrows) grid = nrows;
+  if (grid < 1) grid = 1;
+  kern<<<(int)grid, kWinCtaWarps * 32, smem, ctx.stream>>>(A, B, bcomp, ctx.row_lo, b_split, b_range_bad,
+                                                           arith, c_rowptr, rows, nrows, c_colind, c_vals,
+                                                           ctx.status);
+  return cudaGetLastError();
+}
+
 cudaError_t num_kept(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
                      const WinCacheView& cache, const float2* b_split, const int32_t* b_range_bad,
                      int32_t arith, const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
@@ -756,10 +1052,10 @@ cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, cons
   if (bin.hi > kWindowMaxNnz) {  // rows of up to kWindowMaxNnzWide columns: large value array
     timer_begin(ctx.timer, ctx.stream, "num_window");
     e = cudaErrorInvalidValue;
-#define KK_NUM_WIN_LARGE(WB, VM)                                                               \
-  case WB:                                                                                     \
-    e = num_window<WB, false, VM>(ctx, A, B, bcomp, cache, b_split, b_range_bad, arith, c_rowptr, \
-                                  rows, nrows, c_colind, c_vals);                              \
+#define KK_NUM_WIN_LARGE(WB, VM)                                                                 \
+  case WB:                                                                                       \
+    e = num_window_cta<WB, VM>(ctx, A, B, bcomp, b_split, b_range_bad, arith, c_rowptr, rows, nrows, \
+                               c_colind, c_vals);                                                \
     break;
     if (bin.hi <= kWindowMidNnz) {
       switch (bin.slots) {
