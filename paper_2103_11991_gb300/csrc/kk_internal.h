@@ -107,6 +107,13 @@ struct WinScratch {
 // Analysis of B (kk_window.cu): clears *sorted_flag unless every row is
 // strictly ascending, sets KK_ERR_BAD_INDEX on out-of-range structure, and,
 // when bc is non-null, writes the compressed rows (pairs counted into *pairs).
+// Numeric phase of window rows with kept structure (kk_kept.cu); rows without
+// it are appended to left_rows / *left_count for the rebuild kernel.
+cudaError_t launch_num_kept(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                            const WinCacheView& cache, const float2* b_split, const int32_t* b_range_bad,
+                            int32_t arith, const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
+                            int32_t* c_colind, double* c_vals, int32_t* left_rows, int32_t* left_count);
+
 cudaError_t launch_analyze_b(const LaunchCtx& ctx, const CsrView& B, int32_t* sorted_flag,
                              int2* bc, int32_t* len, unsigned long long* pairs);
 
