@@ -32,6 +32,7 @@ using u64 = unsigned long long;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWinWarps = 4;  // warps (rows in flight) per CTA
 constexpr int kWinBatch = 8;  // A entries whose B loads are issued together
+constexpr int kSetBatch = 8;  // groups of compressed-row loads in flight in bc_set_bits
 
 constexpr size_t al16(size_t x) { return (x + 15) / 16 * 16; }
 
@@ -81,11 +82,12 @@ __device__ __forceinline__ void bc_bounds(int p, int pe, const int32_t* __restri
 }
 
 // OR the compressed rows B_C(j,:) of the entries [pa, pe) of A(i,:) into the
-// window whose word 0 is column word lo_w; the first setter of a word also sets
-// its summary bit.  Lanes take the pairs of 32 / G A entries at a time, G the
-// power of two that covers the longest compressed row of the chunk.  x0 / y0:
+// window whose word 0 is column word lo_w, and the word's summary bit.  Lanes
+// take the pairs of 32 / G A entries at a time, G the power of two that covers
+// the longest compressed row of the chunk, with the loads of SETB such groups
+// in flight (the numeric kernels take 4: their register budget is tighter).  x0 / y0:
 // the lane's bounds for the first chunk, already loaded (PRE), else loaded here.
-template <int WORDS, bool PRE = false>
+template <int WORDS, bool PRE = false, int SETB = kSetBatch>
 __device__ __forceinline__ void bc_set_bits(uint32_t* bits, uint32_t* sum, int lo_w, int pa, int pe,
                                             const int32_t* __restrict__ acol,
                                             const int32_t* __restrict__ brp,
@@ -107,10 +109,10 @@ __device__ __forceinline__ void bc_set_bits(uint32_t* bits, uint32_t* sum, int l
       const int lg = maxlen <= 1u ? 0 : maxlen <= 2u ? 1 : maxlen <= 4u ? 2 : maxlen <= 8u ? 3 : 4;
       const int per = 32 >> lg;
       const int sub = lane >> lg, e = lane & ((1 << lg) - 1);
-      for (int t0 = 0; t0 < nch; t0 += 4 * per) {
-        int2 v[4];
+      for (int t0 = 0; t0 < nch; t0 += SETB * per) {
+        int2 v[SETB];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < SETB; ++u) {
           const int t = t0 + u * per + sub;
           const int xs = __shfl_sync(kFull, x, t & 31);
           const int ys = __shfl_sync(kFull, y, t & 31);
@@ -118,12 +120,13 @@ __device__ __forceinline__ void bc_set_bits(uint32_t* bits, uint32_t* sum, int l
           if (t < nch && e < ys) v[u] = bc[xs + e];
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < SETB; ++u) {
           if (v[u].y != 0) {
             const uint32_t w = (uint32_t)(v[u].x - lo_w);
             if (w < (uint32_t)WORDS) {
-              const uint32_t old = atomicOr(&bits[w], (uint32_t)v[u].y);
-              if (old == 0u) atomicOr(&sum[w >> 5], 1u << (w & 31));
+              // no returned value to wait for: the summary bit is set every time
+              atomicOr(&bits[w], (uint32_t)v[u].y);
+              atomicOr(&sum[w >> 5], 1u << (w & 31));
             } else {
               bad = 1;
             }
@@ -138,6 +141,8 @@ __device__ __forceinline__ void bc_set_bits(uint32_t* bits, uint32_t* sum, int l
           const int2 v = bc[xs + e];
           const uint32_t w = (uint32_t)(v.x - lo_w);
           if (w < (uint32_t)WORDS) {
+            // long compressed rows (scattered columns): only the first setter of
+            // a word sets its summary bit, which keeps lanes off shared summary words
             const uint32_t old = atomicOr(&bits[w], (uint32_t)v.y);
             if (old == 0u) atomicOr(&sum[w >> 5], 1u << (w & 31));
           } else {
@@ -383,7 +388,7 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
       }
     } else {
       // rebuild: bits from B_C, ordered word list, prefixes and columns
-      bc_set_bits<WORDS>(bits, sum, lo_w, pa, pe, acol, brp, bcomp.bc, bcomp.len, lane, status);
+      bc_set_bits<WORDS, false, 4>(bits, sum, lo_w, pa, pe, acol, brp, bcomp.bc, bcomp.len, lane, status);
       L = window_list<SUMS>(sum, list, VMAX, lane);
       if (L > VMAX) {  // more words than a window row has columns
         for (int w = lane * 4; w < WORDS; w += 128)
@@ -742,7 +747,7 @@ k_num_window_cta(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ 
     const int na = pe - pa;
     const int qa = (na + kWinCtaWarps - 1) / kWinCtaWarps;
     const int p_lo = pa + min(na, warp * qa), p_hi = pa + min(na, (warp + 1) * qa);
-    bc_set_bits<WORDS>(bits, sum, lo_w, p_lo, p_hi, acol, B.rowptr, bcomp.bc, bcomp.len, lane, status);
+    bc_set_bits<WORDS, false, 4>(bits, sum, lo_w, p_lo, p_hi, acol, B.rowptr, bcomp.bc, bcomp.len, lane, status);
     __syncthreads();
     if (warp == 0) {
       const int L0 = window_list<SUMS>(sum, list, VMAX, lane);
