@@ -248,15 +248,16 @@ def bench_learned(args, dA, dB, madds, plain_ms, ci, va):
         out["rmat20"]["nnz_c"] = int(nnz)
         del cR, vR, dR
         torch.cuda.empty_cache()
-    return out
+    return out, params
 
 
-def bench_batched(args):
+def bench_batched(args, predictor=None):
     """Batched form on the first `--batch-count` pairs of the 2000-pair
-    workload (seeds 5000..), in both execution modes — the batch as one
-    block-diagonal product through the plain kernels (the default), and one
-    persistent work-queue launch per phase replayed from a CUDA graph — against
-    the same products as looped plain calls on one stream."""
+    workload (seeds 5000..), in its execution modes — the batch as one
+    block-diagonal product through the plain kernels (the default), the same
+    through the learned form with the trained predictor (when one is given),
+    and one persistent work-queue launch per phase replayed from a CUDA graph —
+    against the same products as looped plain calls on one stream."""
     import torch
     from paper_2103_11991_gb300 import inputs as I
     from paper_2103_11991_gb300 import spgemm as K
@@ -269,8 +270,13 @@ def bench_batched(args):
     modes = {}
     madds = total = 0
     with torch.cuda.stream(stream):
-        for name, mode in (("packed", 2), ("persistent_graph", 1)):
-            op = K.BatchedSpGEMM(stream=stream, batched_mode=mode)
+        runs = [("packed", 2, 0), ("persistent_graph", 1, 0)]
+        if predictor is not None:
+            runs.insert(1, ("packed_learned", 2, 1))
+        for name, mode, learned in runs:
+            op = K.BatchedSpGEMM(stream=stream, batched_mode=mode, batched_learned=learned)
+            if learned:
+                op.set_predictor(predictor, 0.95)
             rp, off, total = op.symbolic(dAs, dBs)
             ci, va = op.numeric(dAs, dBs, rp, total)
             op.sync()
@@ -479,10 +485,11 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = 2.0 * madds * world / (e2e_ms * 1e-3) / 1e9
 
     forms = {}
+    predictor = None
     if rank == 0 and args.forms in ("all", "learned"):
-        forms["learned"] = bench_learned(args, dA, dB, madds, ms, ci, va)
+        forms["learned"], predictor = bench_learned(args, dA, dB, madds, ms, ci, va)
     if rank == 0 and args.forms in ("all", "batched"):
-        forms["batched"] = bench_batched(args)
+        forms["batched"] = bench_batched(args, predictor)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

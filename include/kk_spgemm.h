@@ -103,6 +103,14 @@ typedef struct {
   int32_t batched_mode;       /* batched form (kk_batched.h): 1 = persistent work-queue kernels
                                  (graph-capturable), 2 = the batch as one block-diagonal product
                                  through the plain two-phase kernels, 0 = automatic (2) */
+  int32_t batched_learned;    /* 1: the block-diagonal batched form runs the learned form
+                                 (kk_learned.h: speculative one-pass sized by the predictor
+                                 attached with kk_spgemm_set_predictor, or by the flop bound
+                                 without one) instead of the plain two phases (default 0).
+                                 The first numeric call after such a symbolic call returns
+                                 the values the speculative pass computed from the values the
+                                 symbolic call saw; later numeric calls recompute from the
+                                 current values */
 } kk_spgemm_options;
 
 typedef struct kk_spgemm_handle_s* kk_spgemm_handle;

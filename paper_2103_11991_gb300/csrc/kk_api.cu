@@ -656,6 +656,7 @@ struct kk_spgemm_handle_s {
   DevBuf d_lrows2;     // int32[m]  plain-path numeric bins' row lists
   DevBuf d_mm;         // int2[n]   B row min/max columns (features)
   bool learned_valid = false;
+  bool p_learned = false;  // the packed batch ran the learned form; its numeric call is due
   std::vector<int32_t> lnum_start;
   // batched form
   DevBuf d_bdesc, d_rowpair, d_bflop, d_bsbin, d_bnbin, d_bsrows, d_bnrows, d_bcnt, d_btiles, d_bstart,
@@ -1109,6 +1110,7 @@ kk_status kk_spgemm_options_default(kk_spgemm_options* opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->arith = KK_ARITH_AUTO;
   opt->debug_checks = 0;
+  opt->batched_learned = 0;
   opt->timing = 0;
   opt->force_tier = -1;
   opt->team_vec_min_len = 12;
@@ -1825,7 +1827,9 @@ kk_status batched_packed_symbolic(kk_spgemm_handle h, int32_t count, const kk_cs
   h->p_kmax = kmax;
   const kk_csr Ap = packed_a(h), Bp = packed_b(h);
   int64_t nnz = 0;
-  kk_status st = kk_spgemm_symbolic(h, &Ap, &Bp, c_rowptr, &nnz);
+  h->p_learned = h->opt.batched_learned != 0;
+  kk_status st = h->p_learned ? kk_spgemm_learned_symbolic(h, &Ap, &Bp, c_rowptr, &nnz)
+                              : kk_spgemm_symbolic(h, &Ap, &Bp, c_rowptr, &nnz);
   if (st != KK_OK) return st;
   KK_CUDA(h, launch_b_offsets(s, count, dd, RA, c_rowptr, h->d_boff.as<int64_t>()), "offsets");
   KK_CUDA(h, cudaMemcpyAsync(h->h_boff, h->d_boff.p, sizeof(int64_t) * ((size_t)count + 1),
@@ -1854,7 +1858,12 @@ kk_status batched_packed_numeric(kk_spgemm_handle h, int32_t count, bool moved, 
                            h->d_pb_rp.as<int32_t>(), h->d_pb_ci.as<int32_t>(), h->d_pb_v.as<double>(),
                            h->p_RA, h->p_NA, h->p_RB, h->p_NB), "pack");
   const kk_csr Ap = packed_a(h), Bp = packed_b(h);
-  return kk_spgemm_numeric(h, &Ap, &Bp, c_rowptr, c_colind, c_vals);
+  // the first numeric call after a learned symbolic call copies the values the
+  // speculative pass computed; later calls recompute from the current values
+  const bool fresh = h->p_learned;
+  h->p_learned = false;
+  return fresh ? kk_spgemm_learned_numeric(h, &Ap, &Bp, c_rowptr, c_colind, c_vals)
+               : kk_spgemm_numeric(h, &Ap, &Bp, c_rowptr, c_colind, c_vals);
 }
 
 }  // namespace

@@ -5,7 +5,7 @@ Training data come from the symbolic phase itself: for every row of a training
 product the GPU computes the row features (``kk_spgemm_row_features``) and the
 symbolic phase's count gives the capacity-class label
 (``kk_capacity_classes``).  The training matrices are seeded synthetic
-families disjoint from the evaluation inputs: R-MAT graphs at scales 12-16
+families disjoint from the evaluation inputs: R-MAT graphs at scales 14-18
 (seeds 1000+), 2D 5/9-point and 3D 7/27-point stencils on grids other than the
 evaluation grids, and uniform random rows.  The network is trained by the
 library's own forward/backward/Adam kernels (``kk_mlp_train``).
@@ -27,7 +27,7 @@ TUNED = os.path.join(PKG, "tuned")
 def training_pairs(small: bool = False):
     """(A, B) training products.  ``small`` keeps a reduced set for tests."""
     pairs = []
-    rscales = [11, 12] if small else [12, 13, 14, 15, 16]
+    rscales = [11, 12] if small else [14, 15, 16, 17, 18]
     for t, s in enumerate(rscales):
         A = I.rmat(s, 16, 0.57, 0.19, 0.19, seed=1000 + t)
         pairs.append((A, A))

@@ -51,7 +51,8 @@ class KkOptions(ctypes.Structure):
                 ("num_cta_max_nnz", ctypes.c_int32), ("use_window", ctypes.c_int32),
                 ("batched_graph", ctypes.c_int32), ("sym_load_pct", ctypes.c_int32),
                 ("num_load_pct", ctypes.c_int32), ("structure_cache", ctypes.c_int32),
-                ("wide_cache_mb", ctypes.c_int32), ("batched_mode", ctypes.c_int32)]
+                ("wide_cache_mb", ctypes.c_int32), ("batched_mode", ctypes.c_int32),
+                ("batched_learned", ctypes.c_int32)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -470,6 +471,11 @@ class BatchedSpGEMM:
         self.opt = make_options(**options)
         self.stream = stream
         self.h = kk_spgemm_handle_create(self.opt, stream)
+
+    def set_predictor(self, params, quantile: float = 0.95):
+        """Predictor for the learned form of the packed batch (option
+        ``batched_learned=1``)."""
+        kk_spgemm_set_predictor(self.h, params, quantile)
 
     def symbolic(self, As, Bs):
         import torch

@@ -70,3 +70,29 @@ def test_oracle_and_product_are_independent():
             txt = open(f).read()
             assert not re.search(r"^\s*(import|from)\s+paper_2103_11991_gb300", txt, flags=re.M), f
             assert "kk_spgemm" not in txt and "csrc" not in txt, f
+
+
+def _struct_fields(header, name):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r";", src)
+    assert m, name
+    return re.findall(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*;", m.group(1))
+
+
+def test_binding_structs_match_header():
+    # the ctypes mirrors of the option and matrix structs list the header's
+    # fields in the header's order (all 32-bit or pointer fields)
+    from paper_2103_11991_gb300 import spgemm as K
+    assert [f for f, _ in K.KkOptions._fields_] == _struct_fields("kk_spgemm.h", "kk_spgemm_options")
+    assert [f for f, _ in K.KkCsr._fields_] == _struct_fields("kk_spgemm.h", "kk_csr")
+
+
+def test_options_default_fills_every_field(lib):
+    from paper_2103_11991_gb300 import spgemm as K
+    o = K.KkOptions()
+    for f, _ in o._fields_:
+        setattr(o, f, -12345)
+    assert lib.kk_spgemm_options_default(ctypes.byref(o)) == 0
+    assert all(getattr(o, f) != -12345 for f, _ in o._fields_)
+    assert o.batched_learned == 0 and o.structure_cache == 1

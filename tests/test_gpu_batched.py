@@ -87,3 +87,33 @@ def test_batched_packed_moved_arrays():
         op.sync()
         torch.cuda.synchronize()
         _check_batch(pairs, rowptr, off, colind[:total], vals[:total])
+
+
+@pytest.mark.parametrize("pred", ["none", "class2"])
+def test_batched_learned_matches_oracle(pred):
+    # the block-diagonal batch through the learned form: one speculative pass
+    # (rows sized by the flop bound, or all predicted class 2 so that most rows
+    # overflow and are re-run), then a numeric refresh with new values
+    from paper_2103_11991_gb300 import spgemm as K
+    pairs = _pairs(30, 7300)
+    dA = [K.DeviceCSR.from_host(A) for A, _ in pairs]
+    dB = [K.DeviceCSR.from_host(B) for _, B in pairs]
+    with K.BatchedSpGEMM(batched_mode=2, batched_learned=1) as op:
+        if pred == "class2":
+            th = np.zeros(1872, dtype=np.float32)
+            th[1872 - 16 + 2] = 10.0
+            op.set_predictor(th, 0.95)
+        rowptr, off, total = op.symbolic(dA, dB)
+        st = op.stats()
+        assert st["onepass_rows"] > 0
+        if pred == "class2":
+            assert st["overflow_rows"] > 0
+        colind, vals = op.numeric(dA, dB, rowptr, total)
+        op.sync()
+        _check_batch(pairs, rowptr, off, colind[:total], vals[:total])
+        for d in dA:
+            d.vals.mul_(-2.0)
+        colind2, vals2 = op.numeric(dA, dB, rowptr, total, colind, vals)
+        op.sync()
+        scaled = [(I.CSR(A.m, A.n, A.rowptr, A.colind, A.vals * -2.0), B) for A, B in pairs]
+        _check_batch(scaled, rowptr, off, colind2[:total], vals2[:total])
