@@ -1227,13 +1227,13 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   if (m > 0) {
     timer_begin(h->timer, s, "analyze");
     if ((st = analyze_b(h, bv)) != KK_OK) return st;
+    // smallest team whose U = 8 gathers per lane cover a typical row in one
+    // round (more rows in flight per SM; measured against teams of 4 and 8)
     const long long avg = m > 0 ? (long long)av.nnz / m : 0;
-    if (avg <= 2)
-      launch_analyze_a<1, 2>(h, av, bv, dm, s);
-    else if (avg <= 8)
-      launch_analyze_a<4, 2>(h, av, bv, dm, s);
+    if (avg <= 8)
+      launch_analyze_a<1, 8>(h, av, bv, dm, s);
     else
-      launch_analyze_a<8, 4>(h, av, bv, dm, s);
+      launch_analyze_a<4, 8>(h, av, bv, dm, s);
     timer_end(h->timer, s);
     KK_CUDA(h, cudaGetLastError(), "analyze launch");
     if ((st = run_binning(h, m, h->d_sbin.as<uint8_t>(), nbs, h->d_srows.as<int32_t>(), sym_start)) != KK_OK)
