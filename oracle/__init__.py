@@ -15,9 +15,11 @@ Contents
 ``mlp.py``           fp64 numpy forward/backward of the row-capacity MLP.
 ``features.py``      row features and capacity-bucket labels written from their
                      plain definitions (numpy).
+``jacobi.py``        Jacobi-fused SpGEMM C = (I - omega D^-1 A) B, paper Sec.
+                     "Jacobi-Fused SpGEMM Kernel", on top of the Gustavson oracle.
 
-Parity status: every function here is pinned by ``tests/test_oracle.py`` and
-``tests/test_oracle_mlp.py`` (dense brute force, closed forms, invariants,
+Parity status: every function here is pinned by ``tests/test_oracle.py``,
+``tests/test_oracle_mlp.py`` and ``tests/test_oracle_jacobi.py`` (dense brute force, closed forms, invariants,
 finite differences).
 """
 from __future__ import annotations

@@ -311,6 +311,58 @@ def random_sparse(m: int, n: int, density: float, seed: int, duplicates: bool = 
     return _from_sorted_coo(m, n, rows, cols, vals)
 
 
+def with_diagonal(A: CSR, seed: int, lo: float = 1.0, hi: float = 2.0, split: bool = False) -> CSR:
+    """Square A with a stored diagonal entry in every row: rows that lack one get
+    an entry appended at the end of the row (so unsorted rows stay unsorted),
+    value uniform in [lo, hi) with a random sign.  ``split`` also stores the
+    diagonal of every other row as two entries (a repeated column) whose values
+    add up to the drawn one."""
+    if A.m != A.n:
+        raise ValueError("with_diagonal needs a square matrix")
+    m = A.m
+    rows = np.repeat(np.arange(m, dtype=np.int64), A.row_lengths())
+    cols = A.colind.astype(np.int64)
+    vals = A.vals.astype(np.float64)
+    on = rows == cols
+    has = np.zeros(m, dtype=bool)
+    has[rows[on]] = True
+    # existing diagonal entries are redrawn too, so that no row sums to zero
+    u = uniform01(seed, "diag.vals", m)
+    sg = np.where(uniform01(seed, "diag.sign", m) < 0.5, -1.0, 1.0)
+    d = sg * (lo + (hi - lo) * u)
+    keep_first = np.zeros(len(rows), dtype=bool)
+    if on.any():
+        first = np.nonzero(on)[0]
+        _, idx = np.unique(rows[first], return_index=True)
+        keep_first[first[idx]] = True
+    vals = np.where(on, 0.0, vals)
+    vals = np.where(keep_first, d[rows], vals)
+    add_r = np.nonzero(~has)[0]
+    pieces_r = [rows, add_r]
+    pieces_c = [cols, add_r]
+    pieces_v = [vals, d[add_r]]
+    if split:
+        sr = np.arange(0, m, 2, dtype=np.int64)
+        half = 0.25 * d[sr]
+        pieces_r.append(sr)
+        pieces_c.append(sr)
+        pieces_v.append(half)
+        # the first stored diagonal entry of these rows keeps d - d/4
+        first_of = np.full(m, -1, dtype=np.int64)
+        allr = np.concatenate(pieces_r[:2])
+        allc = np.concatenate(pieces_c[:2])
+        alld = np.nonzero(allr == allc)[0]
+        first_of[allr[alld[::-1]]] = alld[::-1]
+        v01 = np.concatenate(pieces_v[:2])
+        v01[first_of[sr]] -= half
+        pieces_v[0], pieces_v[1] = v01[:len(rows)], v01[len(rows):]
+    r = np.concatenate(pieces_r)
+    c = np.concatenate(pieces_c)
+    v = np.concatenate(pieces_v)
+    o = np.argsort(r, kind="stable")  # entries keep their order within a row
+    return _from_sorted_coo(m, m, r[o], c[o], v[o])
+
+
 # ----------------------------------------------------------------------------
 # Identity and permutations (for invariants)
 # ----------------------------------------------------------------------------
