@@ -11,6 +11,7 @@
 //   bin sizes].
 // Numeric call sequence: split B's values into DF32 pairs (range-checked), one
 // numeric kernel per non-empty bin.  No host synchronisation.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -22,6 +23,7 @@
 #include "kk_device.cuh"
 #include "kk_batched.h"
 #include "kk_learned.h"
+#include "kk_jacobi.h"
 
 namespace kk {
 
@@ -582,6 +584,47 @@ __global__ void __launch_bounds__(kFpThreads) k_fingerprint(FpArrays arr, unsign
 }
 
 // ---------------------------------------------------------------------------
+// Jacobi-fused numeric phase: the values of A' with C = A' B = (I - omega D^-1 A) B,
+// i.e. a'_ij = s_i a_ij and a'_ii = 1 + s_i a_ii at the row's first stored
+// diagonal entry, s_i = -omega / D(i), D(i) = the sum of the row's stored
+// diagonal entries.  One team of kJacTeam lanes per row.
+// ---------------------------------------------------------------------------
+constexpr int kJacTeam = 4;
+__global__ void k_jacobi_values(CsrView A, double omega, double* __restrict__ out, int* status) {
+  const int tl = threadIdx.x % kJacTeam;
+  const unsigned mask = team_mask<kJacTeam>();
+  const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kJacTeam;
+  const long long nteams = (long long)gridDim.x * blockDim.x / kJacTeam;
+  int bad = 0;
+  for (long long r = team0; r < A.m; r += nteams) {
+    const int pa = A.rowptr[r], pe = A.rowptr[r + 1];
+    double d = 0.0;
+    int first = 0x7fffffff;
+    for (int p = pa + tl; p < pe; p += kJacTeam) {
+      if (A.colind[p] == (int)r) {
+        d += A.vals[p];
+        first = min(first, p);
+      }
+    }
+#pragma unroll
+    for (int o = kJacTeam / 2; o > 0; o >>= 1) {
+      d += __shfl_xor_sync(mask, d, o, kJacTeam);
+      first = min(first, __shfl_xor_sync(mask, first, o, kJacTeam));
+    }
+    if (first == 0x7fffffff || d == 0.0) {
+      bad = 1;
+      continue;
+    }
+    const double s = -omega / d;
+    for (int p = pa + tl; p < pe; p += kJacTeam) {
+      const double a = A.vals[p];
+      out[p] = p == first ? fma(s, a, 1.0) : s * a;
+    }
+  }
+  if (bad) set_status(status, KK_ERR_INVALID_ARG);
+}
+
+// ---------------------------------------------------------------------------
 // DF32 split of B's values, with the window check.
 // ---------------------------------------------------------------------------
 // HBM-bound: each thread keeps kSplitUnroll coalesced loads in flight.
@@ -640,6 +683,7 @@ struct kk_spgemm_handle_s {
   DevBuf d_binstart;   // int32[2 * (kMaxBins + 1)]
   DevBuf d_scan;       // long long[nblk]
   DevBuf d_bsplit;     // float2[nnzB]
+  DevBuf d_jvals;      // float64[nnzA]: A's values scaled for the Jacobi-fused numeric phase
   // learned form
   DevBuf d_params;     // float[KK_MLP_NUM_PARAMS]
   bool have_pred = false;
@@ -1060,6 +1104,7 @@ kk_status check_device_status(kk_spgemm_handle h, int status) {
   const char* what = "device error";
   switch (status) {
     case KK_ERR_BAD_INDEX: what = "a column index lies outside its range"; break;
+    case KK_ERR_INVALID_ARG: what = "a row of A has no nonzero stored diagonal (Jacobi)"; break;
     case KK_ERR_CAPACITY: what = "an accumulator overflowed"; break;
     case KK_ERR_STRUCTURE_MISMATCH: what = "the structure differs from the symbolic phase"; break;
     case KK_ERR_TIMEOUT: what = "a bounded device wait ran out"; break;
@@ -1393,6 +1438,32 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
     if (e != cudaSuccess) return cuda_fail(h, e, "numeric launch");
   }
   return KK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Jacobi-fused numeric phase (kk_jacobi.h)
+// ---------------------------------------------------------------------------
+kk_status kk_spgemm_jacobi_numeric(kk_spgemm_handle h, double omega, const kk_csr* A,
+                                   const kk_csr* B, const int64_t* c_rowptr, int32_t* c_colind,
+                                   double* c_vals) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  kk_status st;
+  if ((st = check_csr(h, A, "A", true)) != KK_OK) return st;
+  if (A->m != A->n) return fail(h, KK_ERR_INVALID_ARG, "Jacobi needs a square A");
+  if (!std::isfinite(omega)) return fail(h, KK_ERR_INVALID_ARG, "omega is not finite");
+  if (A->nnz > 0) {
+    KK_CUDA(h, h->d_jvals.ensure(sizeof(double) * (size_t)A->nnz), "alloc Jacobi values");
+  }
+  if (A->m > 0) {
+    timer_begin(h->timer, h->stream, "jacobi_values");
+    k_jacobi_values<<<grid_for((long long)A->m * kJacTeam, 256, h->num_sms * 8), 256, 0, h->stream>>>(
+        view(A), omega, h->d_jvals.as<double>(), &h->d_misc.as<Misc>()->status);
+    timer_end(h->timer, h->stream);
+    KK_CUDA(h, cudaGetLastError(), "Jacobi launch");
+  }
+  kk_csr Aj = *A;
+  Aj.vals = A->nnz > 0 ? h->d_jvals.as<double>() : A->vals;
+  return kk_spgemm_numeric(h, &Aj, B, c_rowptr, c_colind, c_vals);
 }
 
 // ---------------------------------------------------------------------------

@@ -74,6 +74,9 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I32), _I32]),
     "kk_spgemm_stats": (_I32, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    # Jacobi-fused numeric phase (include/kk_jacobi.h)
+    "kk_spgemm_jacobi_numeric": (_I32, [_P, ctypes.c_double, ctypes.POINTER(KkCsr),
+                                        ctypes.POINTER(KkCsr), _P, _P, _P]),
     # learned form (include/kk_learned.h)
     "kk_spgemm_row_features": (_I32, [_P, ctypes.POINTER(KkCsr), ctypes.POINTER(KkCsr), _P]),
     "kk_capacity_classes": (_I32, [_P, _I32, _P, _P]),
@@ -171,6 +174,16 @@ def kk_spgemm_numeric(h, A: "DeviceCSR", B: "DeviceCSR", c_rowptr, c_colind, c_v
                                             ctypes.c_void_p(c_rowptr.data_ptr()),
                                             ctypes.c_void_p(c_colind.data_ptr()),
                                             ctypes.c_void_p(c_vals.data_ptr())), h)
+
+
+def kk_spgemm_jacobi_numeric(h, omega: float, A: "DeviceCSR", B: "DeviceCSR", c_rowptr, c_colind,
+                             c_vals):
+    a, b = A.abi(), B.abi()
+    _check(load_library().kk_spgemm_jacobi_numeric(h, ctypes.c_double(float(omega)), ctypes.byref(a),
+                                                   ctypes.byref(b),
+                                                   ctypes.c_void_p(c_rowptr.data_ptr()),
+                                                   ctypes.c_void_p(c_colind.data_ptr()),
+                                                   ctypes.c_void_p(c_vals.data_ptr())), h)
 
 
 def kk_spgemm_sync(h):
@@ -360,6 +373,19 @@ class SpGEMM:
         if vals is None:
             vals = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
         kk_spgemm_numeric(self.h, A, B, rowptr, colind, vals)
+        return colind[:nnz], vals[:nnz]
+
+    def jacobi_numeric(self, A: DeviceCSR, B: DeviceCSR, rowptr, nnz, omega: float, colind=None,
+                       vals=None):
+        """C = (I - omega D^-1 A) B on the structure of the last symbolic call
+        of (A, B) on this handle."""
+        import torch
+        dev = A.rowptr.device
+        if colind is None:
+            colind = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+        if vals is None:
+            vals = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
+        kk_spgemm_jacobi_numeric(self.h, omega, A, B, rowptr, colind, vals)
         return colind[:nnz], vals[:nnz]
 
     def __call__(self, A: DeviceCSR, B: DeviceCSR) -> DeviceCSR:
