@@ -251,6 +251,49 @@ def bench_learned(args, dA, dB, madds, plain_ms, ci, va):
     return out, params
 
 
+def bench_jacobi(args):
+    """Jacobi-fused numeric phase on the AMG prolongator smoothing of the
+    Galerkin workload: P_s = (I - omega D^-1 A) P with A the 7-point Laplacian
+    on 128^3 and P the 2x2x2 aggregation prolongator, omega = 2/3.  Times the
+    plain symbolic + Jacobi numeric step, the Jacobi numeric refresh alone, and
+    the plain numeric phase of A*P on the same handle (the fused step's cost
+    over the plain product)."""
+    import torch
+    from paper_2103_11991_gb300 import inputs as I
+    from paper_2103_11991_gb300 import spgemm as K
+    g = 128
+    A = I.stencil_3d(g, g, g, 7, 6.0, -1.0)
+    P = I.aggregation_prolongator(g, g, g, 2)
+    dA, dP = K.DeviceCSR.from_host(A), K.DeviceCSR.from_host(P)
+    stream = torch.cuda.current_stream()
+    omega = 2.0 / 3.0
+    op = K.SpGEMM()
+    rp, nnz = op.symbolic(dA, dP)
+    ci, va = op.jacobi_numeric(dA, dP, rp, nnz, omega)
+    op.sync()
+    madds = op.stats()["flops"]
+
+    def step():
+        r, n = op.symbolic(dA, dP)
+        op.jacobi_numeric(dA, dP, r, n, omega, ci, va)
+
+    step_ms = _events_ms(step, 5, stream)
+    jac_ms = _events_ms(lambda: op.jacobi_numeric(dA, dP, rp, nnz, omega, ci, va), 10, stream)
+    plain_ms = _events_ms(lambda: op.numeric(dA, dP, rp, nnz, ci, va), 10, stream)
+    op.close()
+    # compulsory bytes of the fused numeric phase: A (structure + values, read
+    # twice: the scaling pass and the product), its scaled values written and
+    # read, P, C written
+    byts = 2 * (4 * (A.m + 1) + 12 * A.nnz) + 16 * A.nnz + 4 * (P.m + 1) + 12 * P.nnz + 8 * (A.m + 1) \
+        + 12 * nnz
+    return {"workload": "prolongator smoothing (I - 2/3 D^-1 A) P, A 7-point Laplacian 128^3, "
+                        "P 2x2x2 aggregation", "nnz_c": int(nnz), "madds": int(madds),
+            "ms_per_step": step_ms, "value": 2.0 * madds / (step_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "jacobi_numeric_ms": jac_ms, "plain_numeric_ms": plain_ms,
+            "fused_over_plain": jac_ms / plain_ms,
+            "numeric_hbm_gbs": byts / (jac_ms * 1e-3) / 1e9}
+
+
 def bench_batched(args, predictor=None):
     """Batched form on the first `--batch-count` pairs of the 2000-pair
     workload (seeds 5000..), in its execution modes — the batch as one
@@ -490,6 +533,8 @@ def run_ours(args, rank, world, local_rank):
         forms["learned"], predictor = bench_learned(args, dA, dB, madds, ms, ci, va)
     if rank == 0 and args.forms in ("all", "batched"):
         forms["batched"] = bench_batched(args, predictor)
+    if rank == 0 and args.forms in ("all", "jacobi"):
+        forms["jacobi"] = bench_jacobi(args)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -534,8 +579,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per step of the dominant kernel (default: profiles/ncu_traffic.json)")
-    ap.add_argument("--forms", default="all", choices=["all", "learned", "batched", "none"],
-                    help="also measure the learned and batched forms")
+    ap.add_argument("--forms", default="all", choices=["all", "learned", "batched", "jacobi", "none"],
+                    help="also measure the learned, batched and Jacobi-fused forms")
     ap.add_argument("--batch-count", type=int, default=400,
                     help="pairs of the 2000-pair batched workload to measure")
     ap.add_argument("--scale", type=int, default=100,

@@ -589,36 +589,83 @@ __global__ void __launch_bounds__(kFpThreads) k_fingerprint(FpArrays arr, unsign
 // diagonal entry, s_i = -omega / D(i), D(i) = the sum of the row's stored
 // diagonal entries.  One team of kJacTeam lanes per row.
 // ---------------------------------------------------------------------------
-constexpr int kJacTeam = 4;
-__global__ void k_jacobi_values(CsrView A, double omega, double* __restrict__ out, int* status) {
-  const int tl = threadIdx.x % kJacTeam;
-  const unsigned mask = team_mask<kJacTeam>();
-  const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kJacTeam;
-  const long long nteams = (long long)gridDim.x * blockDim.x / kJacTeam;
+// 1/d to about one unit in the last place without the float64 divide (a long
+// sequence on the FP64 pipe, which is slow on this part): a float32 reciprocal
+// refined by two Newton-Raphson steps x <- x + x(1 - d x), each of which about
+// doubles the correct bits (24 -> 48 -> 53).  Outside the float32 range the
+// float64 divide is used.
+__device__ __forceinline__ double jacobi_recip(double d) {
+  const double ad = fabs(d);
+  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+  double x = (double)__frcp_rn((float)d);
+  x = fma(x, fma(-d, x, 1.0), x);
+  x = fma(x, fma(-d, x, 1.0), x);
+  return x;
+}
+
+// T lanes per row, the loads of U entries per lane in flight; a row of at most
+// T * U entries is written from registers.  The next row's bounds are loaded
+// while a row is processed.
+template <int T, int U>
+__global__ void __launch_bounds__(256) k_jacobi_values(CsrView A, double omega, double* __restrict__ out,
+                                                       int* status) {
+  const int tl = threadIdx.x % T;
+  const unsigned mask = team_mask<T>();
+  const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / T;
+  const long long nteams = (long long)gridDim.x * blockDim.x / T;
   int bad = 0;
-  for (long long r = team0; r < A.m; r += nteams) {
-    const int pa = A.rowptr[r], pe = A.rowptr[r + 1];
+  long long r = team0;
+  int pa_n = 0, pe_n = 0;
+  if (r < A.m) {
+    pa_n = A.rowptr[r];
+    pe_n = A.rowptr[r + 1];
+  }
+  for (; r < A.m; r += nteams) {
+    const int pa = pa_n, pe = pe_n;
+    if (r + nteams < A.m) {
+      pa_n = A.rowptr[r + nteams];
+      pe_n = A.rowptr[r + nteams + 1];
+    }
     double d = 0.0;
     int first = 0x7fffffff;
-    for (int p = pa + tl; p < pe; p += kJacTeam) {
-      if (A.colind[p] == (int)r) {
-        d += A.vals[p];
-        first = min(first, p);
+    double v[U];
+    for (int p0 = pa; p0 < pe; p0 += T * U) {
+      int c[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int p = p0 + u * T + tl;
+        c[u] = p < pe ? A.colind[p] : -1;
+        v[u] = p < pe ? A.vals[p] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c[u] == (int)r) {
+          d += v[u];
+          first = min(first, p0 + u * T + tl);
+        }
       }
     }
 #pragma unroll
-    for (int o = kJacTeam / 2; o > 0; o >>= 1) {
-      d += __shfl_xor_sync(mask, d, o, kJacTeam);
-      first = min(first, __shfl_xor_sync(mask, first, o, kJacTeam));
+    for (int o = T / 2; o > 0; o >>= 1) {
+      d += __shfl_xor_sync(mask, d, o, T);
+      first = min(first, __shfl_xor_sync(mask, first, o, T));
     }
     if (first == 0x7fffffff || d == 0.0) {
       bad = 1;
       continue;
     }
-    const double s = -omega / d;
-    for (int p = pa + tl; p < pe; p += kJacTeam) {
-      const double a = A.vals[p];
-      out[p] = p == first ? fma(s, a, 1.0) : s * a;
+    const double s = -omega * jacobi_recip(d);
+    if (pe - pa <= T * U) {  // the row's values are still in registers
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int p = pa + u * T + tl;
+        if (p < pe) out[p] = p == first ? fma(s, v[u], 1.0) : s * v[u];
+      }
+    } else {
+      for (int p = pa + tl; p < pe; p += T) {
+        const double a = A.vals[p];
+        out[p] = p == first ? fma(s, a, 1.0) : s * a;
+      }
     }
   }
   if (bad) set_status(status, KK_ERR_INVALID_ARG);
@@ -1115,6 +1162,20 @@ kk_status check_device_status(kk_spgemm_handle h, int status) {
 
 }  // namespace
 
+// Jacobi scaling pass with teams of T lanes, one resident wave of blocks.
+template <int T, int U>
+static void launch_jacobi_values(kk_spgemm_handle h, const kk_csr* A, double omega) {
+  static int per_sm = 0;
+  if (per_sm == 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_values<T, U>, 256, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    per_sm = 4;
+  }
+  k_jacobi_values<T, U><<<grid_for((long long)A->m * T, 256, h->num_sms * (per_sm > 0 ? per_sm : 1)), 256,
+                          0, h->stream>>>(view(A), omega, h->d_jvals.as<double>(),
+                                          &h->d_misc.as<Misc>()->status);
+}
+
 // Analysis of A with teams of T lanes, one resident wave of blocks (the kernel
 // strides over rows).
 template <int T, int U>
@@ -1456,8 +1517,14 @@ kk_status kk_spgemm_jacobi_numeric(kk_spgemm_handle h, double omega, const kk_cs
   }
   if (A->m > 0) {
     timer_begin(h->timer, h->stream, "jacobi_values");
-    k_jacobi_values<<<grid_for((long long)A->m * kJacTeam, 256, h->num_sms * 8), 256, 0, h->stream>>>(
-        view(A), omega, h->d_jvals.as<double>(), &h->d_misc.as<Misc>()->status);
+    // one lane per row for short rows (AMG operators), a warp for long ones
+    const long long avg = (long long)A->nnz / A->m;
+    if (avg <= 8)
+      launch_jacobi_values<1, 8>(h, A, omega);
+    else if (avg <= 32)
+      launch_jacobi_values<4, 8>(h, A, omega);
+    else
+      launch_jacobi_values<32, 4>(h, A, omega);
     timer_end(h->timer, h->stream);
     KK_CUDA(h, cudaGetLastError(), "Jacobi launch");
   }
