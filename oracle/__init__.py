@@ -17,9 +17,12 @@ Contents
                      plain definitions (numpy).
 ``jacobi.py``        Jacobi-fused SpGEMM C = (I - omega D^-1 A) B, paper Sec.
                      "Jacobi-Fused SpGEMM Kernel", on top of the Gustavson oracle.
+``spadd.py``         sparse matrix addition C = alpha A + beta B, paper Sec. "SpAdd"
+                     (per-row merge of the two rows, plain Python).
 
 Parity status: every function here is pinned by ``tests/test_oracle.py``,
-``tests/test_oracle_mlp.py`` and ``tests/test_oracle_jacobi.py`` (dense brute force, closed forms, invariants,
+``tests/test_oracle_mlp.py``, ``tests/test_oracle_jacobi.py`` and
+``tests/test_oracle_spadd.py`` (dense brute force, closed forms, invariants,
 finite differences).
 """
 from __future__ import annotations
