@@ -24,6 +24,7 @@
 #include "kk_batched.h"
 #include "kk_learned.h"
 #include "kk_jacobi.h"
+#include "kk_spadd.h"
 
 namespace kk {
 
@@ -731,6 +732,9 @@ struct kk_spgemm_handle_s {
   DevBuf d_scan;       // long long[nblk]
   DevBuf d_bsplit;     // float2[nnzB]
   DevBuf d_jvals;      // float64[nnzA]: A's values scaled for the Jacobi-fused numeric phase
+  DevBuf d_apos, d_bpos;  // SpAdd: slot in C's row of every entry of A and of B (int32)
+  DevBuf d_acnt;          // SpAdd: nnz(C(i,:)) (int32[m])
+  DevBuf d_along;         // SpAdd: [0] long-row count, [1..] long rows (int32[m + 1])
   // learned form
   DevBuf d_params;     // float[KK_MLP_NUM_PARAMS]
   bool have_pred = false;
@@ -748,6 +752,11 @@ struct kk_spgemm_handle_s {
   DevBuf d_mm;         // int2[n]   B row min/max columns (features)
   bool learned_valid = false;
   bool p_learned = false;  // the packed batch ran the learned form; its numeric call is due
+  // SpAdd: the arrays, sizes and result of the last symbolic call
+  bool add_valid = false;
+  const void* add_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  int32_t add_m = 0, add_n = 0, add_nnza = 0, add_nnzb = 0;
+  int64_t add_nnzc = 0;
   std::vector<int32_t> lnum_start;
   // batched form
   DevBuf d_bdesc, d_rowpair, d_bflop, d_bsbin, d_bnbin, d_bsrows, d_bnrows, d_bcnt, d_btiles, d_bstart,
@@ -1561,6 +1570,90 @@ kk_status run_scan(kk_spgemm_handle h, int32_t m, const int32_t* cnt, int64_t* o
 }  // namespace
 
 extern "C" {
+
+// ---------------------------------------------------------------------------
+// Sparse matrix addition (kk_spadd.h)
+// ---------------------------------------------------------------------------
+kk_status kk_spadd_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B, int64_t* c_rowptr,
+                            int64_t* nnz_c) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  kk_status st;
+  if ((st = check_csr(h, A, "A", false)) != KK_OK) return st;
+  if ((st = check_csr(h, B, "B", false)) != KK_OK) return st;
+  if (A->m != B->m || A->n != B->n) return fail(h, KK_ERR_INVALID_ARG, "A and B have different shapes");
+  if (!c_rowptr || !nnz_c) return fail(h, KK_ERR_INVALID_ARG, "c_rowptr / nnz_c is NULL");
+  h->add_valid = false;
+  const int32_t m = A->m;
+  cudaStream_t s = h->stream;
+  Misc* dm = h->d_misc.as<Misc>();
+  Misc* hm = static_cast<Misc*>(h->h_pinned);
+  KK_CUDA(h, h->d_apos.ensure(sizeof(int32_t) * (size_t)(A->nnz > 0 ? A->nnz : 1)), "alloc SpAdd");
+  KK_CUDA(h, h->d_bpos.ensure(sizeof(int32_t) * (size_t)(B->nnz > 0 ? B->nnz : 1)), "alloc SpAdd");
+  KK_CUDA(h, h->d_acnt.ensure(sizeof(int32_t) * (size_t)(m > 0 ? m : 1)), "alloc SpAdd");
+  KK_CUDA(h, h->d_along.ensure(sizeof(int32_t) * ((size_t)m + 1)), "alloc SpAdd");
+  // only the status word is reset: the rest of the device record belongs to
+  // the SpGEMM state of this handle (fingerprints, flags), which SpAdd leaves alone
+  KK_CUDA(h, cudaMemsetAsync(&dm->status, 0, sizeof(int), s), "memset");
+  KK_CUDA(h, cudaMemsetAsync(h->d_along.p, 0, sizeof(int32_t), s), "memset");
+  int64_t nnz = 0;
+  if (m > 0) {
+    LaunchCtx ctx = ctx_of(h);
+    timer_begin(h->timer, s, "spadd_symbolic");
+    cudaError_t e = launch_spadd_symbolic(ctx, view(A), view(B), h->d_acnt.as<int32_t>(),
+                                          h->d_apos.as<int32_t>(), h->d_bpos.as<int32_t>(),
+                                          h->d_along.as<int32_t>() + 1, h->d_along.as<int32_t>());
+    timer_end(h->timer, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "SpAdd symbolic launch");
+    timer_begin(h->timer, s, "scan");
+    if ((st = run_scan(h, m, h->d_acnt.as<int32_t>(), c_rowptr, &dm->grand, view(A), nullptr)) != KK_OK)
+      return st;
+    timer_end(h->timer, s);
+  } else {
+    KK_CUDA(h, cudaMemsetAsync(c_rowptr, 0, sizeof(int64_t), s), "memset");
+  }
+  KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
+  KK_CUDA(h, cudaStreamSynchronize(s), "sync");
+  if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
+  if (m > 0) nnz = hm->grand;
+  h->add_valid = true;
+  h->add_key[0] = A->rowptr;
+  h->add_key[1] = A->colind;
+  h->add_key[2] = B->rowptr;
+  h->add_key[3] = B->colind;
+  h->add_m = A->m;
+  h->add_n = A->n;
+  h->add_nnza = A->nnz;
+  h->add_nnzb = B->nnz;
+  h->add_nnzc = nnz;
+  *nnz_c = nnz;
+  return KK_OK;
+}
+
+kk_status kk_spadd_numeric(kk_spgemm_handle h, double alpha, const kk_csr* A, double beta,
+                           const kk_csr* B, const int64_t* c_rowptr, int32_t* c_colind, double* c_vals) {
+  if (!h) return KK_ERR_INVALID_ARG;
+  if (!h->add_valid) return fail(h, KK_ERR_NOT_SYMBOLIC, "SpAdd numeric before SpAdd symbolic");
+  kk_status st;
+  if ((st = check_csr(h, A, "A", true)) != KK_OK) return st;
+  if ((st = check_csr(h, B, "B", true)) != KK_OK) return st;
+  if (A->m != h->add_m || A->n != h->add_n || B->m != h->add_m || B->n != h->add_n ||
+      A->nnz != h->add_nnza || B->nnz != h->add_nnzb || A->rowptr != h->add_key[0] ||
+      A->colind != h->add_key[1] || B->rowptr != h->add_key[2] || B->colind != h->add_key[3])
+    return fail(h, KK_ERR_STRUCTURE_MISMATCH,
+                "SpAdd numeric needs the index arrays of the SpAdd symbolic call");
+  if (!c_rowptr) return fail(h, KK_ERR_INVALID_ARG, "c_rowptr is NULL");
+  if (h->add_nnzc == 0) return KK_OK;
+  if (!c_colind || !c_vals) return fail(h, KK_ERR_INVALID_ARG, "C arrays are NULL");
+  cudaStream_t s = h->stream;
+  timer_begin(h->timer, s, "spadd_numeric");
+  KK_CUDA(h, cudaMemsetAsync(c_vals, 0, sizeof(double) * (size_t)h->add_nnzc, s), "memset");
+  cudaError_t e = launch_spadd_numeric(ctx_of(h), view(A), view(B), alpha, beta, c_rowptr,
+                                       h->d_apos.as<int32_t>(), h->d_bpos.as<int32_t>(), c_colind, c_vals);
+  timer_end(h->timer, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "SpAdd numeric launch");
+  return KK_OK;
+}
+
 
 kk_status kk_spgemm_row_features(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B, float* features) {
   if (!h) return KK_ERR_INVALID_ARG;

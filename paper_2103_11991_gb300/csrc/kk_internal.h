@@ -107,6 +107,17 @@ struct WinScratch {
 // Analysis of B (kk_window.cu): clears *sorted_flag unless every row is
 // strictly ascending, sets KK_ERR_BAD_INDEX on out-of-range structure, and,
 // when bc is non-null, writes the compressed rows (pairs counted into *pairs).
+// Sparse matrix addition (kk_spadd.cu): symbolic counts and the slots of A's
+// and B's entries in C (rows of more than 256 combined entries go through
+// long_rows / *long_count, zeroed by the caller); numeric adds into C's values
+// (zeroed by the caller) and writes C's columns.
+cudaError_t launch_spadd_symbolic(const LaunchCtx& ctx, const CsrView& A, const CsrView& B, int32_t* cnt,
+                                  int32_t* apos, int32_t* bpos, int32_t* long_rows,
+                                  int32_t* long_count);
+cudaError_t launch_spadd_numeric(const LaunchCtx& ctx, const CsrView& A, const CsrView& B, double alpha,
+                                 double beta, const int64_t* c_rowptr, const int32_t* apos,
+                                 const int32_t* bpos, int32_t* c_colind, double* c_vals);
+
 // Numeric phase of window rows with kept structure (kk_kept.cu); rows without
 // it are appended to left_rows / *left_count for the rebuild kernel.
 cudaError_t launch_num_kept(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,

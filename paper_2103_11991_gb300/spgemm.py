@@ -74,6 +74,11 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I32), _I32]),
     "kk_spgemm_stats": (_I32, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    # sparse matrix addition (include/kk_spadd.h)
+    "kk_spadd_symbolic": (_I32, [_P, ctypes.POINTER(KkCsr), ctypes.POINTER(KkCsr), _P,
+                                 ctypes.POINTER(ctypes.c_int64)]),
+    "kk_spadd_numeric": (_I32, [_P, ctypes.c_double, ctypes.POINTER(KkCsr), ctypes.c_double,
+                                ctypes.POINTER(KkCsr), _P, _P, _P]),
     # Jacobi-fused numeric phase (include/kk_jacobi.h)
     "kk_spgemm_jacobi_numeric": (_I32, [_P, ctypes.c_double, ctypes.POINTER(KkCsr),
                                         ctypes.POINTER(KkCsr), _P, _P, _P]),
@@ -184,6 +189,24 @@ def kk_spgemm_jacobi_numeric(h, omega: float, A: "DeviceCSR", B: "DeviceCSR", c_
                                                    ctypes.c_void_p(c_rowptr.data_ptr()),
                                                    ctypes.c_void_p(c_colind.data_ptr()),
                                                    ctypes.c_void_p(c_vals.data_ptr())), h)
+
+
+def kk_spadd_symbolic(h, A: "DeviceCSR", B: "DeviceCSR", c_rowptr) -> int:
+    a, b = A.abi(), B.abi()
+    nnz = ctypes.c_int64(0)
+    _check(load_library().kk_spadd_symbolic(h, ctypes.byref(a), ctypes.byref(b),
+                                            ctypes.c_void_p(c_rowptr.data_ptr()), ctypes.byref(nnz)), h)
+    return int(nnz.value)
+
+
+def kk_spadd_numeric(h, alpha: float, A: "DeviceCSR", beta: float, B: "DeviceCSR", c_rowptr, c_colind,
+                     c_vals):
+    a, b = A.abi(), B.abi()
+    _check(load_library().kk_spadd_numeric(h, ctypes.c_double(float(alpha)), ctypes.byref(a),
+                                           ctypes.c_double(float(beta)), ctypes.byref(b),
+                                           ctypes.c_void_p(c_rowptr.data_ptr()),
+                                           ctypes.c_void_p(c_colind.data_ptr()),
+                                           ctypes.c_void_p(c_vals.data_ptr())), h)
 
 
 def kk_spgemm_sync(h):
@@ -373,6 +396,23 @@ class SpGEMM:
         if vals is None:
             vals = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
         kk_spgemm_numeric(self.h, A, B, rowptr, colind, vals)
+        return colind[:nnz], vals[:nnz]
+
+    def spadd_symbolic(self, A: DeviceCSR, B: DeviceCSR):
+        """Structure of C = alpha A + beta B: (int64 row pointers, nnz(C))."""
+        import torch
+        rowptr = torch.empty(A.m + 1, dtype=torch.int64, device=A.rowptr.device)
+        return rowptr, kk_spadd_symbolic(self.h, A, B, rowptr)
+
+    def spadd_numeric(self, alpha: float, A: DeviceCSR, beta: float, B: DeviceCSR, rowptr, nnz,
+                      colind=None, vals=None):
+        import torch
+        dev = A.rowptr.device
+        if colind is None:
+            colind = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+        if vals is None:
+            vals = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
+        kk_spadd_numeric(self.h, alpha, A, beta, B, rowptr, colind, vals)
         return colind[:nnz], vals[:nnz]
 
     def jacobi_numeric(self, A: DeviceCSR, B: DeviceCSR, rowptr, nnz, omega: float, colind=None,
