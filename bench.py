@@ -294,6 +294,40 @@ def bench_jacobi(args):
             "numeric_hbm_gbs": byts / (jac_ms * 1e-3) / 1e9}
 
 
+def bench_spadd(args):
+    """Sparse matrix addition C = A + B of two 500,000 x 500,000 matrices
+    with 30 uniformly random sorted columns per row (the shape of the paper's
+    SpAdd experiment): symbolic + numeric per step, the numeric refresh alone,
+    and both against their compulsory bytes."""
+    import torch
+    from paper_2103_11991_gb300 import inputs as I
+    from paper_2103_11991_gb300 import spgemm as K
+    n = 500_000
+    A = I.random_rows(n, n, 30, 30, seed=31, purpose="spadd.A")
+    B = I.random_rows(n, n, 30, 30, seed=32, purpose="spadd.B")
+    dA, dB = K.DeviceCSR.from_host(A), K.DeviceCSR.from_host(B)
+    stream = torch.cuda.current_stream()
+    op = K.SpGEMM()
+    rp, nnz = op.spadd_symbolic(dA, dB)
+    ci, va = op.spadd_numeric(1.0, dA, 1.0, dB, rp, nnz)
+    op.sync()
+
+    def step():
+        r, c = op.spadd_symbolic(dA, dB)
+        op.spadd_numeric(1.0, dA, 1.0, dB, r, c, ci, va)
+
+    step_ms = _events_ms(step, 5, stream)
+    num_ms = _events_ms(lambda: op.spadd_numeric(1.0, dA, 1.0, dB, rp, nnz, ci, va), 10, stream)
+    op.close()
+    nz = A.nnz + B.nnz
+    sym_b = 2 * 4 * (n + 1) + 4 * nz + 4 * nz + 8 * (n + 1)           # structure in; slots, row pointers out
+    num_b = 2 * 4 * (n + 1) + 8 * (n + 1) + 16 * nz + 4 * nz + 12 * nnz  # + values and slots in; C out
+    return {"workload": "C = A + B, 500,000^2, 30 random sorted columns per row each",
+            "nnz_a_plus_b": int(nz), "nnz_c": int(nnz), "ms_per_step": step_ms,
+            "numeric_ms": num_ms, "step_gbs": (sym_b + num_b) / (step_ms * 1e-3) / 1e9,
+            "numeric_gbs": num_b / (num_ms * 1e-3) / 1e9, "unit": "GB/s of compulsory bytes"}
+
+
 def bench_batched(args, predictor=None):
     """Batched form on the first `--batch-count` pairs of the 2000-pair
     workload (seeds 5000..), in its execution modes — the batch as one
@@ -535,6 +569,8 @@ def run_ours(args, rank, world, local_rank):
         forms["batched"] = bench_batched(args, predictor)
     if rank == 0 and args.forms in ("all", "jacobi"):
         forms["jacobi"] = bench_jacobi(args)
+    if rank == 0 and args.forms in ("all", "spadd"):
+        forms["spadd"] = bench_spadd(args)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -579,8 +615,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per step of the dominant kernel (default: profiles/ncu_traffic.json)")
-    ap.add_argument("--forms", default="all", choices=["all", "learned", "batched", "jacobi", "none"],
-                    help="also measure the learned, batched and Jacobi-fused forms")
+    ap.add_argument("--forms", default="all", choices=["all", "learned", "batched", "jacobi", "spadd", "none"],
+                    help="also measure the learned, batched, Jacobi-fused and SpAdd forms")
     ap.add_argument("--batch-count", type=int, default=400,
                     help="pairs of the 2000-pair batched workload to measure")
     ap.add_argument("--scale", type=int, default=100,
