@@ -596,8 +596,9 @@ __global__ void __launch_bounds__(kFpThreads) k_fingerprint(FpArrays arr, unsign
 // doubles the correct bits (24 -> 48 -> 53).  Outside the float32 range the
 // float64 divide is used.
 __device__ __forceinline__ double jacobi_recip(double d) {
-  const double ad = fabs(d);
-  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+  // |d| in [2^-99, 2^99], decided on the exponent bits (no float64 compare)
+  const uint32_t e = ((uint32_t)(__double_as_longlong(d) >> 52)) & 0x7FFu;
+  if (e < 1023u - 99u || e > 1023u + 99u) return 1.0 / d;
   double x = (double)__frcp_rn((float)d);
   x = fma(x, fma(-d, x, 1.0), x);
   x = fma(x, fma(-d, x, 1.0), x);
@@ -627,8 +628,12 @@ __global__ void __launch_bounds__(256) k_jacobi_values(CsrView A, double omega, 
       pa_n = A.rowptr[r + nteams];
       pe_n = A.rowptr[r + nteams + 1];
     }
-    double d = 0.0;
-    int first = 0x7fffffff;
+    // The float64 work is kept to one operation per entry plus the row's
+    // reciprocal (FP64 is the scarce pipe on this part): the diagonal value is
+    // picked by selects, repeats of it are added on a branch taken only when a
+    // row has them, and every entry gets one fma with 1 or 0 as the addend.
+    double d = 0.0, dx = 0.0;
+    int first = 0x7fffffff, nd = 0;
     double v[U];
     for (int p0 = pa; p0 < pe; p0 += T * U) {
       int c[U];
@@ -638,20 +643,36 @@ __global__ void __launch_bounds__(256) k_jacobi_values(CsrView A, double omega, 
         c[u] = p < pe ? A.colind[p] : -1;
         v[u] = p < pe ? A.vals[p] : 0.0;
       }
+      const int nd0 = nd;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (c[u] == (int)r) {
-          d += v[u];
-          first = min(first, p0 + u * T + tl);
+        const bool on = c[u] == (int)r;
+        d = (on && nd == 0) ? v[u] : d;
+        nd += on ? 1 : 0;
+        first = on ? min(first, p0 + u * T + tl) : first;
+      }
+      if (nd - nd0 > (nd0 == 0 ? 1 : 0)) {
+        // repeated diagonal entries: all but the lane's first one go to dx
+        int k = nd0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (c[u] == (int)r) {
+            if (k > 0) dx += v[u];
+            ++k;
+          }
         }
       }
     }
+    d += dx;
+    if (T > 1) {
 #pragma unroll
-    for (int o = T / 2; o > 0; o >>= 1) {
-      d += __shfl_xor_sync(mask, d, o, T);
-      first = min(first, __shfl_xor_sync(mask, first, o, T));
+      for (int o = T / 2; o > 0; o >>= 1) {
+        d += __shfl_xor_sync(mask, d, o, T);
+        nd += __shfl_xor_sync(mask, nd, o, T);
+        first = min(first, __shfl_xor_sync(mask, first, o, T));
+      }
     }
-    if (first == 0x7fffffff || d == 0.0) {
+    if (nd == 0 || (__double_as_longlong(d) << 1) == 0) {
       bad = 1;
       continue;
     }
@@ -660,13 +681,10 @@ __global__ void __launch_bounds__(256) k_jacobi_values(CsrView A, double omega, 
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int p = pa + u * T + tl;
-        if (p < pe) out[p] = p == first ? fma(s, v[u], 1.0) : s * v[u];
+        if (p < pe) out[p] = fma(s, v[u], p == first ? 1.0 : 0.0);
       }
     } else {
-      for (int p = pa + tl; p < pe; p += T) {
-        const double a = A.vals[p];
-        out[p] = p == first ? fma(s, a, 1.0) : s * a;
-      }
+      for (int p = pa + tl; p < pe; p += T) out[p] = fma(s, A.vals[p], p == first ? 1.0 : 0.0);
     }
   }
   if (bad) set_status(status, KK_ERR_INVALID_ARG);

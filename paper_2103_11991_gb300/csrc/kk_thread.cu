@@ -76,15 +76,20 @@ k_num_thread(CsrView A, CsrView B, const int64_t* __restrict__ c_rowptr,
       for (int q = B.rowptr[j]; q < be; ++q) {
         const int c = B.colind[q];
         const double b = B.vals[q];
-        bool found = false;
+        // the slot holding c, if any (keys are distinct); the float64 update is
+        // then done once on a value picked by selects, not once per slot under a
+        // predicate (the FP64 pipe is the scarce one on this part)
+        int hit = -1;
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-          if (k < n && key[k] == c) {
-            val[k] = fma(a, b, val[k]);
-            found = true;
-          }
-        }
-        if (!found) {
+        for (int k = 0; k < N; ++k) hit = (k < n && key[k] == c) ? k : hit;
+        if (hit >= 0) {
+          double cur = 0.0;
+#pragma unroll
+          for (int k = 0; k < N; ++k) cur = k == hit ? val[k] : cur;
+          const double t = fma(a, b, cur);
+#pragma unroll
+          for (int k = 0; k < N; ++k) val[k] = k == hit ? t : val[k];
+        } else {
           if (n < N) {
             // insertion keeps the columns ascending
             int pos = 0;
@@ -97,11 +102,12 @@ k_num_thread(CsrView A, CsrView B, const int64_t* __restrict__ c_rowptr,
                 val[k] = val[k - 1];
               }
             }
+            const double prod = a * b;
 #pragma unroll
             for (int k = 0; k < N; ++k) {
               if (k == pos) {
                 key[k] = c;
-                val[k] = a * b;
+                val[k] = prod;
               }
             }
             ++n;
