@@ -268,6 +268,7 @@ k_analyze_a(CsrView A, const int32_t* __restrict__ brp,
 constexpr int kBinBlock = 256;
 constexpr int kBinPerThread = 8;
 constexpr int kBinRows = kBinBlock * kBinPerThread;
+constexpr int kBinScanPer = 8;  // counts per thread in the bin-offset scan
 
 __global__ void __launch_bounds__(kBinBlock)
 k_bin_count(int32_t m, const uint8_t* __restrict__ bin, int32_t nb, int32_t nblk,
@@ -291,16 +292,25 @@ k_bin_count(int32_t m, const uint8_t* __restrict__ bin, int32_t nb, int32_t nblk
 // bin_start[b] = first position of bin b, bin_start[nb] = total.
 __global__ void __launch_bounds__(1024)
 k_bin_scan(int32_t nb, int32_t nblk, int32_t* __restrict__ blk, int32_t* __restrict__ bin_start) {
+  // every thread scans kBinScanPer consecutive counts, so one pass of the
+  // 1024-thread block covers 8,192 (bin, block) counts (few barriers)
+  constexpr int P = kBinScanPer;
   __shared__ int warp_tot[32];
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const long long total = (long long)nb * nblk;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (long long c0 = 0; c0 < total; c0 += blockDim.x) {
-    const long long idx = c0 + threadIdx.x;
-    const int v = idx < total ? blk[idx] : 0;
-    int incl = team_inclusive_scan<32>(v, lane, 0xffffffffu);
+  for (long long c0 = 0; c0 < total; c0 += (long long)blockDim.x * P) {
+    const long long i0 = c0 + (long long)threadIdx.x * P;
+    int v[P];
+    int sum = 0;
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+      v[t] = i0 + t < total ? blk[i0 + t] : 0;
+      sum += v[t];
+    }
+    const int incl = team_inclusive_scan<32>(sum, lane, 0xffffffffu);
     if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
     if (warp == 0) {
@@ -309,13 +319,18 @@ k_bin_scan(int32_t nb, int32_t nblk, int32_t* __restrict__ blk, int32_t* __restr
       warp_tot[lane] = wi - w;
     }
     __syncthreads();
-    const int excl = carry + warp_tot[warp] + incl - v;
-    if (idx < total) {
-      blk[idx] = excl;
-      if (idx % nblk == 0) bin_start[idx / nblk] = excl;
+    int run = carry + warp_tot[warp] + incl - sum;
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+      const long long idx = i0 + t;
+      if (idx < total) {
+        blk[idx] = run;
+        if (idx % nblk == 0) bin_start[idx / nblk] = run;
+      }
+      run += v[t];
     }
     __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    if (threadIdx.x == blockDim.x - 1) carry = run;
     __syncthreads();
   }
   if (threadIdx.x == 0) bin_start[nb] = carry;
