@@ -410,6 +410,24 @@ def _ncu_traffic():
         return None, None
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The maximum of ``value`` over the ranks of the default process group
+    (the value itself without one): replicas report the slowest rank's time."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(madds_per_rank: int, ms: float, world: int) -> float:
+    """Whole-job throughput of ``world`` replicas that each did ``madds_per_rank``
+    multiply-adds in ``ms`` (the slowest rank's time): 2 flops per multiply-add."""
+    return 2.0 * madds_per_rank * world / (ms * 1e-3) / 1e9
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2103_11991_gb300 import inputs as I
@@ -455,13 +473,10 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     op.sync()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
         tdist.barrier()
-    value = 2.0 * madds * world / (ms * 1e-3) / 1e9
+    value = job_gflops(madds, ms, world)
 
     # per-kernel durations on the launching stream (separate, timed handle)
     top = K.SpGEMM(timing=1)
@@ -554,12 +569,8 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = 2.0 * madds * world / (e2e_ms * 1e-3) / 1e9
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, "cuda")
+    e2e_value = job_gflops(madds, e2e_ms, world)
 
     forms = {}
     predictor = None
