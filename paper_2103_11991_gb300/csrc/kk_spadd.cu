@@ -6,7 +6,9 @@
 // shared memory and are sorted by a bitonic network; equal columns are then
 // adjacent, so a scan of "first of its column" flags gives nnz(C(i,:)) and, for
 // every entry of A and of B, its slot in the row of C (the paper's Apos and
-// Bpos).  When both rows are sorted the keys are laid out as A ascending, then
+// Bpos).  Rows that are both strictly ascending take their slots by binary
+// search of each entry in the other row (no sort).  When both rows are sorted
+// (repeats allowed) the keys are laid out as A ascending, then
 // padding, then B descending: a bitonic sequence, so only the final merge
 // stage runs (the paper's sorted-input method); otherwise the full sort runs
 // (its unsorted-input method).  Rows of up to kAddWarpMax combined entries take
@@ -105,6 +107,41 @@ __device__ __forceinline__ void add_load(const CsrView& A, const CsrView& B, int
   }
 }
 
+// First index in the sorted row x[0, len) whose column is >= c.
+__device__ __forceinline__ int add_lower_bound(const int32_t* __restrict__ x, int len, int c) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (x[mid] < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Slots of one strictly ascending row against another (merge by binary
+// search, no sort): entry k of x at column c lands at
+//   k + #{y < c} - #{columns of x before k that are also in y},
+// the last term an exclusive scan of "found in y" flags.  Returns the number
+// of columns x shares with y.
+__device__ __forceinline__ int add_slots_sorted(const int32_t* __restrict__ x, int lx,
+                                                const int32_t* __restrict__ y, int ly,
+                                                int32_t* __restrict__ pos, int lane) {
+  int common = 0;
+  for (int t0 = 0; t0 < lx; t0 += 32) {
+    const int t = t0 + lane;
+    int lb = 0, found = 0;
+    if (t < lx) {
+      const int c = x[t];
+      lb = add_lower_bound(y, ly, c);
+      found = (lb < ly && y[lb] == c) ? 1 : 0;
+    }
+    const int incl = team_inclusive_scan<32>(found, lane, kFull);
+    if (t < lx) pos[t] = t + lb - (common + incl - found);
+    common += __shfl_sync(kFull, incl, 31);
+  }
+  return common;
+}
+
 // One warp per row; rows longer than kAddWarpMax go to the long-row list.
 __global__ void __launch_bounds__(kAddWarps * 32)
 k_spadd_sym_warp(CsrView A, CsrView B, int32_t* __restrict__ cnt, int32_t* __restrict__ apos,
@@ -125,6 +162,24 @@ k_spadd_sym_warp(CsrView A, CsrView B, int32_t* __restrict__ cnt, int32_t* __res
     }
     if (L == 0) {
       if (lane == 0) cnt[r] = 0;
+      continue;
+    }
+    // both rows strictly ascending (no repeated column): slots by binary search
+    int strict_bad = 0;
+    for (int t = lane; t < la; t += 32) {
+      const int c = A.colind[pa + t];
+      if ((unsigned)c >= (unsigned)A.n) bad = 1;
+      if (t > 0 && A.colind[pa + t - 1] >= c) strict_bad = 1;
+    }
+    for (int t = lane; t < lb; t += 32) {
+      const int c = B.colind[pb + t];
+      if ((unsigned)c >= (unsigned)B.n) bad = 1;
+      if (t > 0 && B.colind[pb + t - 1] >= c) strict_bad = 1;
+    }
+    if (!__any_sync(kFull, strict_bad)) {
+      const int common = add_slots_sorted(A.colind + pa, la, B.colind + pb, lb, apos + pa, lane);
+      add_slots_sorted(B.colind + pb, lb, A.colind + pa, la, bpos + pb, lane);
+      if (lane == 0) cnt[r] = la + lb - common;
       continue;
     }
     const int n = next_pow2(L);
