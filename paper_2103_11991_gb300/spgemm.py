@@ -74,6 +74,8 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I32), _I32]),
     "kk_spgemm_stats": (_I32, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    # result download helper (include/kk_copy.h)
+    "kk_copy_to_host": (_I32, [_P, _P, _P, ctypes.c_size_t]),
     # sparse matrix addition (include/kk_spadd.h)
     "kk_spadd_symbolic": (_I32, [_P, ctypes.POINTER(KkCsr), ctypes.POINTER(KkCsr), _P,
                                  ctypes.POINTER(ctypes.c_int64)]),
@@ -207,6 +209,21 @@ def kk_spadd_numeric(h, alpha: float, A: "DeviceCSR", beta: float, B: "DeviceCSR
                                            ctypes.c_void_p(c_rowptr.data_ptr()),
                                            ctypes.c_void_p(c_colind.data_ptr()),
                                            ctypes.c_void_p(c_vals.data_ptr())), h)
+
+
+def kk_copy_to_host(dst, src, stream=None):
+    """Copy device tensor ``src`` into page-locked host tensor ``dst`` (same
+    number of bytes) with the library's streaming kernel on ``stream`` (a
+    torch.cuda.Stream; default torch's current stream).  Asynchronous."""
+    import torch
+    nbytes = src.numel() * src.element_size()
+    if dst.numel() * dst.element_size() < nbytes:
+        raise ValueError("destination smaller than source")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(load_library().kk_copy_to_host(ctypes.c_void_p(raw), ctypes.c_void_p(dst.data_ptr()),
+                                          ctypes.c_void_p(src.data_ptr()), ctypes.c_size_t(nbytes)))
 
 
 def kk_spgemm_sync(h):

@@ -219,3 +219,21 @@ def test_very_wide_k_uses_hash_and_chunk_tiers(tier):
     check_against_oracle(A, B, rp, ci, va)
     key = "num_cta_rows" if tier == 1 else "num_dense_rows"
     assert st[key] > 0
+
+
+def test_copy_to_host_kernel():
+    import torch
+    from paper_2103_11991_gb300 import spgemm as K
+    src = torch.arange(1_000_003, dtype=torch.float64, device="cuda") * 0.5
+    dst = torch.empty(1_000_003, dtype=torch.float64).pin_memory()
+    K.kk_copy_to_host(dst, src)  # 8,000,024 bytes: vectorised kernel
+    torch.cuda.synchronize()
+    assert torch.equal(dst, src.cpu())
+    src32 = torch.arange(1001, dtype=torch.int32, device="cuda")
+    dst32 = torch.zeros(1001, dtype=torch.int32).pin_memory()
+    K.kk_copy_to_host(dst32, src32)  # 4,004 bytes: not a multiple of 16, copy engine
+    torch.cuda.synchronize()
+    assert torch.equal(dst32, src32.cpu())
+    with pytest.raises(K.KKError) as e:  # pageable destination
+        K.kk_copy_to_host(torch.empty(1001, dtype=torch.int32), src32)
+    assert e.value.status == 1
