@@ -278,22 +278,38 @@ k_spadd_num(CsrView A, CsrView B, double alpha, double beta, const int64_t* __re
             int32_t* __restrict__ c_colind, double* __restrict__ c_vals) {
   const int lane = threadIdx.x & 31;
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-  const bool a1 = alpha == 1.0, b1 = beta == 1.0;  // skip the float64 multiply
+  // coefficients of 1 skip the float64 multiply (FP64 is the scarce pipe): the
+  // branches are uniform over the grid, so no multiply is issued at all
+  const bool a1 = alpha == 1.0, b1 = beta == 1.0;
   for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < A.m; r += nw) {
     const int64_t off = c_rowptr[r];
     const int pa = A.rowptr[r], pae = A.rowptr[r + 1];
-    for (int p = pa + lane; p < pae; p += 32) {
-      const int64_t s = off + apos[p];
-      c_colind[s] = A.colind[p];
-      const double v = A.vals[p];
-      atomicAdd(&c_vals[s], a1 ? v : alpha * v);
+    if (a1) {
+      for (int p = pa + lane; p < pae; p += 32) {
+        const int64_t s = off + apos[p];
+        c_colind[s] = A.colind[p];
+        atomicAdd(&c_vals[s], A.vals[p]);
+      }
+    } else {
+      for (int p = pa + lane; p < pae; p += 32) {
+        const int64_t s = off + apos[p];
+        c_colind[s] = A.colind[p];
+        atomicAdd(&c_vals[s], alpha * A.vals[p]);
+      }
     }
     const int pb = B.rowptr[r], pbe = B.rowptr[r + 1];
-    for (int p = pb + lane; p < pbe; p += 32) {
-      const int64_t s = off + bpos[p];
-      c_colind[s] = B.colind[p];
-      const double v = B.vals[p];
-      atomicAdd(&c_vals[s], b1 ? v : beta * v);
+    if (b1) {
+      for (int p = pb + lane; p < pbe; p += 32) {
+        const int64_t s = off + bpos[p];
+        c_colind[s] = B.colind[p];
+        atomicAdd(&c_vals[s], B.vals[p]);
+      }
+    } else {
+      for (int p = pb + lane; p < pbe; p += 32) {
+        const int64_t s = off + bpos[p];
+        c_colind[s] = B.colind[p];
+        atomicAdd(&c_vals[s], beta * B.vals[p]);
+      }
     }
   }
 }
