@@ -14,7 +14,7 @@ and row i of the result is
 so C has the structure of E (B(i,:) is inside E(i,:) because A(i,i) is stored).
 Steps, in that order: E from the Gustavson oracle (``oracle.spgemm``), the
 diagonal D(i) as the sum of the row's stored (i,i) entries (repeated entries
-add, as everywhere in this build), the row factor s_i = -omega / D(i) computed
+add, as in every oracle here), the row factor s_i = -omega / D(i) computed
 once per row, then c = s_i * e + b for every column of E(i,:), with b = B(i,c)
 (repeats summed) or 0 where B(i,:) has no entry.  A row without a diagonal
 entry, or whose diagonal sums to zero, is outside the method's assumption and
