@@ -332,6 +332,76 @@ def bench_jacobi(args):
             "numeric_hbm_gbs": byts / (jac_ms * 1e-3) / 1e9}
 
 
+def bench_galerkin(args):
+    """Galerkin triple product of the AMG workload, Ac = R (A P): A the 7-point
+    Laplacian on 128^3 (6 / -1), P the 2x2x2 aggregation prolongator, R = P^T
+    stored explicitly; two chained products, A*P then R*(AP), each on its own
+    handle.  Times the first product (symbolic + numeric of both) and a numeric
+    refresh of both with the structure kept, A's values rescaled for each
+    refresh by one seeded factor s in [0.5, 2) (the three rescaled value arrays
+    are prepared before timing; the mean over them is reported).  Every result
+    is checked against the closed form Ac = 4 s x (7-point Laplacian on 64^3):
+    exactly for the first product, within 1e-12 of the entry's magnitude after
+    a refresh."""
+    import torch
+    from paper_2103_11991_gb300 import inputs as I
+    from paper_2103_11991_gb300 import spgemm as K
+    d = I.config_inputs("amg_galerkin_128")
+    A, P, R = d["A"], d["P"], d["R"]
+    dA, dP, dR = (K.DeviceCSR.from_host(X) for X in (A, P, R))
+    L = I.stencil_3d(64, 64, 64, 7, 1.0, -1.0)  # pattern and signs of the closed form
+    Lw = torch.from_numpy(np.where(L.vals > 0, 24.0, -4.0)).cuda()
+    stream = torch.cuda.current_stream()
+    ap, rap = K.SpGEMM(), K.SpGEMM()
+    rp1, n1 = ap.symbolic(dA, dP)
+    c1, v1 = ap.numeric(dA, dP, rp1, n1)
+    dAP = K.DeviceCSR(A.m, P.n, rp1.to(torch.int32), c1, v1)
+    rp2, n2 = rap.symbolic(dR, dAP)
+    c2, v2 = rap.numeric(dR, dAP, rp2, n2)
+    rap.sync()
+    madds = ap.stats()["flops"] + rap.stats()["flops"]
+    ok = n2 == L.nnz and bool(torch.equal(v2, Lw)) and \
+        bool(torch.equal(c2, torch.from_numpy(L.colind).cuda())) and \
+        bool(torch.equal(rp2.cpu(), torch.from_numpy(L.rowptr.astype(np.int64))))
+
+    def first():
+        r1, m1 = ap.symbolic(dA, dP)
+        ap.numeric(dA, dP, r1, m1, c1, v1)
+        dAP.rowptr.copy_(r1)
+        r2, m2 = rap.symbolic(dR, dAP)
+        rap.numeric(dR, dAP, r2, m2, c2, v2)
+
+    first_ms = _events_ms(first, 5, stream)
+    scales = I.uniform01(41, "galerkin.refresh", 3) * 1.5 + 0.5
+    base = dA.vals.clone()
+    scaled = [base * float(sc) for sc in scales]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(scales))]
+    refresh_ms = []
+    for k, sc in enumerate(scales):
+        dA.vals = scaled[k]
+        torch.cuda.synchronize()
+        ev[2 * k].record(stream)
+        ap.numeric(dA, dP, rp1, n1, c1, v1)
+        rap.numeric(dR, dAP, rp2, n2, c2, v2)
+        ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        refresh_ms.append(ev[2 * k].elapsed_time(ev[2 * k + 1]))
+        ok = ok and bool(torch.all(torch.abs(v2 - Lw * float(sc)) <= 1e-12 * torch.abs(Lw * float(sc))))
+    ap.close()
+    rap.close()
+    ref_ms = statistics.mean(refresh_ms)
+    # compulsory bytes of the two numeric phases
+    num_b = (12 * A.nnz + 12 * (A.m + 1) + 12 * P.nnz + 4 * (P.m + 1) + 12 * n1) + \
+        (12 * R.nnz + 12 * (R.m + 1) + 12 * n1 + 4 * (A.m + 1) + 12 * n2)
+    return {"workload": "Ac = R (A P), A 7-point Laplacian 128^3, P 2x2x2 aggregation, R = P^T",
+            "nnz_ap": int(n1), "nnz_c": int(n2), "madds": int(madds),
+            "first_ms": first_ms, "first_value": 2.0 * madds / (first_ms * 1e-3) / 1e9,
+            "refresh_ms": ref_ms, "refresh_value": 2.0 * madds / (ref_ms * 1e-3) / 1e9,
+            "refresh_ms_each": refresh_ms, "refresh_scales": [float(x) for x in scales],
+            "refresh_hbm_gbs": num_b / (ref_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "outputs_agree": ok}
+
+
 def bench_spadd(args):
     """Sparse matrix addition C = A + B of two 500,000 x 500,000 matrices
     with 30 uniformly random sorted columns per row (the shape of the paper's
@@ -651,6 +721,8 @@ def run_ours(args, rank, world, local_rank):
         forms["learned"], predictor = bench_learned(args, dA, dB, madds, ms, ci, va)
     if rank == 0 and args.forms in ("all", "batched"):
         forms["batched"] = bench_batched(args, predictor)
+    if rank == 0 and args.forms in ("all", "galerkin"):
+        forms["galerkin"] = bench_galerkin(args)
     if rank == 0 and args.forms in ("all", "jacobi"):
         forms["jacobi"] = bench_jacobi(args)
     if rank == 0 and args.forms in ("all", "spadd"):
@@ -708,7 +780,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per step of the dominant kernel (default: profiles/ncu_traffic.json)")
-    ap.add_argument("--forms", default="all", choices=["all", "learned", "batched", "jacobi", "spadd", "none"],
+    ap.add_argument("--forms", default="all", choices=["all", "learned", "batched", "galerkin", "jacobi", "spadd", "none"],
                     help="also measure the learned, batched, Jacobi-fused and SpAdd forms")
     ap.add_argument("--batch-count", type=int, default=400,
                     help="pairs of the 2000-pair batched workload to measure")

@@ -69,6 +69,16 @@ def test_amg_galerkin_128_full_exact():
         L = I.stencil_3d(64, 64, 64, 7, 24.0, -4.0)
         assert_structure_equal(rp2.cpu().numpy(), c2.cpu().numpy(), L.rowptr, L.colind)
         assert np.array_equal(v2.cpu().numpy(), L.vals)
+        # numeric refreshes on the kept structure, A's values rescaled by s:
+        # R (sA P) = 4 s x the Laplacian, each entry within 1e-12 of its size
+        base = dA.vals.clone()
+        for s in I.uniform01(41, "galerkin.refresh", 3) * 1.5 + 0.5:
+            dA.vals = base * float(s)
+            op1.numeric(dA, dP, rp1, n1, c1, v1)
+            op2.numeric(dR, dAP, rp2, n2, c2, v2)
+            op2.sync()
+            want = L.vals * float(s)
+            assert np.all(np.abs(v2.cpu().numpy() - want) <= 1e-12 * np.abs(want))
 
 
 def test_rmat20_full_sampled():
