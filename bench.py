@@ -440,10 +440,13 @@ def bench_batched(args, predictor=None):
     """Batched form on the first `--batch-count` pairs of the 2000-pair
     workload (seeds 5000..), in its execution modes — the batch as one
     block-diagonal product through the plain kernels (the default), the same
-    through the learned form with the trained predictor (when one is given),
-    and one persistent work-queue launch per phase replayed from a CUDA graph —
-    against the same products as looped plain calls on one stream."""
+    with the autotuner's stored options for the batch family on this device
+    (when a tuning file exists), the same through the learned form with the
+    trained predictor (when one is given), and one persistent work-queue
+    launch per phase replayed from a CUDA graph — against the same products as
+    looped plain calls on one stream."""
     import torch
+    from paper_2103_11991_gb300 import autotune
     from paper_2103_11991_gb300 import inputs as I
     from paper_2103_11991_gb300 import spgemm as K
     t0 = time.perf_counter()
@@ -455,11 +458,14 @@ def bench_batched(args, predictor=None):
     modes = {}
     madds = total = 0
     with torch.cuda.stream(stream):
-        runs = [("packed", 2, 0), ("persistent_graph", 1, 0)]
+        runs = [("packed", 2, 0, {}), ("persistent_graph", 1, 0, {})]
         if predictor is not None:
-            runs.insert(1, ("packed_learned", 2, 1))
-        for name, mode, learned in runs:
-            op = K.BatchedSpGEMM(stream=stream, batched_mode=mode, batched_learned=learned)
+            runs.insert(1, ("packed_learned", 2, 1, {}))
+        tuned = autotune.tuned_options("batch")
+        if tuned:
+            runs.insert(1, ("packed_autotuned", 2, 0, tuned))
+        for name, mode, learned, extra in runs:
+            op = K.BatchedSpGEMM(stream=stream, batched_mode=mode, batched_learned=learned, **extra)
             if learned:
                 op.set_predictor(predictor, 0.95)
             rp, off, total = op.symbolic(dAs, dBs)
@@ -473,6 +479,8 @@ def bench_batched(args, predictor=None):
 
             ms = _events_ms(step, 3, stream)
             modes[name] = {"ms_per_step": ms, "value": 2.0 * madds / (ms * 1e-3) / 1e9}
+            if extra:
+                modes[name]["options"] = extra
             op.close()
             del rp, ci, va
         plain = K.SpGEMM(stream=stream)
@@ -489,11 +497,13 @@ def bench_batched(args, predictor=None):
         torch.cuda.synchronize()
         loop_ms = (time.perf_counter() - t1) * 1e3
         plain.close()
-    best = modes["packed"]["ms_per_step"]
+    best_mode = min(modes, key=lambda k: modes[k]["ms_per_step"])
+    best = modes[best_mode]["ms_per_step"]
     for m in modes.values():
         m["speedup_vs_looped"] = loop_ms / m["ms_per_step"]
     return {"pairs": len(pairs), "rows": int(sum(A.m for A, _ in pairs)), "nnz_c": int(total),
-            "madds": int(madds), "ms_per_step": best, "value": 2.0 * madds / (best * 1e-3) / 1e9,
+            "madds": int(madds), "mode": best_mode, "ms_per_step": best,
+            "value": 2.0 * madds / (best * 1e-3) / 1e9,
             "looped_plain_ms": loop_ms, "looped_plain_value": 2.0 * madds / (loop_ms * 1e-3) / 1e9,
             "speedup_vs_looped": loop_ms / best, "unit": "GFLOP/s", "modes": modes,
             "generation_s": gen_s}
