@@ -318,7 +318,25 @@ def bench_jacobi(args):
     step_ms = _events_ms(step, 5, stream)
     jac_ms = _events_ms(lambda: op.jacobi_numeric(dA, dP, rp, nnz, omega, ci, va), 10, stream)
     plain_ms = _events_ms(lambda: op.numeric(dA, dP, rp, nnz, ci, va), 10, stream)
+    op.jacobi_numeric(dA, dP, rp, nnz, omega, ci, va)  # C holds the fused result again
+    op.sync()
     op.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on the whole workload (about a second on one core), and
+        # the GPU result against it: structure exact, values within 1e-12 of
+        # the per-entry scale |s_i| sum |a||p| + |P(i,c)|
+        from oracle import jacobi as J
+        t = time.perf_counter()
+        ref = J.jacobi_spgemm(A, P, omega)
+        secs = time.perf_counter() - t
+        bound = J.jacobi_abs(A, P, omega)
+        agree = bool(np.array_equal(rp.cpu().numpy(), ref.rowptr) and
+                     np.array_equal(ci.cpu().numpy(), ref.colind) and
+                     np.all(np.abs(va.cpu().numpy() - ref.vals) <= 1e-12 * bound))
+        cpu = {"value": 2.0 * madds / secs / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"the whole workload once, {secs:.2f} s single-threaded",
+               "outputs_agree": agree}
     # compulsory bytes of the fused numeric phase: A (structure + values, read
     # twice: the scaling pass and the product), its scaled values written and
     # read, P, C written
@@ -329,7 +347,7 @@ def bench_jacobi(args):
             "ms_per_step": step_ms, "value": 2.0 * madds / (step_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
             "jacobi_numeric_ms": jac_ms, "plain_numeric_ms": plain_ms,
             "fused_over_plain": jac_ms / plain_ms,
-            "numeric_hbm_gbs": byts / (jac_ms * 1e-3) / 1e9}
+            "numeric_hbm_gbs": byts / (jac_ms * 1e-3) / 1e9, "cpu_baseline": cpu}
 
 
 def bench_galerkin(args):
@@ -426,14 +444,37 @@ def bench_spadd(args):
 
     step_ms = _events_ms(step, 5, stream)
     num_ms = _events_ms(lambda: op.spadd_numeric(1.0, dA, 1.0, dB, rp, nnz, ci, va), 10, stream)
+    op.sync()
     op.close()
     nz = A.nnz + B.nnz
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on the first 50,000 rows (about 2 s on one core), in the
+        # same unit, and the GPU rows against it (exact: at most one term from
+        # each of A and B per entry)
+        from oracle import spadd as S
+        r = 50_000
+        blk = [I.CSR(r, n, X.rowptr[:r + 1], X.colind[:X.rowptr[r]], X.vals[:X.rowptr[r]]) for X in (A, B)]
+        t = time.perf_counter()
+        ref = S.spadd(blk[0], blk[1], 1.0, 1.0)
+        secs = time.perf_counter() - t
+        rpb = rp[:r + 1].cpu().numpy()
+        agree = bool(np.array_equal(rpb, ref.rowptr) and
+                     np.array_equal(ci[:rpb[-1]].cpu().numpy(), ref.colind) and
+                     np.array_equal(va[:rpb[-1]].cpu().numpy(), ref.vals))
+        nzb = blk[0].nnz + blk[1].nnz
+        byts = 2 * 4 * (r + 1) + 4 * nzb + 4 * nzb + 8 * (r + 1) + \
+            2 * 4 * (r + 1) + 8 * (r + 1) + 16 * nzb + 4 * nzb + 12 * int(ref.rowptr[-1])
+        cpu = {"value": byts / secs / 1e9, "unit": "GB/s of compulsory bytes", "cores": 1,
+               "kind": "oracle", "sample": f"rows 0..{r - 1} of {n}, {secs:.2f} s single-threaded",
+               "outputs_agree": agree}
     sym_b = 2 * 4 * (n + 1) + 4 * nz + 4 * nz + 8 * (n + 1)           # structure in; slots, row pointers out
     num_b = 2 * 4 * (n + 1) + 8 * (n + 1) + 16 * nz + 4 * nz + 12 * nnz  # + values and slots in; C out
     return {"workload": "C = A + B, 500,000^2, 30 random sorted columns per row each",
             "nnz_a_plus_b": int(nz), "nnz_c": int(nnz), "ms_per_step": step_ms,
             "numeric_ms": num_ms, "step_gbs": (sym_b + num_b) / (step_ms * 1e-3) / 1e9,
-            "numeric_gbs": num_b / (num_ms * 1e-3) / 1e9, "unit": "GB/s of compulsory bytes"}
+            "numeric_gbs": num_b / (num_ms * 1e-3) / 1e9, "unit": "GB/s of compulsory bytes",
+            "cpu_baseline": cpu}
 
 
 def bench_batched(args, predictor=None):
