@@ -408,6 +408,16 @@ def bench_galerkin(args):
     ap.close()
     rap.close()
     ref_ms = statistics.mean(refresh_ms)
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle's first product of both (A*P, then R*(AP)), on one core
+        import oracle
+        t = time.perf_counter()
+        APo = oracle.spgemm(A, P)
+        oracle.spgemm(R, I.CSR(APo.m, APo.n, APo.rowptr, APo.colind, APo.vals))
+        secs = time.perf_counter() - t
+        cpu = {"value": 2.0 * madds / secs / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first product of both once, {secs:.2f} s single-threaded"}
     # compulsory bytes of the two numeric phases
     num_b = (12 * A.nnz + 12 * (A.m + 1) + 12 * P.nnz + 4 * (P.m + 1) + 12 * n1) + \
         (12 * R.nnz + 12 * (R.m + 1) + 12 * n1 + 4 * (A.m + 1) + 12 * n2)
@@ -417,7 +427,7 @@ def bench_galerkin(args):
             "refresh_ms": ref_ms, "refresh_value": 2.0 * madds / (ref_ms * 1e-3) / 1e9,
             "refresh_ms_each": refresh_ms, "refresh_scales": [float(x) for x in scales],
             "refresh_hbm_gbs": num_b / (ref_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
-            "outputs_agree": ok}
+            "outputs_agree": ok, "cpu_baseline": cpu}
 
 
 def bench_spadd(args):
@@ -538,6 +548,18 @@ def bench_batched(args, predictor=None):
         torch.cuda.synchronize()
         loop_ms = (time.perf_counter() - t1) * 1e3
         plain.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on the first 40 pairs of the batch, on one core
+        import oracle
+        k = min(40, len(pairs))
+        t = time.perf_counter()
+        for A, B in pairs[:k]:
+            oracle.spgemm(A, B)
+        secs = time.perf_counter() - t
+        mk = sum(int(oracle.row_flops(A, B).sum()) for A, B in pairs[:k])
+        cpu = {"value": 2.0 * mk / secs / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"pairs 0..{k - 1}, {secs:.2f} s single-threaded"}
     best_mode = min(modes, key=lambda k: modes[k]["ms_per_step"])
     best = modes[best_mode]["ms_per_step"]
     for m in modes.values():
@@ -547,7 +569,7 @@ def bench_batched(args, predictor=None):
             "value": 2.0 * madds / (best * 1e-3) / 1e9,
             "looped_plain_ms": loop_ms, "looped_plain_value": 2.0 * madds / (loop_ms * 1e-3) / 1e9,
             "speedup_vs_looped": loop_ms / best, "unit": "GFLOP/s", "modes": modes,
-            "generation_s": gen_s}
+            "generation_s": gen_s, "cpu_baseline": cpu}
 
 
 def _ncu_traffic():
