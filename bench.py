@@ -32,6 +32,13 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 WORKLOAD = "stencil3d27_100"
+# Arithmetic of the headline step: native float64 (KK_ARITH_FP64).  The DF32
+# form (float32 pairs, 48-bit significand) is reported beside it in forms.df32.
+HEAD_ARITH = 1
+# FP64 FMA rate of this GPU (profiles/gb300_pipes.md: 1.010 TFLOP/s measured by
+# a throughput probe on the GB300, 0.505 T fused multiply-adds per second): the
+# bound of a numeric phase that does one float64 fma per multiply-add.
+DFMA_PEAK_PER_S = 0.505e12
 WORKLOAD_DESC = ("C=A*A, A = 3D 27-point stencil on 100^3 (1,000,000 rows, 26,463,592 nnz, "
                  "26/-1), CSR int32/f64; C 120,553,784 nnz")
 
@@ -287,6 +294,104 @@ def bench_learned(args, dA, dB, madds, plain_ms, ci, va):
         del cR, vR, dR
         torch.cuda.empty_cache()
     return out, params
+
+
+def bench_df32(args, dA, dB, madds, fp64_ms, ci, va):
+    """The benchmark step with values carried as float32 pairs (DF32: 48-bit
+    significand, B's values truncated to it, error bound (n + 2) 2^-46
+    sum|a||b| for n <= 64 contributions; rows beyond that run in float64):
+    narrower arithmetic than the float64 headline, timed beside it."""
+    import torch
+    from paper_2103_11991_gb300 import spgemm as K
+    stream = torch.cuda.current_stream()
+    op = K.SpGEMM(arith=2)
+    rp, nnz = op.symbolic(dA, dB)
+    op.numeric(dA, dB, rp, nnz, ci, va)
+
+    def step():
+        r, n = op.symbolic(dA, dB)
+        op.numeric(dA, dB, r, n, ci, va)
+
+    ms = _events_ms(step, max(3, args.steps // 2), stream)
+    num_ms = _events_ms(lambda: op.numeric(dA, dB, rp, nnz, ci, va), max(3, args.steps // 2), stream)
+    op.sync()
+    arith = {1: "fp64", 2: "df32"}.get(op.last_arith(), "?")
+    op.close()
+    op = K.SpGEMM(arith=HEAD_ARITH)  # C holds the headline arithmetic's result again
+    r, n = op.symbolic(dA, dB)
+    op.numeric(dA, dB, r, n, ci, va)
+    op.sync()
+    op.close()
+    return {"arith": arith, "note": "float32 pairs, 48-bit significand: narrower than fp64",
+            "ms_per_step": ms, "value": 2.0 * madds / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "numeric_ms": num_ms, "speedup_vs_fp64": fp64_ms / ms}
+
+
+def bench_latency(args):
+    """Latency of the small plain product C = A*A, A the 2D 5-point Laplacian
+    on 64^2 (4,096 rows, 20,224 nonzeros): median over --latency-calls calls
+    of a complete product as the caller sees it (symbolic with its nnz(C)
+    read-back, numeric, sync; host clock), and of a numeric refresh on the
+    kept structure; the device time per call from CUDA events beside it."""
+    import torch
+    from paper_2103_11991_gb300 import inputs as I
+    from paper_2103_11991_gb300 import spgemm as K
+    A = I.config_inputs("stencil2d_64")["A"]
+    dA = K.DeviceCSR.from_host(A)
+    stream = torch.cuda.current_stream()
+    op = K.SpGEMM(arith=HEAD_ARITH)
+    rp, nnz = op.symbolic(dA, dA)
+    ci, va = op.numeric(dA, dA, rp, nnz)
+    op.sync()
+    madds = op.stats()["flops"]
+    n = max(10, args.latency_calls)
+
+    def full():
+        r, c = op.symbolic(dA, dA)
+        op.numeric(dA, dA, r, c, ci, va)
+        op.sync()
+
+    def refresh():
+        op.numeric(dA, dA, rp, nnz, ci, va)
+        op.sync()
+
+    out = {"workload": "C = A*A, A 2D 5-point Laplacian 64^2 (4/-1), FP64", "nnz_c": int(nnz),
+           "madds": int(madds), "calls": n, "unit": "us"}
+    for name, fn in (("product", full), ("numeric_refresh", refresh)):
+        for _ in range(20):
+            fn()
+        lat = []
+        for _ in range(n):
+            t = time.perf_counter()
+            fn()
+            lat.append((time.perf_counter() - t) * 1e6)
+        lat.sort()
+        out[name] = {"median_us": lat[n // 2], "p10_us": lat[n // 10], "p90_us": lat[(9 * n) // 10]}
+    out["product"]["device_us"] = 1e3 * _events_ms(
+        lambda: op.numeric(dA, dA, *op.symbolic(dA, dA), ci, va), 100, stream)
+    out["numeric_refresh"]["device_us"] = 1e3 * _events_ms(
+        lambda: op.numeric(dA, dA, rp, nnz, ci, va), 100, stream)
+    out["value"] = 2.0 * madds / (out["product"]["median_us"] * 1e-6) / 1e9
+    out["value_unit"] = "GFLOP/s at the median product latency"
+    out["cpu_baseline"] = None
+    if not args.no_cpu_baseline:
+        # the oracle's latency for the same product on one core, and the GPU
+        # result against it (integer-valued stencil: exact)
+        import oracle
+        lat = []
+        for _ in range(20):
+            t = time.perf_counter()
+            ref = oracle.spgemm(A, A)
+            lat.append((time.perf_counter() - t) * 1e6)
+        lat.sort()
+        out["cpu_baseline"] = {
+            "value": lat[10], "unit": "us (median latency)", "cores": 1, "kind": "oracle",
+            "sample": "the whole product, 20 calls single-threaded",
+            "outputs_agree": bool(np.array_equal(rp.cpu().numpy(), ref.rowptr) and
+                                  np.array_equal(ci.cpu().numpy(), ref.colind) and
+                                  np.array_equal(va.cpu().numpy(), ref.vals))}
+    op.close()
+    return out
 
 
 def bench_jacobi(args):
@@ -627,7 +732,7 @@ def run_ours(args, rank, world, local_rank):
     d = I.config_inputs("stencil3d27_100", scale=args.scale)
     A, B = d["A"], d["B"]
     dA, dB = K.DeviceCSR.from_host(A), K.DeviceCSR.from_host(B)
-    op = K.SpGEMM()
+    op = K.SpGEMM(arith=HEAD_ARITH)
     # warm-up (also sizes the handle's scratch and C)
     rp, nnz = op.symbolic(dA, dB)
     ci, va = op.numeric(dA, dB, rp, nnz)
@@ -660,7 +765,7 @@ def run_ours(args, rank, world, local_rank):
     value = job_gflops(madds, ms, world)
 
     # per-kernel durations on the launching stream (separate, timed handle)
-    top = K.SpGEMM(timing=1)
+    top = K.SpGEMM(timing=1, arith=HEAD_ARITH)
     for _ in range(2):
         trp, tnnz = top.symbolic(dA, dB)
         tci, tva = top.numeric(dA, dB, trp, tnnz)
@@ -688,11 +793,13 @@ def run_ours(args, rank, world, local_rank):
                "num_team_vec": "team", "num_team_flat": "team", "num_cta": "cta", "num_dense": "dense"}
     if tier_of.get(dom_name) == "window":
         dom_ms = sum(kt[k][0] for k in ("num_kept", "num_window") if k in kt)
+    dom_madds = None
     if dom_name in tier_of:
         t = tier_of[dom_name]
         rows_t = tst[f"num_{t}_rows"] if t != "window" else tst["num_window_rows"]
         per_step_bytes = (12 * tst[f"num_{t}_a"] + 12 * (rows_t + 1) + 12 * tst[f"num_{t}_c"]
                           + 12 * B.nnz + 4 * (B.m + 1))
+        dom_madds = tst[f"num_{t}_f"]
     elif dom_name.startswith("sym_"):
         per_step_bytes = sym_b
     else:
@@ -719,6 +826,14 @@ def run_ours(args, rank, world, local_rank):
         "ms_per_step": dom_ms_per_step,
         "step_frac": (sym_b + num_b) / (ms * 1e-3) / 1e9 / peak,
     }
+    if dom_madds is not None:
+        # the FP64 pipe bound of the same kernel: one float64 fma per multiply-add
+        dfma = dom_madds / (dom_ms_per_step * 1e-3)
+        roofline["dfma"] = {
+            "bound": "fp64_fma", "achieved": dfma / 1e12, "peak": DFMA_PEAK_PER_S / 1e12,
+            "unit": "T FMA/s", "frac": dfma / DFMA_PEAK_PER_S, "madds_per_step": dom_madds,
+            "floor_ms": dom_madds / DFMA_PEAK_PER_S * 1e3,
+            "peak_source": "measured FP64 FMA probe on this GPU model (profiles/gb300_pipes.md)"}
     kernels = {k: {"ms_per_step": v[0] / reps, "launches_per_step": v[1] / reps} for k, v in kt.items()}
 
     # end to end through the API with host buffers: every step copies A in from
@@ -766,7 +881,7 @@ def run_ours(args, rank, world, local_rank):
 
     e2e_serial_ms = timed(serial, e2e_steps)
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    pops = [K.SpGEMM(stream=st_) for st_ in streams]
+    pops = [K.SpGEMM(stream=st_, arith=HEAD_ARITH) for st_ in streams]
     pbuf = [(torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda"),
              torch.empty(max(nnz, 1), dtype=torch.float64, device="cuda")) for _ in streams]
     houts = [hout0, host_out()]
@@ -790,6 +905,10 @@ def run_ours(args, rank, world, local_rank):
 
     forms = {}
     predictor = None
+    if rank == 0 and args.forms in ("all", "df32"):
+        forms["df32"] = bench_df32(args, dA, dB, madds, ms, ci, va)
+    if rank == 0 and args.forms in ("all", "latency"):
+        forms["stencil2d_64"] = bench_latency(args)
     if rank == 0 and args.forms in ("all", "learned"):
         forms["learned"], predictor = bench_learned(args, dA, dB, madds, ms, ci, va)
     if rank == 0 and args.forms in ("all", "batched"):
@@ -825,6 +944,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "nnz_c": nnz,
                        "madds": madds, "l2": "inputs larger than L2 (A 318 MB); no flush",
                        "arith": {1: "fp64", 2: "df32"}.get(op.last_arith(), "?"),
+                       "batch_pairs": args.batch_count,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -853,9 +973,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per step of the dominant kernel (default: profiles/ncu_traffic.json)")
-    ap.add_argument("--forms", default="all", choices=["all", "learned", "batched", "galerkin", "jacobi", "spadd", "none"],
-                    help="also measure the learned, batched, Jacobi-fused and SpAdd forms")
-    ap.add_argument("--batch-count", type=int, default=400,
+    ap.add_argument("--forms", default="all",
+                    choices=["all", "df32", "latency", "learned", "batched", "galerkin", "jacobi", "spadd",
+                             "none"],
+                    help="also measure the DF32 arithmetic, the 64^2 latency, the learned, batched, "
+                         "Jacobi-fused and SpAdd forms")
+    ap.add_argument("--latency-calls", type=int, default=1000,
+                    help="calls of the 64^2 5-point product whose median latency is reported")
+    ap.add_argument("--batch-count", type=int, default=2000,
                     help="pairs of the 2000-pair batched workload to measure")
     ap.add_argument("--scale", type=int, default=100,
                     help="grid edge of the 27-point workload (100 = the benchmark; smaller only "

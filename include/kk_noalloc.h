@@ -3,12 +3,13 @@
  * first).
  *
  * The paper has no counterpart of this entry point.  It exists for callers
- * that cannot call cudaMalloc: code running inside a CUDA-graph capture or a
- * memory-pool-restricted context, allocators that forbid device allocations
- * behind their back, and real-time paths where an allocation (and the
- * implicit synchronisation it may bring) is not allowed.  The regular
- * kk_spgemm_symbolic needs a handle, and creating a handle and growing its
- * scratch allocate device memory.
+ * that cannot call cudaMalloc: a host application that owns all device memory
+ * through its own pool allocator and forbids allocations behind its back, a
+ * plug-in that runs inside such a framework, or a latency-critical loop in
+ * which an allocation (and the device-wide synchronisation cudaMalloc and
+ * cudaFree may bring) is not allowed.  The regular kk_spgemm_symbolic needs a
+ * handle, and creating a handle and growing its scratch allocate device
+ * memory.
  *
  * kk_spgemm_symbolic_noalloc computes the same row pointers and nnz(C) as
  * kk_spgemm_symbolic for C = A*B (same conventions: int32 A / B structure on
@@ -30,9 +31,14 @@
  * The call is enqueued on cuda_stream (NULL = legacy default stream) and
  * blocks until nnz(C) is on the host.  Errors: KK_ERR_INVALID_ARG (NULL or
  * inconsistent arguments), KK_ERR_CAPACITY (too many rows), KK_ERR_BAD_INDEX
- * (a column index of A outside B's rows), KK_ERR_CUDA.  It uses a slower
- * single-kernel counting scheme (one CTA per row, chunked bit vector) than the
- * binned kernels of kk_spgemm_symbolic.
+ * (A.rowptr[0] != 0, a row of A whose bounds are decreasing or outside A's
+ * entries, a column of A outside B's rows, a referenced row of B whose bounds
+ * are decreasing or outside B's entries, or a column of B outside [0, B.n)):
+ * every row is checked before any of its indices is used to read memory, and a
+ * bad row counts 0 -- c_rowptr is still written, but nnz_c is not set),
+ * KK_ERR_CUDA.  It uses a slower counting scheme (one CTA per row, a bit vector
+ * swept over the row's non-empty 32768-column windows) than the binned kernels
+ * of kk_spgemm_symbolic.
  */
 #ifndef KK_NOALLOC_H_
 #define KK_NOALLOC_H_

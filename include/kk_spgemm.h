@@ -183,7 +183,9 @@ kk_status kk_spgemm_kernel_times(kk_spgemm_handle h, int32_t max_kernels, const 
  * numeric tier (team, CTA, dense, window), for per-kernel byte accounting;
  * stats[24] = window rows whose structure the last symbolic call kept for the
  * numeric phase (options.structure_cache), stats[25] = (word, mask) pairs of
- * the compressed B it built (compare with nnz(B)); stats[26..31] = 0. */
+ * the compressed B it built (compare with nnz(B)); after a plain symbolic
+ * call stats[26..29] = multiply-adds of the rows in each numeric tier (team,
+ * CTA, dense, window), for the FP64-pipe bound; stats[30..31] = 0. */
 kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[32]);
 
 #ifdef __cplusplus

@@ -496,9 +496,10 @@ struct TierOfBin {
 };
 
 __global__ void k_tier_sums(int32_t m, const uint8_t* __restrict__ nbin, const int64_t* __restrict__ rowptr,
-                            const int32_t* __restrict__ arp, TierOfBin tb, unsigned long long* tier_c,
-                            unsigned long long* tier_a) {
-  unsigned long long c[4] = {0, 0, 0, 0}, a[4] = {0, 0, 0, 0};
+                            const int32_t* __restrict__ arp, const long long* __restrict__ flop, TierOfBin tb,
+                            unsigned long long* tier_c, unsigned long long* tier_a,
+                            unsigned long long* tier_f) {
+  unsigned long long c[4] = {0, 0, 0, 0}, a[4] = {0, 0, 0, 0}, f[4] = {0, 0, 0, 0};
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (long long)gridDim.x * blockDim.x) {
     const uint8_t b = nbin[i];
@@ -506,6 +507,7 @@ __global__ void k_tier_sums(int32_t m, const uint8_t* __restrict__ nbin, const i
     const int t = tb.tier[b];
     c[t] += (unsigned long long)(rowptr[i + 1] - rowptr[i]);
     a[t] += (unsigned long long)(arp[i + 1] - arp[i]);
+    f[t] += (unsigned long long)flop[i];
   }
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
@@ -513,10 +515,12 @@ __global__ void k_tier_sums(int32_t m, const uint8_t* __restrict__ nbin, const i
     for (int o = 16; o > 0; o >>= 1) {
       c[t] += __shfl_xor_sync(0xffffffffu, c[t], o);
       a[t] += __shfl_xor_sync(0xffffffffu, a[t], o);
+      f[t] += __shfl_xor_sync(0xffffffffu, f[t], o);
     }
     if ((threadIdx.x & 31) == 0) {
       if (c[t]) atomicAdd(&tier_c[t], c[t]);
       if (a[t]) atomicAdd(&tier_a[t], a[t]);
+      if (f[t]) atomicAdd(&tier_f[t], f[t]);
     }
   }
 }
@@ -852,6 +856,7 @@ struct Misc {
   long long grand2;
   unsigned long long tier_c[4];  // numeric tiers: C entries of their rows
   unsigned long long tier_a[4];  // numeric tiers: A entries of their rows
+  unsigned long long tier_f[4];  // numeric tiers: multiply-adds of their rows
   unsigned long long kept;       // window rows whose structure was kept
   unsigned long long bc_pairs;   // pairs of the compressed B
   unsigned long long fp[2];      // structure fingerprints: symbolic call, numeric call
@@ -1448,7 +1453,8 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
     if ((st = run_binning(h, m, h->d_nbin.as<uint8_t>(), nbn, h->d_nrows.as<int32_t>(), num_start)) != KK_OK)
       return st;
     k_tier_sums<<<grid_for(m, 256, h->num_sms * 8), 256, 0, s>>>(
-        m, h->d_nbin.as<uint8_t>(), c_rowptr, av.rowptr, tier_of_bins(h->num_bins), dm->tier_c, dm->tier_a);
+        m, h->d_nbin.as<uint8_t>(), c_rowptr, av.rowptr, h->d_flop.as<long long>(), tier_of_bins(h->num_bins),
+        dm->tier_c, dm->tier_a, dm->tier_f);
   } else {
     KK_CUDA(h, cudaMemsetAsync(c_rowptr, 0, sizeof(int64_t), s), "memset rowptr");
     KK_CUDA(h, cudaMemsetAsync(num_start, 0, sizeof(int32_t) * (nbn + 1), s), "memset");
@@ -1467,6 +1473,7 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   for (int t = 0; t < 4; ++t) {
     h->stats[16 + t] = (int64_t)hm->tier_c[t];
     h->stats[20 + t] = (int64_t)hm->tier_a[t];
+    h->stats[26 + t] = (int64_t)hm->tier_f[t];
   }
   h->stats[24] = (int64_t)hm->kept;
   h->stats[25] = (int64_t)hm->bc_pairs;
@@ -1494,7 +1501,9 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
   const CsrView av = view(A), bv = view(B);
   cudaStream_t s = h->stream;
   Misc* dm = h->d_misc.as<Misc>();
-  const int32_t arith = h->opt.arith == KK_ARITH_FP64 ? kArithF64 : kArithDF32;
+  // DF32 needs B's rows strictly ascending (its error bound counts at most
+  // nnz(A(i,:)) contributions per entry); otherwise the product runs in float64
+  const int32_t arith = (h->opt.arith == KK_ARITH_FP64 || !h->b_sorted) ? kArithF64 : kArithDF32;
   h->last_arith = arith;
   if (h->am == 0 || h->nnz_c == 0) return KK_OK;
   const float2* bsplit = nullptr;
@@ -1790,7 +1799,9 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
   std::vector<int32_t> lstart(h_start, h_start + nbl + 1);
   KK_CUDA(h, h->d_scol.ensure(sizeof(int32_t) * (size_t)(staging > 0 ? staging : 1)), "alloc staging");
   KK_CUDA(h, h->d_sval.ensure(sizeof(double) * (size_t)(staging > 0 ? staging : 1)), "alloc staging");
-  const int32_t arith = h->opt.arith == KK_ARITH_FP64 ? kArithF64 : kArithDF32;
+  // DF32 needs B's rows strictly ascending (its error bound counts at most
+  // nnz(A(i,:)) contributions per entry); otherwise the product runs in float64
+  const int32_t arith = (h->opt.arith == KK_ARITH_FP64 || !h->b_sorted) ? kArithF64 : kArithDF32;
   h->last_arith = arith;
   if (arith == kArithDF32 && bv.nnz > 0) {
     KK_CUDA(h, h->d_bsplit.ensure(sizeof(float2) * (size_t)bv.nnz), "alloc split");

@@ -289,7 +289,8 @@ __device__ __forceinline__ void warp_num_row(const PairDesc& p, int i, long long
   }
   __syncwarp();
   const int pa = p.A.rowptr[i], pe = p.A.rowptr[i + 1];
-  const bool df = df_all && p.range_bad == 0 && row_df_ok<32>(p.A.vals, pa, pe, lane, 0xffffffffu);
+  const bool df = df_all && p.range_bad == 0 && p.b_sorted && df_row_terms_ok(pa, pe) &&
+                  row_df_ok<32>(p.A.vals, pa, pe, lane, 0xffffffffu);
   const bool atomic = flat || !p.b_sorted;
   const FullRange rng{p.A.colind, p.B.rowptr};
   const int32_t* bcol = p.B.colind;
@@ -352,7 +353,8 @@ __device__ __forceinline__ void cta_num_row(const PairDesc& p, int i, long long 
     vals[s] = 0ull;
   }
   const int pa = p.A.rowptr[i], pe = p.A.rowptr[i + 1];
-  const bool df = df_all && p.range_bad == 0 && block_df_ok(p.A.vals, pa, pe, flag);  // syncs
+  const bool df = df_all && p.range_bad == 0 && p.b_sorted && df_row_terms_ok(pa, pe) &&
+                  block_df_ok(p.A.vals, pa, pe, flag);  // syncs
   const FullRange rng{p.A.colind, p.B.rowptr};
   const int32_t* bcol = p.B.colind;
   const double* bval = p.B.vals;

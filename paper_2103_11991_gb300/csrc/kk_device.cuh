@@ -108,11 +108,20 @@ __device__ __forceinline__ int map_slot(int* keys, int32_t key, int log2s, int* 
 // step (two-sum of the high parts, float32 add of the low parts, fast-two-sum
 // renormalisation) < 2^-47 of the running magnitude.  For n contributions to one
 // entry the error stays below (n + 2) * 2^-46 * sum|a||b|, which is under
-// 1e-12 * sum|a||b| for n <= 68 and, with independent rounding, far below it
-// for longer sums.  Small integer values and their products are exact.
+// 1e-12 * sum|a||b| for n <= 68.  Small integer values and their products are
+// exact.
+//
+// So a row takes DF32 only where that bound holds for every entry of C(i,:):
+// B's rows strictly ascending (checked by the B analysis; otherwise the whole
+// product runs in float64), which caps an entry's contributions at
+// nnz(A(i,:)), and nnz(A(i,:)) <= kDfMaxTerms.  Longer rows run in float64.
 // ---------------------------------------------------------------------------
 constexpr int kDfMinExp = -50;
 constexpr int kDfMaxExp = 50;
+constexpr int kDfMaxTerms = 64;
+
+// True if the DF32 bound holds for a row of A with entries [pa, pe).
+__device__ __forceinline__ bool df_row_terms_ok(int pa, int pe) { return pe - pa <= kDfMaxTerms; }
 
 struct DF {
   float hi, lo;

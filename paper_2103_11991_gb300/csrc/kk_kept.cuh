@@ -215,6 +215,7 @@ __device__ __forceinline__ bool kept_values(int pa, int pe, bool df_all,
                                             const int32_t* __restrict__ bcol,
                                             const float2* __restrict__ bspl,
                                             const double* __restrict__ bval, int lane, int& missing) {
+  df_all = df_all && df_row_terms_ok(pa, pe);
   bool df = df_all;
   if (df_all && pe - pa > 32) df = row_df_ok<32>(aval, pa, pe, lane, 0xffffffffu);
   for (int p0 = pa; p0 < pe; p0 += 32) {

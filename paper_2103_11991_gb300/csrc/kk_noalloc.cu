@@ -8,11 +8,13 @@
 // on a device the addresses are looked up with cudaGetSymbolAddress while that
 // device is current and cached per device.
 //
-// Work: one CTA per row counts the distinct columns of C(i,:) with a shared-
-// memory bit vector swept over the row's column range in chunks (the dense
-// symbolic accumulator of the paper's Sec. "Standard SpGEMM Kernel"), writes
-// the count to the scratch array, and two scan kernels turn the counts into
-// C's row pointers (scratch block sums).
+// Work: one CTA per row first checks every index the row will read (A's row
+// bounds and columns, the bounds and columns of each referenced B row), then
+// counts the distinct columns of C(i,:) with a shared-memory bit vector swept
+// over the row's non-empty 32768-column windows (the dense symbolic
+// accumulator of the paper's Sec. "Standard SpGEMM Kernel"), writes the count
+// to the scratch array, and two scan kernels turn the counts into C's row
+// pointers (scratch block sums).
 #include <mutex>
 
 #include "kk_device.cuh"
@@ -42,18 +44,8 @@ std::mutex g_na_mutex;
 NaScratch g_na_dev[64];
 bool g_na_ready[64] = {false};
 
-// Column range of row i's products (min, max); (INT_MAX, -1) when empty.
-__device__ void na_row_range(const CsrView& A, const CsrView& B, int i, int* red_lo, int* red_hi,
-                             int& lo, int& hi) {
-  int l = 0x7fffffff, h = -1;
-  for (int p = A.rowptr[i] + threadIdx.x; p < A.rowptr[i + 1]; p += blockDim.x) {
-    const int j = A.colind[p];
-    for (int q = B.rowptr[j]; q < B.rowptr[j + 1]; ++q) {
-      const int c = B.colind[q];
-      l = min(l, c);
-      h = max(h, c);
-    }
-  }
+// Block-wide min / max of (l, h) through the per-warp slots red_lo / red_hi.
+__device__ void na_block_minmax(int* red_lo, int* red_hi, int& l, int& h) {
   for (int o = 16; o > 0; o >>= 1) {
     l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
     h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
@@ -71,8 +63,34 @@ __device__ void na_row_range(const CsrView& A, const CsrView& B, int i, int* red
     h = max(h, red_hi[w]);
   }
   __syncthreads();
-  lo = l;
-  hi = h;
+}
+
+// Checks every index row i's products read, before any of them is used to
+// index: A's row bounds (A.rowptr[0] must be 0), A's columns inside B's rows,
+// the bounds of each referenced B row inside B's entries, and B's columns
+// inside [0, B.n).  Returns true (for the whole block) if any check failed.
+__device__ bool na_row_bad(const CsrView& A, const CsrView& B, int i, int pa, int pe) {
+  int bad = 0;
+  if (i == 0 && threadIdx.x == 0 && A.rowptr[0] != 0) bad = 1;
+  if (pa < 0 || pe < pa || pe > A.nnz) bad = 1;
+  if (__syncthreads_or(bad)) return true;
+  for (int p = pa + threadIdx.x; p < pe; p += blockDim.x) {
+    const int j = A.colind[p];
+    if ((unsigned)j >= (unsigned)B.m) {
+      bad = 1;
+      continue;
+    }
+    const int bs = B.rowptr[j], be = B.rowptr[j + 1];
+    if (bs < 0 || be < bs || be > B.nnz) bad = 1;
+  }
+  if (__syncthreads_or(bad)) return true;
+  // every referenced B row is now known to lie inside B's entries
+  for (int p = pa + threadIdx.x; p < pe; p += blockDim.x) {
+    const int j = A.colind[p];
+    for (int q = B.rowptr[j]; q < B.rowptr[j + 1]; ++q)
+      if ((unsigned)B.colind[q] >= (unsigned)B.n) bad = 1;
+  }
+  return __syncthreads_or(bad) != 0;
 }
 
 __global__ void __launch_bounds__(kNaBlock)
@@ -82,32 +100,36 @@ k_na_count(CsrView A, CsrView B, int32_t* __restrict__ counts, int* __restrict__
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = blockIdx.x; i < A.m; i += gridDim.x) {
     const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
-    if (pa < 0 || pe < pa || pe > A.nnz) {
-      if (threadIdx.x == 0) atomicCAS(status, 0, KK_ERR_BAD_INDEX);
-      if (threadIdx.x == 0) counts[i] = 0;
-      continue;
-    }
-    int bad = 0;
-    for (int p = pa + threadIdx.x; p < pe; p += blockDim.x)
-      if ((unsigned)A.colind[p] >= (unsigned)B.m) bad = 1;
-    if (__syncthreads_or(bad)) {
+    if (na_row_bad(A, B, i, pa, pe)) {
       if (threadIdx.x == 0) {
         atomicCAS(status, 0, KK_ERR_BAD_INDEX);
         counts[i] = 0;
       }
       continue;
     }
-    int lo, hi;
-    na_row_range(A, B, i, red_lo, red_hi, lo, hi);
+    // smallest column of the row's products (the first window starts there)
+    int c0 = 0x7fffffff, unused = -1;
+    for (int p = pa + threadIdx.x; p < pe; p += blockDim.x) {
+      const int j = A.colind[p];
+      for (int q = B.rowptr[j]; q < B.rowptr[j + 1]; ++q) c0 = min(c0, B.colind[q]);
+    }
+    na_block_minmax(red_lo, red_hi, c0, unused);
     int total = 0;
-    for (long long c0 = lo; c0 <= hi; c0 += kNaChunkBits) {
+    // One pass per non-empty window of kNaChunkBits columns: a pass counts the
+    // columns in [c0, c0 + kNaChunkBits) and finds the smallest column past
+    // the window, where the next pass starts (empty windows are skipped, so
+    // the number of passes is at most the number of products).
+    while (c0 != 0x7fffffff) {
       for (int w = threadIdx.x; w < kNaChunkBits / 32; w += blockDim.x) bits[w] = 0u;
       __syncthreads();
+      int next = 0x7fffffff, unused2 = -1;
       for (int p = pa + threadIdx.x; p < pe; p += blockDim.x) {
         const int j = A.colind[p];
         for (int q = B.rowptr[j]; q < B.rowptr[j + 1]; ++q) {
-          const long long o = (long long)B.colind[q] - c0;
+          const int c = B.colind[q];
+          const long long o = (long long)c - c0;
           if (o >= 0 && o < kNaChunkBits) atomicOr(&bits[o >> 5], 1u << (o & 31));
+          else if (o >= kNaChunkBits) next = min(next, c);
         }
       }
       __syncthreads();
@@ -118,6 +140,8 @@ k_na_count(CsrView A, CsrView B, int32_t* __restrict__ counts, int* __restrict__
       __syncthreads();
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += red_c[w];
       __syncthreads();
+      na_block_minmax(red_lo, red_hi, next, unused2);
+      c0 = next;
     }
     if (threadIdx.x == 0) counts[i] = total;
   }

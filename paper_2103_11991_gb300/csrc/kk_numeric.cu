@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kTeamBlock) k_num_team(NumArgs g) {
     }
     __syncwarp(mask);
     const int pa = g.A.rowptr[i], pe = g.A.rowptr[i + 1];
-    const bool df = df_all && row_df_ok<TEAM>(g.A.vals, pa, pe, tl, mask);
+    const bool df = df_all && df_row_terms_ok(pa, pe) && row_df_ok<TEAM>(g.A.vals, pa, pe, tl, mask);
     if (df) {
       visit_products<TEAM, FLAT, DF>(pa, pe, 0, 1, tl, mask, rng, PrepDF{g.A.vals},
                                      [&](DF a, int, int q) {
@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(256, 3) k_num_warp_vec(NumArgs g) {
     for (int s = lane * 4; s < S; s += 128) *reinterpret_cast<int4*>(&keys[s]) = make_int4(-1, -1, -1, -1);
     __syncwarp();
     const int pa = g.A.rowptr[i], pe = g.A.rowptr[i + 1];
-    bool df = df_all;
-    if (df_all && pe - pa > 32) {
+    bool df = df_all && df_row_terms_ok(pa, pe);
+    if (df && pe - pa > 32) {
       // multi-chunk row: check the whole row against the DF32 window first
       int bad = 0;
       for (int p = pa + lane; p < pe; p += 32) {
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kCtaBlock) k_num_cta(NumArgs g) {
       vals[s] = 0ull;
     }
     const int pa = g.A.rowptr[i], pe = g.A.rowptr[i + 1];
-    const bool df = df_all && block_df_ok(g.A.vals, pa, pe, &flag);  // contains __syncthreads
+    const bool df = df_all && df_row_terms_ok(pa, pe) && block_df_ok(g.A.vals, pa, pe, &flag);  // syncs
     if (df) {
       visit_products<32, true, DF>(pa, pe, warp, nwarps, lane, 0xffffffffu, rng, PrepDF{g.A.vals},
                                    [&](DF a, int, int q) {
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kDenseBlock) k_num_dense(NumArgs g) {
     const int64_t off = g.c_rowptr[i];
     const int64_t cnt = g.c_rowptr[i + 1] - off;
     const int pa = g.A.rowptr[i], pe = g.A.rowptr[i + 1];
-    const bool df = df_all && block_df_ok(g.A.vals, pa, pe, &flag);
+    const bool df = df_all && df_row_terms_ok(pa, pe) && block_df_ok(g.A.vals, pa, pe, &flag);
     int64_t run = 0;
     for (long long c0l = 0; c0l < k; c0l += W) {
       const int c0 = (int)c0l;

@@ -119,17 +119,25 @@ __device__ __forceinline__ void bc_set_bits(uint32_t* bits, uint32_t* sum, int l
           v[u] = make_int2(0, 0);
           if (t < nch && e < ys) v[u] = bc[xs + e];
         }
+        // the pairs' ORs are issued together; a lane whose OR found its word
+        // empty then sets the word's summary bit (one summary update per
+        // non-empty word instead of one per pair: fewer atomics, and fewer
+        // lanes of one instruction on the same summary word)
+        uint32_t old[SETB];
 #pragma unroll
         for (int u = 0; u < SETB; ++u) {
+          old[u] = ~0u;
           if (v[u].y != 0) {
             const uint32_t w = (uint32_t)(v[u].x - lo_w);
-            if (w < (uint32_t)WORDS) {
-              // no returned value to wait for: the summary bit is set every time
-              atomicOr(&bits[w], (uint32_t)v[u].y);
-              atomicOr(&sum[w >> 5], 1u << (w & 31));
-            } else {
-              bad = 1;
-            }
+            if (w < (uint32_t)WORDS) old[u] = atomicOr(&bits[w], (uint32_t)v[u].y);
+            else bad = 1;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < SETB; ++u) {
+          if (old[u] == 0u) {
+            const uint32_t w = (uint32_t)(v[u].x - lo_w);
+            atomicOr(&sum[w >> 5], 1u << (w & 31));
           }
         }
       }
@@ -433,8 +441,9 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
     __syncwarp();
     // arithmetic of this row: DF32 unless a value of the row is outside its
     // window (rows of up to 32 entries decide from the split below)
-    bool df = df_all;
-    if (df_all && pe - pa > 32) df = row_df_ok<32>(aval, pa, pe, lane, kFull);
+    const bool df_row = df_all && df_row_terms_ok(pa, pe);
+    bool df = df_row;
+    if (df_row && pe - pa > 32) df = row_df_ok<32>(aval, pa, pe, lane, kFull);
     int missing = 0;
     for (int p0 = pa; p0 < pe; p0 += 32) {
       const int p = p0 + lane;
@@ -447,8 +456,8 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
         a = aval[p];
       }
       DF ad;
-      const int split_bad = df_all ? (df_split(a, ad) ? 0 : 1) : 1;
-      if (df_all && pe - pa <= 32) df = __any_sync(kFull, split_bad) == 0;
+      const int split_bad = df_row ? (df_split(a, ad) ? 0 : 1) : 1;
+      if (df_row && pe - pa <= 32) df = __any_sync(kFull, split_bad) == 0;
       if (df) {
         info.z = __float_as_int(ad.hi);
         info.w = __float_as_int(ad.lo);
@@ -797,7 +806,7 @@ k_num_window_cta(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ 
     if (tid == 0 && total != cnt) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
     __syncthreads();
     // arithmetic of this row: DF32 unless one of its A values is outside the window
-    const bool df = df_all && row_df_ok<32>(aval, pa, pe, lane, kFull);
+    const bool df = df_all && df_row_terms_ok(pa, pe) && row_df_ok<32>(aval, pa, pe, lane, kFull);
     int missing = 0;
     if (df)
       window_values<WORDS, VMAX>(p_lo, p_hi, true, acol, aval, B.rowptr, B.colind, bspl, B.vals, bits, pre,

@@ -261,7 +261,7 @@ def kk_spgemm_stats(h) -> dict:
             "sym_window_rows", "num_window_rows", "onepass_rows", "overflow_rows", "heavy_rows",
             "staging_entries", "num_team_c", "num_cta_c", "num_dense_c", "num_window_c",
             "num_team_a", "num_cta_a", "num_dense_a", "num_window_a", "kept_structure_rows",
-            "compressed_b_pairs"]
+            "compressed_b_pairs", "num_team_f", "num_cta_f", "num_dense_f", "num_window_f"]
     return {k: int(arr[i]) for i, k in enumerate(keys)}
 
 

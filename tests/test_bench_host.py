@@ -27,8 +27,16 @@ def _copy_record(tmp_path):
     shutil.copy(os.path.join(root, "profiles", "ncu_traffic.json"), tmp_path / "profiles")
     src = tmp_path / "paper_2103_11991_gb300" / "csrc"
     src.mkdir(parents=True)
+    import hashlib
+    h = hashlib.sha256()
     for name in rec["sources"]:
         shutil.copy(os.path.join(root, "paper_2103_11991_gb300", "csrc", name), src / name)
+        h.update((src / name).read_bytes())
+    # the copy's record matches the copied sources, whether or not the
+    # committed record is current
+    rec["source_sha256"] = h.hexdigest()
+    with open(tmp_path / "profiles" / "ncu_traffic.json", "w") as f:
+        json.dump(rec, f)
     return rec, src
 
 

@@ -101,6 +101,39 @@ def test_rmat20_full_sampled():
     torch.cuda.empty_cache()
 
 
+def test_rmat20_learned_full_sampled():
+    """The learned form on its own workload (R-MAT scale 20) at full size, in
+    the configuration the bench times (predictor trained on the training
+    families, quantile 0.95): row pointers identical to the plain symbolic
+    phase's, the same count bounds, and the heaviest rows, a middle block and
+    the last rows against the oracle."""
+    import torch
+    from paper_2103_11991_gb300 import learned as L
+    from paper_2103_11991_gb300 import spgemm as K
+    X, y = L.make_training_set(L.training_pairs(small=True))
+    params, _ = L.train_predictor(X, y, epochs=30)
+    del X, y
+    A = I.config_inputs("rmat20")["A"]
+    dA = K.DeviceCSR.from_host(A)
+    with K.SpGEMM() as op:
+        rp_plain, nnz_plain = op.symbolic(dA, dA)
+        rp_plain = rp_plain.cpu().numpy()
+    with K.SpGEMM() as op:
+        op.set_predictor(params, 0.95)
+        rp, nnz = op.learned_symbolic(dA, dA)
+        ci, va = op.learned_numeric(dA, dA, rp, nnz)
+        op.sync()
+        st = op.stats()
+        assert nnz == nnz_plain
+        assert np.array_equal(rp.cpu().numpy(), rp_plain)
+        assert st["onepass_rows"] > 0
+        cnt = np.diff(rp_plain)
+        assert np.all(cnt <= np.minimum(oracle.row_flops(A, A), A.n))
+        _check_blocks(A, A, rp, ci, va, [(0, 48), (400_000, 402_000), (A.m - 2000, A.m)])
+        del ci, va
+    torch.cuda.empty_cache()
+
+
 @pytest.fixture(scope="module")
 def batch2000():
     return I.config_inputs("batch2000")["pairs"]

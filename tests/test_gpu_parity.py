@@ -237,3 +237,57 @@ def test_copy_to_host_kernel():
     with pytest.raises(K.KKError) as e:  # pageable destination
         K.kk_copy_to_host(torch.empty(1001, dtype=torch.int32), src32)
     assert e.value.status == 1
+
+
+def _long_short_rows(seed):
+    """A with 48 rows of 200-300 entries and 48 rows of 10-60 entries; B rows
+    (k = 256 columns, so every C row fits the window tier's value array) all
+    hold columns 0..7, so those entries of a long row get more than 200
+    contributions each."""
+    long_a = I.random_rows(48, 2000, 200, 300, seed=seed)
+    short_a = I.random_rows(48, 2000, 10, 60, seed=seed + 1)
+    rp = np.concatenate([long_a.rowptr, long_a.rowptr[-1] + short_a.rowptr[1:]])
+    ci = np.concatenate([long_a.colind, short_a.colind])
+    A = I.CSR(96, 2000, rp.astype(np.int64), ci, I.uniform01(seed, "long.a", len(ci)) * 2 - 1)
+    Br = I.random_rows(2000, 248, 10, 30, seed=seed + 2)
+    rows, cols = [], []
+    for j in range(2000):
+        c = np.concatenate([np.arange(8), 8 + Br.colind[Br.rowptr[j]:Br.rowptr[j + 1]]])
+        rows.append(np.full(len(c), j))
+        cols.append(c)
+    rows, cols = np.concatenate(rows), np.concatenate(cols)
+    brp = np.zeros(2001, dtype=np.int64)
+    np.add.at(brp, rows + 1, 1)
+    B = I.CSR(2000, 256, np.cumsum(brp), cols, I.uniform01(seed, "long.b", len(cols)) * 2 - 1)
+    return A, B
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_df32_rows_beyond_its_bound_run_in_float64(seed):
+    """DF32's error bound (n + 2) * 2^-46 * sum|a||b| is under 1e-12 only up to
+    68 contributions per entry: rows of more than 64 A entries must run in
+    float64.  The window tier adds in A-row order, so a float64 row matches the
+    oracle bit for bit, which a DF32 row of random values does not; the short
+    rows still run in DF32 (the handle reports DF32) within the bound."""
+    A, B = _long_short_rows(40 + seed)
+    rp, ci, va, arith, st = run_gpu(A, B, arith=2, force_tier=3)
+    assert arith == 2
+    assert st["num_window_rows"] == A.m
+    ref = check_against_oracle(A, B, rp, ci, va)
+    long_end = int(ref.rowptr[48])
+    assert np.array_equal(va[:long_end], ref.vals[:long_end]), "long rows did not run in float64"
+    assert not np.array_equal(va[long_end:], ref.vals[long_end:]), "short rows did not run in DF32"
+    # every tier keeps the bound on the same product
+    for tier in (-1, 0, 1):
+        rp, ci, va, _, _ = run_gpu(A, B, arith=2, force_tier=tier)
+        check_against_oracle(A, B, rp, ci, va)
+
+
+def test_df32_needs_strictly_ascending_b():
+    """With a repeated column in a B row an entry can get more contributions
+    than A(i,:) has entries, so the whole product runs in float64."""
+    A = I.random_sparse(120, 90, 0.1, 11)
+    B = I.random_sparse(90, 130, 0.1, 12, duplicates=True)
+    rp, ci, va, arith, _ = run_gpu(A, B, arith=2)
+    assert arith == 1
+    check_against_oracle(A, B, rp, ci, va)
