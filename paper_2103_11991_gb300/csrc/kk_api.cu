@@ -819,7 +819,7 @@ struct kk_spgemm_handle_s {
   int64_t stats[32] = {0};
   int32_t last_arith = kArithDF32;
   // compressed B (window tier) and the arrays it was built from
-  DevBuf d_bc;         // int2[nnzB]
+  DevBuf d_bc;         // int2[nnzB + 2] (the padding lets 16-byte loads of pairs end past the last row)
   DevBuf d_bclen;      // int32[B.m]
   bool bc_valid = false;
   const void* bc_key[2] = {nullptr, nullptr};
@@ -1002,7 +1002,7 @@ kk_status analyze_b(kk_spgemm_handle h, const CsrView& bv) {
   int2* bc = nullptr;
   int32_t* len = nullptr;
   if (h->opt.use_window) {
-    KK_CUDA(h, h->d_bc.ensure(sizeof(int2) * (size_t)(bv.nnz > 0 ? bv.nnz : 1)), "alloc compressed B");
+    KK_CUDA(h, h->d_bc.ensure(sizeof(int2) * ((size_t)bv.nnz + 2)), "alloc compressed B");
     KK_CUDA(h, h->d_bclen.ensure(sizeof(int32_t) * (size_t)bv.m), "alloc compressed B");
     bc = h->d_bc.as<int2>();
     len = h->d_bclen.as<int32_t>();
@@ -1034,7 +1034,7 @@ kk_status ensure_bcomp(kk_spgemm_handle h, const CsrView& bv, BComp* out, int* b
                     h->bc_m == bv.m && h->bc_nnz == bv.nnz;
   if (!same) {
     h->bc_valid = false;
-    KK_CUDA(h, h->d_bc.ensure(sizeof(int2) * (size_t)(bv.nnz > 0 ? bv.nnz : 1)), "alloc compressed B");
+    KK_CUDA(h, h->d_bc.ensure(sizeof(int2) * ((size_t)bv.nnz + 2)), "alloc compressed B");
     KK_CUDA(h, h->d_bclen.ensure(sizeof(int32_t) * (size_t)bv.m), "alloc compressed B");
     // sortedness is not re-decided here: the flag goes to a scratch word
     KK_CUDA(h, launch_analyze_b(ctx_of(h), bv, &h->d_misc.as<Misc>()->pad, h->d_bc.as<int2>(),

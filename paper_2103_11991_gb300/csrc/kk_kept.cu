@@ -134,8 +134,16 @@ cudaError_t launch_num_kept(const LaunchCtx& ctx, const CsrView& A, const CsrVie
   auto kern = check ? k_num_kept<true> : k_num_kept<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  long long blocks = (nrows + kKeptWarps * 4 - 1) / (kKeptWarps * 4);
-  const long long capb = (long long)ctx.num_sms * 16;
+  // one resident wave: the rows in flight form one contiguous band, so the B
+  // rows they share stay in L2 (a grid of several waves runs bands far apart)
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kKeptWarps * 32, smem) != cudaSuccess ||
+      per_sm < 1) {
+    (void)cudaGetLastError();
+    per_sm = 1;
+  }
+  long long blocks = (nrows + kKeptWarps - 1) / kKeptWarps;
+  const long long capb = (long long)ctx.num_sms * per_sm;
   if (blocks > capb) blocks = capb;
   if (blocks < 1) blocks = 1;
   kern<<<(int)blocks, kKeptWarps * 32, smem, ctx.stream>>>(

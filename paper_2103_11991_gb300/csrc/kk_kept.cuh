@@ -80,21 +80,25 @@ __device__ __forceinline__ void kept_batch(const int4* ainfo, int t0, int lo_c, 
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
     const int2 az = *reinterpret_cast<const int2*>(&ainfo[t0 + u].z);
-    if (DFM) {
-      DF a, b;
-      a.hi = __int_as_float(az.x);
-      a.lo = __int_as_float(az.y);
-      b.hi = bv[u].x;
-      b.lo = bv[u].y;
-      DF s = df_unpack(vacc[rk[u]]);
-      df_fma(s, a, b);
-      vacc[rk[u]] = df_pack(s);
-    } else {
-      const double x = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
-      const double y = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
-                                            (unsigned)__float_as_int(bv[u].x));
-      double* v = reinterpret_cast<double*>(&vacc[rk[u]]);
-      *v = fma(x, y, *v);
+    // lanes without a product (or with a column outside the kept structure)
+    // skip the update and its shared-memory traffic
+    if (rk[u] < kWindowMaxNnz) {
+      if (DFM) {
+        DF a, b;
+        a.hi = __int_as_float(az.x);
+        a.lo = __int_as_float(az.y);
+        b.hi = bv[u].x;
+        b.lo = bv[u].y;
+        DF s = df_unpack(vacc[rk[u]]);
+        df_fma(s, a, b);
+        vacc[rk[u]] = df_pack(s);
+      } else {
+        const double x = __longlong_as_double(((long long)az.y << 32) | (unsigned)az.x);
+        const double y = __longlong_as_double(((long long)__float_as_int(bv[u].y) << 32) |
+                                              (unsigned)__float_as_int(bv[u].x));
+        double* v = reinterpret_cast<double*>(&vacc[rk[u]]);
+        *v = fma(x, y, *v);
+      }
     }
     __syncwarp();  // this A entry's updates are visible before the next one's
   }
@@ -135,20 +139,22 @@ __device__ __forceinline__ void kept_chunk_long(const int4* ainfo, int nch, int 
       const bool ok = q0 + lane < in.y;
       const int c = ok ? bcol[q] : 0;
       const int rank = kept_rank<PROBE, CHECK>(table, (uint32_t)(c - lo_c), ok, missing);
-      if (DFM) {
-        DF a, b;
-        a.hi = __int_as_float(in.z);
-        a.lo = __int_as_float(in.w);
-        const float2 bb = ok ? bspl[q] : make_float2(0.f, 0.f);
-        b.hi = bb.x;
-        b.lo = bb.y;
-        DF s = df_unpack(vacc[rank]);
-        df_fma(s, a, b);
-        vacc[rank] = df_pack(s);
-      } else {
-        const double x = __longlong_as_double(((long long)in.w << 32) | (unsigned)in.z);
-        double* v = reinterpret_cast<double*>(&vacc[rank]);
-        *v = fma(x, ok ? bval[q] : 0.0, *v);
+      if (rank < kWindowMaxNnz) {
+        if (DFM) {
+          DF a, b;
+          a.hi = __int_as_float(in.z);
+          a.lo = __int_as_float(in.w);
+          const float2 bb = bspl[q];
+          b.hi = bb.x;
+          b.lo = bb.y;
+          DF s = df_unpack(vacc[rank]);
+          df_fma(s, a, b);
+          vacc[rank] = df_pack(s);
+        } else {
+          const double x = __longlong_as_double(((long long)in.w << 32) | (unsigned)in.z);
+          double* v = reinterpret_cast<double*>(&vacc[rank]);
+          *v = fma(x, bval[q], *v);
+        }
       }
       __syncwarp();
     }

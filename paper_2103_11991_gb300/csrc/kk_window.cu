@@ -47,11 +47,11 @@ struct WinWords {
 template <int W>
 struct SymWinGeom : WinWords<W> {
   using WinWords<W>::WORDS;
-  using WinWords<W>::SUMS;
-  // bits u32[WORDS] | sum u32[SUMS] | list u16[kCacheWords]
-  static constexpr size_t kSumOff = al16((size_t)WORDS * 4);
-  static constexpr size_t kListOff = al16(kSumOff + (size_t)SUMS * 4);
-  static constexpr size_t kWarpBytes = al16(kListOff + (size_t)kCacheWords * 2);
+  // one mark byte per group of 32 words
+  static constexpr int GROUPS = (WORDS + 31) / 32;
+  // bits u32[WORDS] | gmark u8[GROUPS]
+  static constexpr size_t kMarkOff = al16((size_t)WORDS * 4);
+  static constexpr size_t kWarpBytes = al16(kMarkOff + (size_t)GROUPS);
 };
 
 template <int W, int VMAX = kWindowMaxNnz>
@@ -119,25 +119,17 @@ __device__ __forceinline__ void bc_set_bits(uint32_t* bits, uint32_t* sum, int l
           v[u] = make_int2(0, 0);
           if (t < nch && e < ys) v[u] = bc[xs + e];
         }
-        // the pairs' ORs are issued together; a lane whose OR found its word
-        // empty then sets the word's summary bit (one summary update per
-        // non-empty word instead of one per pair: fewer atomics, and fewer
-        // lanes of one instruction on the same summary word)
-        uint32_t old[SETB];
 #pragma unroll
         for (int u = 0; u < SETB; ++u) {
-          old[u] = ~0u;
           if (v[u].y != 0) {
             const uint32_t w = (uint32_t)(v[u].x - lo_w);
-            if (w < (uint32_t)WORDS) old[u] = atomicOr(&bits[w], (uint32_t)v[u].y);
-            else bad = 1;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < SETB; ++u) {
-          if (old[u] == 0u) {
-            const uint32_t w = (uint32_t)(v[u].x - lo_w);
-            atomicOr(&sum[w >> 5], 1u << (w & 31));
+            if (w < (uint32_t)WORDS) {
+              // no returned value to wait for: the summary bit is set every time
+              atomicOr(&bits[w], (uint32_t)v[u].y);
+              atomicOr(&sum[w >> 5], 1u << (w & 31));
+            } else {
+              bad = 1;
+            }
           }
         }
       }
@@ -156,6 +148,81 @@ __device__ __forceinline__ void bc_set_bits(uint32_t* bits, uint32_t* sum, int l
           } else {
             bad = 1;
           }
+        }
+      }
+    }
+  }
+  if (bad) set_status(status, KK_ERR_CAPACITY);
+  __syncwarp();
+}
+
+// The symbolic kernel's OR of the compressed rows B_C(j,:) of A entries
+// [pa, pe) into the window (word 0 = column word lo_w), with a mark byte per
+// group of 32 words (plain stores: lanes that mark the same group write the
+// same value).  Pairs are loaded 16 bytes (two pairs) at a time from the even
+// pair index at or below the row's start (the compressed B is padded so the
+// last load stays inside it), by a team of G lanes per entry with 2G covering
+// the chunk's longest row span: one load instruction then fetches all of an
+// entry's pairs, so it touches each entry's cache line once (the kernel was
+// bound by L1 tag lookups of narrower loads that revisited the same lines).
+// Two steps' loads are in flight.  Rows spanning more than 64 pairs are walked
+// an entry at a time.  x0 / y0: the lane's bounds for the first chunk.
+template <int WORDS>
+__device__ __forceinline__ void or_pair(uint32_t* bits, uint8_t* gmark, int lo_w, int wc, uint32_t m,
+                                        int& bad) {
+  const uint32_t w = (uint32_t)(wc - lo_w);
+  if (w < (uint32_t)WORDS) {
+    atomicOr(&bits[w], m);
+    gmark[w >> 5] = 1;
+  } else {
+    bad = 1;
+  }
+}
+
+template <int WORDS>
+__device__ __forceinline__ void bc_or_marked(uint32_t* bits, uint8_t* gmark, int lo_w, int pa, int pe,
+                                             const int32_t* __restrict__ acol,
+                                             const int32_t* __restrict__ brp,
+                                             const int2* __restrict__ bc,
+                                             const int32_t* __restrict__ bclen, int lane, int* status,
+                                             int x0, int y0) {
+  int bad = 0;
+  const int4* __restrict__ bc4 = reinterpret_cast<const int4*>(bc);
+  for (int p0 = pa; p0 < pe; p0 += 32) {
+    int x = x0, y = y0;
+    if (p0 != pa) bc_bounds(p0 + lane, pe, acol, brp, bclen, x, y);
+    const int nch = min(32, pe - p0);
+    // pairs to fetch from the even index below the row's start
+    const unsigned span = y > 0 ? (unsigned)((x & 1) + y) : 0u;
+    const unsigned maxspan = __reduce_max_sync(kFull, span);
+    if (maxspan <= 64u) {
+      const int lg = maxspan <= 2u ? 0 : maxspan <= 4u ? 1 : maxspan <= 8u ? 2 : maxspan <= 16u ? 3
+                   : maxspan <= 32u ? 4 : 5;
+      const int E = 32 >> lg;
+      const int sub = lane >> lg, e2 = 2 * (lane & ((1 << lg) - 1));
+      for (int t0 = 0; t0 < nch; t0 += 2 * E) {
+        const int ta = t0 + sub, tb = t0 + E + sub;
+        const int xa = __shfl_sync(kFull, x, ta & 31), ya = __shfl_sync(kFull, y, ta & 31);
+        const int xb = __shfl_sync(kFull, x, tb & 31), yb = __shfl_sync(kFull, y, tb & 31);
+        // pair indices [qa, qa + 2) of the row's [xa, xa + ya)
+        const int qa = (xa & ~1) + e2, qb = (xb & ~1) + e2;
+        const bool la = ta < nch && qa + 1 >= xa && qa < xa + ya;
+        const bool lb = tb < nch && qb + 1 >= xb && qb < xb + yb;
+        int4 va = make_int4(0, 0, 0, 0), vb = make_int4(0, 0, 0, 0);
+        if (la) va = bc4[qa >> 1];
+        if (lb) vb = bc4[qb >> 1];
+        if (la && qa >= xa) or_pair<WORDS>(bits, gmark, lo_w, va.x, (uint32_t)va.y, bad);
+        if (la && qa + 1 < xa + ya) or_pair<WORDS>(bits, gmark, lo_w, va.z, (uint32_t)va.w, bad);
+        if (lb && qb >= xb) or_pair<WORDS>(bits, gmark, lo_w, vb.x, (uint32_t)vb.y, bad);
+        if (lb && qb + 1 < xb + yb) or_pair<WORDS>(bits, gmark, lo_w, vb.z, (uint32_t)vb.w, bad);
+      }
+    } else {
+      for (int t = 0; t < nch; ++t) {
+        const int xs = __shfl_sync(kFull, x, t);
+        const int ys = __shfl_sync(kFull, y, t);
+        for (int e = lane; e < ys; e += 32) {
+          const int2 v = bc[xs + e];
+          or_pair<WORDS>(bits, gmark, lo_w, v.x, (uint32_t)v.y, bad);
         }
       }
     }
@@ -210,17 +277,16 @@ k_sym_window(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ row_
              WinCache cache, int* status) {
   using G = SymWinGeom<W>;
   constexpr int WORDS = G::WORDS;
-  constexpr int SUMS = G::SUMS;
+  constexpr int GROUPS = G::GROUPS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* base = smem_raw + (size_t)warp * G::kWarpBytes;
   uint32_t* bits = reinterpret_cast<uint32_t*>(base);
-  uint32_t* sum = reinterpret_cast<uint32_t*>(base + G::kSumOff);
-  uint16_t* list = reinterpret_cast<uint16_t*>(base + G::kListOff);
+  uint8_t* gmark = base + G::kMarkOff;
   // whole window cleared once; afterwards each row clears what it set
   for (int w = lane * 4; w < WORDS; w += 128)
     *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
-  for (int w = lane; w < SUMS; w += 32) sum[w] = 0u;
+  for (int g = lane; g < GROUPS; g += 32) gmark[g] = 0;
   __syncwarp();
   // Rows are dealt to warps round-robin over the whole grid, so the rows in
   // flight at any time are neighbours and the B rows they share stay in L2.
@@ -249,37 +315,47 @@ k_sym_window(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ row_
       lo_n = row_lo[i_n];
     }
     const int i_nn = r + 2 * nw < r_end ? rows[r + 2 * nw] : -1;
-    bc_set_bits<WORDS, true>(bits, sum, lo >> 5, pa, pe, A.colind, B.rowptr, bcomp.bc, bcomp.len,
-                             lane, status, x, y);
+    bc_or_marked<WORDS>(bits, gmark, lo >> 5, pa, pe, A.colind, B.rowptr, bcomp.bc, bcomp.len, lane, status,
+                        x, y);
     int j_n = -1;
     if (i_n >= 0 && pa_n + lane < pe_n) j_n = A.colind[pa_n + lane];
-    const int L = window_list<SUMS>(sum, list, kCacheWords, lane);
+    // The marked groups of 32 words in order: a lane per word of the group
+    // finds the non-empty ones (ballot), counts their columns, clears them and
+    // stores the word and its bits as the row's kept structure (in order).
+    int c = 0, L = 0;
+    {
+      const unsigned below = (1u << lane) - 1u;
+      uint16_t* cw = cache.w ? cache.w + (size_t)i * kCacheWords : nullptr;
+      uint32_t* cm = cache.w ? cache.m + (size_t)i * kCacheWords : nullptr;
+#pragma unroll
+      for (int g0 = 0; g0 < GROUPS; g0 += 32) {
+        const int g = g0 + lane;
+        const bool mk = g < GROUPS && gmark[g] != 0;
+        unsigned gm = __ballot_sync(kFull, mk);
+        if (mk) gmark[g] = 0;
+        while (gm) {
+          const int gb = __ffs(gm) - 1;
+          gm &= gm - 1;
+          const int w = (g0 + gb) * 32 + lane;
+          const uint32_t m = w < WORDS ? bits[w] : 0u;
+          const unsigned nz = __ballot_sync(kFull, m != 0u);
+          const int pos = L + __popc(nz & below);
+          if (m != 0u) {
+            bits[w] = 0u;
+            c += __popc(m);
+            if (cw && pos < kCacheWords) {
+              cw[pos] = (uint16_t)w;
+              cm[pos] = m;
+            }
+          }
+          L += __popc(nz);
+        }
+      }
+    }
     int x_n = 0, y_n = 0;
     if (j_n >= 0) {
       x_n = B.rowptr[j_n];
       y_n = bcomp.len[j_n];
-    }
-    int c = 0;
-    if (L <= kCacheWords) {
-      // whole 32-entry rounds are written (zeros past L) so the kept structure
-      // is stored in full 32-byte sectors, not merged into partial ones
-      const int Lr = (L + 31) & ~31;
-      for (int e = lane; e < Lr; e += 32) {
-        int w = 0;
-        uint32_t m = 0u;
-        if (e < L) {
-          w = list[e];
-          m = bits[w];
-          bits[w] = 0u;
-        }
-        c += __popc(m);
-        if (cache.w) {
-          cache.w[(size_t)i * kCacheWords + e] = (uint16_t)w;
-          cache.m[(size_t)i * kCacheWords + e] = m;
-        }
-      }
-    } else {
-      c = window_count_clear<WORDS>(bits, lane);
     }
     c = team_sum<32>(c, kFull);
     if (lane == 0) {
@@ -845,6 +921,25 @@ int grid_for_rows(const LaunchCtx& ctx, int nrows) {
   return (int)blocks;
 }
 
+// One resident wave of a row-striding kernel: the SMs' count times the CTAs
+// of `kern` an SM holds at once (never more than the rows need).  With every
+// CTA resident, the rows in flight are one contiguous band that advances
+// through the matrix, so the B rows they share stay in L2; a grid of several
+// waves would run bands far apart in the matrix at once.
+template <class K>
+int resident_grid(const LaunchCtx& ctx, K kern, int threads, size_t smem, int nrows, int rows_per_cta) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1) {
+    (void)cudaGetLastError();
+    per_sm = 1;
+  }
+  long long blocks = (nrows + rows_per_cta - 1) / rows_per_cta;
+  const long long cap = (long long)ctx.num_sms * per_sm;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
 template <int W>
 cudaError_t sym_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B, const BComp& bcomp,
                        const int32_t* rows, int32_t nrows, int32_t* cnt, const WinCache& cache) {
@@ -852,7 +947,7 @@ cudaError_t sym_window(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
   auto kern = k_sym_window<W>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid_for_rows(ctx, nrows), kWinWarps * 32, smem, ctx.stream>>>(
+  kern<<<resident_grid(ctx, kern, kWinWarps * 32, smem, nrows, kWinWarps), kWinWarps * 32, smem, ctx.stream>>>(
       A, B, bcomp, ctx.row_lo, rows, nrows, cnt, cache, ctx.status);
   return cudaGetLastError();
 }
