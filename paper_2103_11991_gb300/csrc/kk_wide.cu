@@ -201,13 +201,113 @@ __device__ __forceinline__ void wide_walk(const CsrView& A, const CsrView& B, in
   }
 }
 
+// Walk for rows whose B rows are long (mean length >= kLongMean): work items
+// are the row's A entries cut into pieces of at most kPiece products; a warp
+// claims an item from a shared counter, finds its entry by a 32-ary search over
+// the item prefix (once per item, not per product) and its lanes stride the
+// piece's B entries, kWideU loads in flight.  Same contract as wide_walk.
+constexpr int kPiece = 2048;
+constexpr long long kLongMean = 64;
+struct LongSmem {
+  int ipre[kSeg + 1];
+  int bst[kSeg];
+  int blen[kSeg];
+  int tmp[33];
+  int next;
+};
+
+template <bool VALS, class Use>
+__device__ __forceinline__ void wide_walk_long(const CsrView& A, const CsrView& B, int pa, int pe,
+                                               LongSmem& ls, int& bad, Use use) {
+  const int lane = threadIdx.x & 31;
+  const int32_t* __restrict__ bcol = B.colind;
+  const double* __restrict__ bval = B.vals;
+  for (int s0 = pa; s0 < pe; s0 += kSeg) {
+    const int ns = min(kSeg, pe - s0);
+    {
+      const int t = threadIdx.x;
+      int bs = 0, len = 0;
+      if (t < ns) {
+        const int j = A.colind[s0 + t];
+        if ((unsigned)j < (unsigned)B.m) {
+          bs = B.rowptr[j];
+          len = B.rowptr[j + 1] - bs;
+        } else {
+          bad = 1;
+        }
+      }
+      int total;
+      const int ex = block_exscan<int>((len + kPiece - 1) / kPiece, ls.tmp, &total);
+      ls.ipre[t] = ex;
+      ls.bst[t] = bs;
+      ls.blen[t] = len;
+      if (t == 0) {
+        ls.ipre[ns] = total;
+        ls.next = 0;
+      }
+      __syncthreads();
+    }
+    const int nitems = ls.ipre[ns];
+    for (;;) {
+      int it = 0;
+      if (lane == 0) it = atomicAdd(&ls.next, 1);
+      it = __shfl_sync(kFull, it, 0);
+      if (it >= nitems) break;
+      // entry of item it: last t with ipre[t] <= it (32-ary search)
+      int lo = 0, hi = ns;
+      while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int cand = lo + lane * step;
+        const bool le = cand < hi && ls.ipre[cand] <= it;
+        const unsigned m = __ballot_sync(kFull, le);
+        const int last = 31 - __clz(m);
+        lo = lo + last * step;
+        hi = min(hi, lo + step);
+      }
+      const int t = lo;
+      const int piece = it - ls.ipre[t];
+      const int q0 = ls.bst[t] + piece * kPiece;
+      const int n = min(kPiece, ls.blen[t] - piece * kPiece);
+      const double a = VALS ? A.vals[s0 + t] : 0.0;
+      for (int g = 0; g < n; g += 32 * kWideU) {
+        int col[kWideU];
+        double ab[kWideU];
+#pragma unroll
+        for (int u = 0; u < kWideU; ++u) {
+          const int f = g + u * 32 + lane;
+          col[u] = -1;
+          ab[u] = 0.0;
+          if (f < n) {
+            col[u] = bcol[q0 + f];
+            if (VALS) ab[u] = a * bval[q0 + f];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kWideU; ++u) use(col[u], ab[u]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // OR the column bits of the products of A entries [pa, pe) into bits (and,
 // with SUM, the summary bits of their words).  Ends with a barrier.
+// The two walks' shared state (never used at the same time).
+union WideWalkSmem {
+  WalkSmem ws;
+  LongSmem ls;
+};
+
+// Mean B-row length of row i's A entries decides the walk.
+__device__ __forceinline__ bool wide_long_rows(const long long* flop, int i, int pa, int pe) {
+  return flop != nullptr && pe > pa && flop[i] >= kLongMean * (long long)(pe - pa);
+}
+
 template <bool SUM>
 __device__ __forceinline__ void wide_set_bits(const CsrView& A, const CsrView& B, int pa, int pe,
-                                              WalkSmem& ws, uint32_t* bits, uint32_t* sum,
-                                              int words, int& bad) {
-  wide_walk<false>(A, B, pa, pe, ws, bad, [&](int c, double) {
+                                              bool long_rows, WideWalkSmem& wsm, uint32_t* bits,
+                                              uint32_t* sum, int words, int& bad) {
+  auto set = [&](int c, double) {
     if (c >= 0) {
       if ((unsigned)c < (unsigned)(words * 32)) {
         atomicOr(&bits[c >> 5], 1u << (c & 31));
@@ -216,7 +316,9 @@ __device__ __forceinline__ void wide_set_bits(const CsrView& A, const CsrView& B
         bad = 1;
       }
     }
-  });
+  };
+  if (long_rows) wide_walk_long<false>(A, B, pa, pe, wsm.ls, bad, set);
+  else wide_walk<false>(A, B, pa, pe, wsm.ws, bad, set);
 }
 
 __global__ void __launch_bounds__(kWideBlock, 1)
@@ -226,7 +328,7 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
   extern __shared__ __align__(16) unsigned char wsm[];
   uint32_t* bits = reinterpret_cast<uint32_t*>(wsm);
   uint32_t* sum = reinterpret_cast<uint32_t*>(wsm + sum_off);
-  __shared__ WalkSmem ws;
+  __shared__ WideWalkSmem walk;
   __shared__ int tmp[33];
   __shared__ int s_slot;
   const int nsum = words >> 5;
@@ -238,12 +340,13 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int i = rows[r];
     const bool sparse = flop[i] < (long long)words;  // few words touched: walk the summary
+    const bool lng = wide_long_rows(flop, i, A.rowptr[i], A.rowptr[i + 1]);
     int c = 0;
     if (sparse) {
       // few words touched: count and clear them through the summary (such rows
       // keep nothing: walking their products again costs less than storing
       // and reloading a k-bit vector)
-      wide_set_bits<true>(A, B, A.rowptr[i], A.rowptr[i + 1], ws, bits, sum, words, bad);
+      wide_set_bits<true>(A, B, A.rowptr[i], A.rowptr[i + 1], lng, walk, bits, sum, words, bad);
       for (int s = threadIdx.x; s < nsum; s += blockDim.x) {
         uint32_t m = sum[s];
         sum[s] = 0u;
@@ -259,7 +362,7 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
       block_exscan<int>(c, tmp, &tot);
       if (threadIdx.x == 0) cnt[i] = tot;
     } else {
-      wide_set_bits<false>(A, B, A.rowptr[i], A.rowptr[i + 1], ws, bits, sum, words, bad);
+      wide_set_bits<false>(A, B, A.rowptr[i], A.rowptr[i + 1], lng, walk, bits, sum, words, bad);
       for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4) {
         const uint4 v = *reinterpret_cast<const uint4*>(&bits[w]);
         c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
@@ -294,9 +397,9 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
 
 __global__ void __launch_bounds__(kWideBlock, 1)
 k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, uint32_t reg_off,
-           uint32_t val_off, const int64_t* __restrict__ c_rowptr, const int32_t* __restrict__ rows,
-           int32_t nrows, int32_t* __restrict__ c_colind, double* __restrict__ c_vals, WideKeep keep,
-           int* status) {
+           uint32_t val_off, const int64_t* __restrict__ c_rowptr, const long long* __restrict__ flop,
+           const int32_t* __restrict__ rows, int32_t nrows, int32_t* __restrict__ c_colind,
+           double* __restrict__ c_vals, WideKeep keep, int* status) {
   extern __shared__ __align__(16) unsigned char wsm[];
   uint32_t* bits = reinterpret_cast<uint32_t*>(wsm);
   uint32_t* sum = reinterpret_cast<uint32_t*>(wsm + sum_off);
@@ -305,7 +408,7 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
   uint8_t* wpre8 = wsm + reg_off + (size_t)(words / 8) * 4;       // rows with values in C
   double* vals = reinterpret_cast<double*>(wsm + val_off);
   uint16_t* list = reinterpret_cast<uint16_t*>(wsm + val_off);
-  __shared__ WalkSmem ws;
+  __shared__ WideWalkSmem walk;
   __shared__ int tmp[33];
   const int nsum = words >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -320,12 +423,13 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
     const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
     const int64_t off = c_rowptr[i];
     const int cnt = (int)(c_rowptr[i + 1] - off);
+    const bool lng = wide_long_rows(flop, i, pa, pe);
     // values in shared memory (and the word list in their place) when the row fits
     const bool sparse = cnt <= vcap && cnt <= 65535;
     bool row_bad = false;
     int total;
     if (sparse) {
-      wide_set_bits<true>(A, B, pa, pe, ws, bits, sum, words, bad);
+      wide_set_bits<true>(A, B, pa, pe, lng, walk, bits, sum, words, bad);
       // ordered list of touched words: summary words in order, bits in order,
       // in rounds of blockDim summary words
       int L = 0;
@@ -380,7 +484,7 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
           *reinterpret_cast<uint4*>(&bits[w]) = *reinterpret_cast<const uint4*>(&src[w]);
         __syncthreads();
       } else {
-        wide_set_bits<false>(A, B, pa, pe, ws, bits, sum, words, bad);
+        wide_set_bits<false>(A, B, pa, pe, lng, walk, bits, sum, words, bad);
       }
       // Each warp owns a contiguous range of words, its lanes consecutive
       // words in it (conflict-free shared loads, and consecutive lanes write
@@ -417,7 +521,7 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
     if (row_bad) mismatch = 1;
     __syncthreads();
     // values: rank = prefix of the word + popc(bits below the column)
-    wide_walk<true>(A, B, pa, pe, ws, bad, [&](int c, double ab) {
+    auto add = [&](int c, double ab) {
       if (c >= 0 && (unsigned)c < (unsigned)(words * 32)) {
         const int w = c >> 5;
         const uint32_t word = bits[w];
@@ -432,7 +536,9 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
           else atomicAdd(&c_vals[off + rank], ab);
         }
       }
-    });
+    };
+    if (lng) wide_walk_long<true>(A, B, pa, pe, walk.ls, bad, add);
+    else wide_walk<true>(A, B, pa, pe, walk.ws, bad, add);
     if (sparse) {
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) c_vals[off + e] = vals[e];
     }
@@ -452,7 +558,7 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
 // Dynamic shared memory available to the wide kernels (their static arrays
 // take the rest of the opt-in limit).
 size_t wide_budget(const LaunchCtx& ctx) {
-  const size_t stat = sizeof(WalkSmem) + 33 * sizeof(int) + 512;
+  const size_t stat = sizeof(WideWalkSmem) + 33 * sizeof(int) + 512;
   return (size_t)ctx.max_smem_optin > stat ? (size_t)ctx.max_smem_optin - stat : 0;
 }
 
@@ -508,7 +614,7 @@ cudaError_t launch_numeric_wide(const LaunchCtx& ctx, const CsrView& A, const Cs
   if (e != cudaSuccess) return e;
   k_num_wide<<<wide_grid(ctx, g.bytes, nrows), kWideBlock, g.bytes, ctx.stream>>>(
       A, B, words, g.vcap, (uint32_t)g.sum_off, (uint32_t)g.reg_off, (uint32_t)g.val_off, c_rowptr,
-      rows, nrows, c_colind, c_vals, ctx.keep, ctx.status);
+      ctx.flop, rows, nrows, c_colind, c_vals, ctx.keep, ctx.status);
   return cudaGetLastError();
 }
 
