@@ -288,9 +288,21 @@ def bench_learned(args, dA, dB, madds, plain_ms, ci, va):
 
         plain_r = _events_ms(plain_step, 3, stream)
         op.close()
+        # the same plain step with the wide tier's long B-row pieces staged into
+        # shared memory by bulk copies (options.stage_long_rows)
+        ops = K.SpGEMM(stage_long_rows=1)
+
+        def staged_step():
+            r, n = ops.symbolic(dR, dR)
+            ops.numeric(dR, dR, r, n, cR, vR)
+
+        staged_r = _events_ms(staged_step, 3, stream)
+        ops.close()
         out["rmat20"] = _learned_vs_plain(args, dR, dR, madds_r, plain_r, cR, vR, params,
                                           "rmat20: R-MAT scale 20, edge factor 16, A*A")
         out["rmat20"]["nnz_c"] = int(nnz)
+        out["rmat20"]["plain_bulk_copy_staging"] = {"ms_per_step": staged_r,
+                                                    "value": 2.0 * madds_r / (staged_r * 1e-3) / 1e9}
         del cR, vR, dR
         torch.cuda.empty_cache()
     return out, params

@@ -111,6 +111,11 @@ typedef struct {
                                  the values the speculative pass computed from the values the
                                  symbolic call saw; later numeric calls recompute from the
                                  current values */
+  int32_t stage_long_rows;    /* 1: in the wide tier's symbolic phase, pieces of long B rows
+                                 (>= 512 entries) are copied into shared memory by bulk copies
+                                 (cp.async.bulk, two buffers of 256 columns per warp, mbarrier
+                                 completion) instead of per-lane loads (default 0: on GB300 the
+                                 per-lane loads measured faster, R-MAT scale 20 47 ms against 62) */
 } kk_spgemm_options;
 
 typedef struct kk_spgemm_handle_s* kk_spgemm_handle;

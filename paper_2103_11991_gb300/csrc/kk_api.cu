@@ -990,7 +990,7 @@ BinTable to_table(const std::vector<BinSpec>& bins) {
 LaunchCtx ctx_of(kk_spgemm_handle h) {
   return LaunchCtx{h->stream, h->timer, &h->d_misc.as<Misc>()->status, h->num_sms, h->max_smem,
                    h->d_rowlo.as<int32_t>(), h->d_flop.as<long long>(), h->keep, h->opt.debug_checks,
-                   nullptr};
+                   h->opt.stage_long_rows, nullptr};
 }
 
 // Analysis of B at the start of a symbolic call; with the window tier on, the
@@ -1278,6 +1278,7 @@ kk_status kk_spgemm_options_default(kk_spgemm_options* opt) {
   opt->structure_cache = 1;
   opt->wide_cache_mb = 0;
   opt->batched_mode = 0;
+  opt->stage_long_rows = 0;
   return KK_OK;
 }
 
@@ -1291,7 +1292,7 @@ kk_status kk_spgemm_handle_create(kk_spgemm_handle* out, const kk_spgemm_options
   if (h->opt.arith < 0 || h->opt.arith > 2 || h->opt.force_tier < -1 || h->opt.force_tier > 3 ||
       h->opt.sym_load_pct < 10 || h->opt.sym_load_pct > 100 || h->opt.num_load_pct < 10 ||
       h->opt.num_load_pct > 50 || h->opt.structure_cache < 0 || h->opt.structure_cache > 1 || h->opt.wide_cache_mb < -1 || h->opt.batched_mode < 0 ||
-      h->opt.batched_mode > 2 ||
+      h->opt.batched_mode > 2 || h->opt.stage_long_rows < 0 || h->opt.stage_long_rows > 1 ||
       h->opt.team_vec_min_len < 0) {
     delete h;
     return KK_ERR_INVALID_ARG;

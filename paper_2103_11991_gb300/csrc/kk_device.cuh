@@ -95,6 +95,60 @@ __device__ __forceinline__ int map_slot(int* keys, int32_t key, int log2s, int* 
 }
 
 // ---------------------------------------------------------------------------
+// Bulk copies global -> shared memory (the TMA unit's cp.async.bulk) completed
+// through an mbarrier in this CTA's shared memory.  Source and destination
+// must be 16-byte aligned and the size a multiple of 16 bytes.
+// ---------------------------------------------------------------------------
+constexpr int kMbarSpinLimit = 1 << 22;  // try_wait rounds before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// makes barrier initialisations visible to the copy unit (and to other threads)
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// orders this thread's earlier shared-memory accesses before later bulk copies
+__device__ __forceinline__ void proxy_async_fence() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for the phase `parity` of bar; false (and KK_ERR_TIMEOUT in the
+// status word) if it did not complete within kMbarSpinLimit rounds.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, int* status) {
+  for (int k = 0; k < kMbarSpinLimit; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  set_status(status, KK_ERR_TIMEOUT);
+  return false;
+}
+
+// ---------------------------------------------------------------------------
 // DF32: a float64 value carried as an unevaluated sum hi + lo of two float32s.
 //
 // Valid window: every nonzero input value has a binary exponent e with

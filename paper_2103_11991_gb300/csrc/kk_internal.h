@@ -34,6 +34,7 @@ struct LaunchCtx {
   const long long* flop;  // flop bound of each row (wide tier)
   WideKeep keep;          // kept wide-tier bit vectors (wide tier)
   int debug_checks;       // options.debug_checks
+  int stage_long_rows;    // options.stage_long_rows (wide symbolic: bulk-copy staging)
   // structure fingerprints of the index arrays at the symbolic call ([0]) and
   // at this numeric call ([1]); null when the kept structure is not in use
   const unsigned long long* fingerprint;

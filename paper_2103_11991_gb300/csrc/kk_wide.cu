@@ -201,6 +201,82 @@ __device__ __forceinline__ void wide_walk(const CsrView& A, const CsrView& B, in
   }
 }
 
+// Bulk-copy staging of long B-row pieces (symbolic wide kernel).  Each warp
+// owns two shared-memory buffers of kStageCols columns (+ alignment slack) and
+// an mbarrier per buffer.  A piece of at least 2 * kStageCols products is cut
+// into sub-pieces; lane 0 copies sub-piece k + 2 with cp.async.bulk while the
+// warp ORs sub-piece k from the other buffer, so the row's columns arrive by
+// the copy unit in large transfers instead of per-lane loads.  The copied
+// range is widened to 16-byte boundaries (the copy unit's rule) and clipped to
+// the last 16-byte boundary inside B's columns; anything past it is read with
+// plain loads.
+constexpr int kStageCols = 256;
+constexpr int kStageSlots = kStageCols + 8;  // int32 per buffer: widening slack
+struct StageState {
+  int32_t* buf;               // this warp's two buffers (2 * kStageSlots)
+  unsigned long long* bar;    // this warp's two mbarriers
+  uint32_t phase;             // bit b: parity the next wait on buffer b expects
+  bool ok;                    // false after a wait ran out: plain loads only
+};
+
+// Issue the copy of sub-piece k of the piece [q0, q0 + n) of B's columns into
+// buffer k & 1 (lane 0).
+__device__ __forceinline__ void stage_issue(const CsrView& B, StageState& st, int q0, int n, int k) {
+  const int q = q0 + k * kStageCols;
+  const int e = q + min(kStageCols, n - k * kStageCols);
+  const int a0 = q & ~3;
+  const int ce = min((e + 3) & ~3, B.nnz & ~3);
+  unsigned long long* bar = st.bar + (k & 1);
+  if (ce > a0) {
+    const uint32_t bytes = (uint32_t)(ce - a0) * 4u;
+    proxy_async_fence();  // the warp's reads of this buffer come before the copy's writes
+    mbar_arrive_expect(bar, bytes);
+    bulk_copy_g2s(st.buf + (k & 1) * kStageSlots, B.colind + a0, bytes, bar);
+  } else {
+    mbar_arrive(bar);
+  }
+}
+
+// The columns of the piece [q0, q0 + n) (n >= 2 * kStageCols) through the
+// staging buffers; use(col) per column.  Falls back to plain loads (and
+// disables staging) if a wait runs out.
+template <class Use>
+__device__ __forceinline__ void stage_walk(const CsrView& B, StageState& st, int q0, int n, int* status,
+                                           Use use) {
+  const int lane = threadIdx.x & 31;
+  const int nsub = (n + kStageCols - 1) / kStageCols;
+  if (lane == 0) {
+    stage_issue(B, st, q0, n, 0);
+    stage_issue(B, st, q0, n, 1);
+  }
+  int k = 0;
+  for (; k < nsub; ++k) {
+    const int b = k & 1;
+    const bool got = mbar_wait(st.bar + b, (st.phase >> b) & 1u, status);
+    if (!__all_sync(kFull, got)) {
+      // give the copies in flight a second bounded wait, then go on without them
+      if (lane == 0) {
+        mbar_wait(st.bar + b, (st.phase >> b) & 1u, status);
+        if (k + 1 < nsub) mbar_wait(st.bar + (b ^ 1), (st.phase >> (b ^ 1)) & 1u, status);
+      }
+      __syncwarp();
+      st.ok = false;
+      break;
+    }
+    st.phase ^= 1u << b;
+    const int q = q0 + k * kStageCols;
+    const int e = q + min(kStageCols, n - k * kStageCols);
+    const int a0 = q & ~3;
+    const int ce = min((e + 3) & ~3, B.nnz & ~3);
+    const int32_t* bufb = st.buf + b * kStageSlots;
+    for (int x = q + lane; x < e; x += 32) use(x < ce ? bufb[x - a0] : B.colind[x]);
+    __syncwarp();  // every lane is done with buffer b before it is refilled
+    if (lane == 0 && k + 2 < nsub) stage_issue(B, st, q0, n, k + 2);
+  }
+  for (int x = q0 + k * kStageCols + lane; x < q0 + n; x += 32) use(B.colind[x]);  // after a give-up
+  __syncwarp();
+}
+
 // Walk for rows whose B rows are long (mean length >= kLongMean): work items
 // are the row's A entries cut into pieces of at most kPiece products; a warp
 // claims an item from a shared counter, finds its entry by a 32-ary search over
@@ -218,7 +294,8 @@ struct LongSmem {
 
 template <bool VALS, class Use>
 __device__ __forceinline__ void wide_walk_long(const CsrView& A, const CsrView& B, int pa, int pe,
-                                               LongSmem& ls, int& bad, Use use) {
+                                               LongSmem& ls, int& bad, Use use, StageState* st = nullptr,
+                                               int* status = nullptr) {
   const int lane = threadIdx.x & 31;
   const int32_t* __restrict__ bcol = B.colind;
   const double* __restrict__ bval = B.vals;
@@ -268,6 +345,10 @@ __device__ __forceinline__ void wide_walk_long(const CsrView& A, const CsrView& 
       const int piece = it - ls.ipre[t];
       const int q0 = ls.bst[t] + piece * kPiece;
       const int n = min(kPiece, ls.blen[t] - piece * kPiece);
+      if (!VALS && st != nullptr && st->ok && n >= 2 * kStageCols) {
+        stage_walk(B, *st, q0, n, status, [&](int c) { use(c, 0.0); });
+        continue;
+      }
       const double a = VALS ? A.vals[s0 + t] : 0.0;
       for (int g = 0; g < n; g += 32 * kWideU) {
         int col[kWideU];
@@ -306,7 +387,8 @@ __device__ __forceinline__ bool wide_long_rows(const long long* flop, int i, int
 template <bool SUM>
 __device__ __forceinline__ void wide_set_bits(const CsrView& A, const CsrView& B, int pa, int pe,
                                               bool long_rows, WideWalkSmem& wsm, uint32_t* bits,
-                                              uint32_t* sum, int words, int& bad) {
+                                              uint32_t* sum, int words, int& bad, StageState* st = nullptr,
+                                              int* status = nullptr) {
   auto set = [&](int c, double) {
     if (c >= 0) {
       if ((unsigned)c < (unsigned)(words * 32)) {
@@ -317,21 +399,34 @@ __device__ __forceinline__ void wide_set_bits(const CsrView& A, const CsrView& B
       }
     }
   };
-  if (long_rows) wide_walk_long<false>(A, B, pa, pe, wsm.ls, bad, set);
+  if (long_rows) wide_walk_long<false>(A, B, pa, pe, wsm.ls, bad, set, st, status);
   else wide_walk<false>(A, B, pa, pe, wsm.ws, bad, set);
 }
 
 __global__ void __launch_bounds__(kWideBlock, 1)
-k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long long* __restrict__ flop,
-           const int32_t* __restrict__ rows, int32_t nrows, int32_t* __restrict__ cnt,
-           WideKeep keep, int* status) {
+k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, uint32_t stage_off,
+           const long long* __restrict__ flop, const int32_t* __restrict__ rows, int32_t nrows,
+           int32_t* __restrict__ cnt, WideKeep keep, int* status) {
   extern __shared__ __align__(16) unsigned char wsm[];
   uint32_t* bits = reinterpret_cast<uint32_t*>(wsm);
   uint32_t* sum = reinterpret_cast<uint32_t*>(wsm + sum_off);
   __shared__ WideWalkSmem walk;
   __shared__ int tmp[33];
   __shared__ int s_slot;
+  __shared__ unsigned long long sbar[kWideBlock / 32 * 2];
   const int nsum = words >> 5;
+  // staging of long B-row pieces through bulk copies (stage_off = 0: off)
+  StageState stage{nullptr, nullptr, 0u, stage_off != 0};
+  if (stage_off != 0) {
+    const int wp = threadIdx.x >> 5;
+    stage.buf = reinterpret_cast<int32_t*>(wsm + stage_off) + (size_t)wp * 2 * kStageSlots;
+    stage.bar = &sbar[wp * 2];
+    if ((threadIdx.x & 31) == 0) {
+      mbar_init(stage.bar, 1);
+      mbar_init(stage.bar + 1, 1);
+      mbar_init_fence();
+    }
+  }
   for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4)
     *reinterpret_cast<uint4*>(&bits[w]) = make_uint4(0u, 0u, 0u, 0u);
   for (int s = threadIdx.x; s < nsum; s += blockDim.x) sum[s] = 0u;
@@ -346,7 +441,8 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
       // few words touched: count and clear them through the summary (such rows
       // keep nothing: walking their products again costs less than storing
       // and reloading a k-bit vector)
-      wide_set_bits<true>(A, B, A.rowptr[i], A.rowptr[i + 1], lng, walk, bits, sum, words, bad);
+      wide_set_bits<true>(A, B, A.rowptr[i], A.rowptr[i + 1], lng, walk, bits, sum, words, bad,
+                          stage_off ? &stage : nullptr, status);
       for (int s = threadIdx.x; s < nsum; s += blockDim.x) {
         uint32_t m = sum[s];
         sum[s] = 0u;
@@ -362,7 +458,8 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, const long lon
       block_exscan<int>(c, tmp, &tot);
       if (threadIdx.x == 0) cnt[i] = tot;
     } else {
-      wide_set_bits<false>(A, B, A.rowptr[i], A.rowptr[i + 1], lng, walk, bits, sum, words, bad);
+      wide_set_bits<false>(A, B, A.rowptr[i], A.rowptr[i + 1], lng, walk, bits, sum, words, bad,
+                           stage_off ? &stage : nullptr, status);
       for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4) {
         const uint4 v = *reinterpret_cast<const uint4*>(&bits[w]);
         c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
@@ -597,10 +694,20 @@ cudaError_t launch_symbolic_wide(const LaunchCtx& ctx, const CsrView& A, const C
   if (nrows <= 0) return cudaSuccess;
   const int words = wide_words(B.n);
   const WideGeom g = wide_geom(words, wide_budget(ctx), false);
-  cudaError_t e = cudaFuncSetAttribute(k_sym_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.bytes);
+  // staging buffers after the bit vector, when they fit and B's columns start
+  // on a 16-byte boundary (the bulk copies' rule)
+  size_t bytes = g.bytes;
+  uint32_t stage_off = 0;
+  const size_t stage_bytes = (size_t)(kWideBlock / 32) * 2 * kStageSlots * 4;
+  const size_t st_off = (g.bytes + 15) / 16 * 16;
+  if (ctx.stage_long_rows && ((uintptr_t)B.colind & 15) == 0 && st_off + stage_bytes <= wide_budget(ctx) - 1024) {
+    stage_off = (uint32_t)st_off;
+    bytes = st_off + stage_bytes;
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_sym_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_sym_wide<<<wide_grid(ctx, g.bytes, nrows), kWideBlock, g.bytes, ctx.stream>>>(
-      A, B, words, (uint32_t)g.sum_off, flop, rows, nrows, cnt, ctx.keep, ctx.status);
+  k_sym_wide<<<wide_grid(ctx, bytes, nrows), kWideBlock, bytes, ctx.stream>>>(
+      A, B, words, (uint32_t)g.sum_off, stage_off, flop, rows, nrows, cnt, ctx.keep, ctx.status);
   return cudaGetLastError();
 }
 

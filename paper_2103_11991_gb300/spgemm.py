@@ -52,7 +52,7 @@ class KkOptions(ctypes.Structure):
                 ("batched_graph", ctypes.c_int32), ("sym_load_pct", ctypes.c_int32),
                 ("num_load_pct", ctypes.c_int32), ("structure_cache", ctypes.c_int32),
                 ("wide_cache_mb", ctypes.c_int32), ("batched_mode", ctypes.c_int32),
-                ("batched_learned", ctypes.c_int32)]
+                ("batched_learned", ctypes.c_int32), ("stage_long_rows", ctypes.c_int32)]
 
 
 # exported symbol -> (restype, argtypes)

@@ -293,14 +293,16 @@ def test_df32_needs_strictly_ascending_b():
     check_against_oracle(A, B, rp, ci, va)
 
 
+@pytest.mark.parametrize("stage", [0, 1])
 @pytest.mark.parametrize("seed", [0, 1])
-def test_wide_rows_beyond_shared_values(seed):
+def test_wide_rows_beyond_shared_values(seed, stage):
     """Wide-tier rows whose values do not fit shared memory (k = 2^20 columns,
     15,000 to 900,000 columns per row of C): the numeric phase reloads the bit
     vector the symbolic phase kept and adds every product into C's values.
     The B rows are long (600 to 2,600 entries), so both phases take the
     entry-piece walk; four rows have more A entries (1,100 to 1,300) than one
-    segment of the walk."""
+    segment of the walk.  With stage = 1 the symbolic phase copies the long
+    B-row pieces into shared memory with bulk copies (options.stage_long_rows)."""
     k = 1 << 20
     n = 3000
     B = I.random_rows(n, k, 600, 2600, seed=60 + seed)
@@ -309,7 +311,7 @@ def test_wide_rows_beyond_shared_values(seed):
     rp = np.concatenate([A1.rowptr, A1.rowptr[-1] + A2.rowptr[1:]]).astype(np.int64)
     A = I.CSR(28, n, rp, np.concatenate([A1.colind, A2.colind]),
               I.uniform01(seed, "wide.a", int(rp[-1])) * 2 - 1)
-    rp_, ci, va, _, st = run_gpu(A, B)
+    rp_, ci, va, _, st = run_gpu(A, B, stage_long_rows=stage)
     ref = check_against_oracle(A, B, rp_, ci, va)
     assert np.diff(ref.rowptr).max() > 20000
     assert st["num_dense_rows"] + st["num_cta_rows"] > 0
