@@ -298,11 +298,28 @@ def bench_learned(args, dA, dB, madds, plain_ms, ci, va):
 
         staged_r = _events_ms(staged_step, 3, stream)
         ops.close()
+        # the plain step with the autotuner's stored options for the R-MAT family
+        from paper_2103_11991_gb300 import autotune
+        tuned = autotune.tuned_options("rmat")
+        tuned_r = None
+        if tuned:
+            opt = K.SpGEMM(**tuned)
+
+            def tuned_step():
+                r, n = opt.symbolic(dR, dR)
+                opt.numeric(dR, dR, r, n, cR, vR)
+
+            tuned_r = _events_ms(tuned_step, 3, stream)
+            opt.close()
         out["rmat20"] = _learned_vs_plain(args, dR, dR, madds_r, plain_r, cR, vR, params,
                                           "rmat20: R-MAT scale 20, edge factor 16, A*A")
         out["rmat20"]["nnz_c"] = int(nnz)
         out["rmat20"]["plain_bulk_copy_staging"] = {"ms_per_step": staged_r,
                                                     "value": 2.0 * madds_r / (staged_r * 1e-3) / 1e9}
+        if tuned_r is not None:
+            out["rmat20"]["plain_autotuned"] = {"ms_per_step": tuned_r, "options": tuned,
+                                                "value": 2.0 * madds_r / (tuned_r * 1e-3) / 1e9,
+                                                "speedup_vs_defaults": plain_r / tuned_r}
         del cR, vR, dR
         torch.cuda.empty_cache()
     return out, params
@@ -337,6 +354,29 @@ def bench_df32(args, dA, dB, madds, fp64_ms, ci, va):
     return {"arith": arith, "note": "float32 pairs, 48-bit significand: narrower than fp64",
             "ms_per_step": ms, "value": 2.0 * madds / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
             "numeric_ms": num_ms, "speedup_vs_fp64": fp64_ms / ms}
+
+
+def bench_autotuned(args, dA, dB, madds, default_ms, ci, va):
+    """The benchmark step (float64) with the autotuner's stored options for the
+    3D-stencil family (searched on other grids) against the library defaults."""
+    import torch
+    from paper_2103_11991_gb300 import autotune
+    from paper_2103_11991_gb300 import spgemm as K
+    tuned = autotune.tuned_options("stencil3d")
+    if not tuned:
+        return None
+    stream = torch.cuda.current_stream()
+    op = K.SpGEMM(arith=HEAD_ARITH, **tuned)
+
+    def step():
+        r, n = op.symbolic(dA, dB)
+        op.numeric(dA, dB, r, n, ci, va)
+
+    ms = _events_ms(step, max(3, args.steps // 2), stream)
+    op.sync()
+    op.close()
+    return {"family": "stencil3d", "options": tuned, "ms_per_step": ms,
+            "value": 2.0 * madds / (ms * 1e-3) / 1e9, "speedup_vs_defaults": default_ms / ms}
 
 
 def bench_latency(args):
@@ -921,6 +961,8 @@ def run_ours(args, rank, world, local_rank):
         forms["df32"] = bench_df32(args, dA, dB, madds, ms, ci, va)
     if rank == 0 and args.forms in ("all", "latency"):
         forms["stencil2d_64"] = bench_latency(args)
+    if rank == 0 and args.forms in ("all", "df32"):
+        forms["autotuned"] = bench_autotuned(args, dA, dB, madds, ms, ci, va)
     if rank == 0 and args.forms in ("all", "learned"):
         forms["learned"], predictor = bench_learned(args, dA, dB, madds, ms, ci, va)
     if rank == 0 and args.forms in ("all", "batched"):

@@ -22,9 +22,11 @@
  *   1 - persistent: the work-queue kernels above.  With options.batched_graph
  *       = 1 and a non-default stream, each phase is captured into a CUDA graph
  *       on its first call and replayed by later calls with the same pairs
- *       (same pointers and sizes).  Rows whose flop bound exceeds 24576
- *       (symbolic) or whose nnz exceeds 4096 (numeric) are outside the batched
- *       accumulators and return KK_ERR_CAPACITY.
+ *       (same pointers and sizes).  A batch with a row beyond the batched
+ *       accumulators (a flop bound or an nnz(C(i,:)) above the largest
+ *       persistent bin) is handed whole to the packed form below, inside the
+ *       same symbolic call (its numeric calls follow); such a batch is then
+ *       not captured.
  *   2 - packed (and 0, the default): the batch becomes one block-diagonal
  *       product diag(A_k) * diag(B_k) in handle scratch (A's columns shifted to
  *       the packed rows of B_k, B's columns kept local, so C's rows come out in

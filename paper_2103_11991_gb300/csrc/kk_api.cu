@@ -832,6 +832,8 @@ struct kk_spgemm_handle_s {
   bool cache_valid = false;
   // wide-tier bit vectors kept by the symbolic phase
   DevBuf d_wbits, d_wslot, d_wnext;
+  bool b_overflow = false;             // the persistent batched form handed a batch to the packed form
+  unsigned long long b_overflow_key = 0;  // ... the batch's key (pairs, output pointer, count)
   bool keep_valid = false;
   const void* keep_key[4] = {nullptr, nullptr, nullptr, nullptr};
   WideKeep keep{nullptr, nullptr, nullptr, 0, 0};  // what the next launches use
@@ -2175,16 +2177,18 @@ kk_status kk_spgemm_batched_symbolic(kk_spgemm_handle h, int32_t count, const kk
     sb += B[k].nnz;
   }
   h->p_valid = false;
-  if (h->opt.batched_mode != 1) {
-    if ((st = batched_packed_symbolic(h, count, A, B, hd, c_rowptr, c_offsets, total_nnz)) != KK_OK)
-      return st;
+  auto packed = [&]() -> kk_status {
+    kk_status st3;
+    if ((st3 = batched_packed_symbolic(h, count, A, B, hd, c_rowptr, c_offsets, total_nnz)) != KK_OK)
+      return st3;
     std::memcpy(h->h_bdesc2, hd, sizeof(PairDesc) * (size_t)count);
     h->b_count = count;
     h->b_R = R;
     h->b_nnzb = nnzb;
     h->b_valid = true;
     return KK_OK;
-  }
+  };
+  if (h->opt.batched_mode != 1) return packed();
   batched_bin_tables(h->b_sym, h->b_num, h->opt.sym_load_pct, h->opt.num_load_pct);
   const size_t R1 = (size_t)(R > 0 ? R : 1);
   const int nblk = (int)((R + kBinRows - 1) / kBinRows);
@@ -2256,8 +2260,21 @@ kk_status kk_spgemm_batched_symbolic(kk_spgemm_handle h, int32_t count, const kk
   unsigned long long key = fnv1a(hd, sizeof(PairDesc) * (size_t)count);
   key = fnv1a(&c_rowptr, sizeof(c_rowptr), key);
   key = fnv1a(&count, sizeof(count), key);
+  // a batch already found to hold rows beyond the persistent kernels'
+  // accumulators goes straight to the block-diagonal form
+  if (h->b_overflow && key == h->b_overflow_key) return packed();
   if ((st = run_maybe_graph(h, use_graph, &h->g_sym, &h->g_sym_key, key, enqueue)) != KK_OK) return st;
   KK_CUDA(h, cudaStreamSynchronize(s), "sync");
+  if (hm->status == KK_ERR_CAPACITY) {
+    // Rows whose flop bound or nnz exceed the persistent kernels' shared-memory
+    // accumulators: the whole batch runs as one block-diagonal product through
+    // the plain two-phase kernels (every tier, no capacity limit); its numeric
+    // calls follow (h->p_valid).
+    KK_CUDA(h, cudaMemsetAsync(&dm->status, 0, sizeof(int), s), "memset");
+    h->b_overflow = true;
+    h->b_overflow_key = key;
+    return packed();
+  }
   if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
   const int64_t* off = static_cast<const int64_t*>(h->h_boff);
   h->b_total = off[count];

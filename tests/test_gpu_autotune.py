@@ -16,7 +16,8 @@ def test_autotune_small_space(tmp_path, monkeypatch):
                         lambda fam: [(A, A) for A in (I.stencil_3d(16, 16, 16, 27, 26.0, -1.0),)])
     space = {"team_vec_min_len": [8, 20], "use_window": [0, 1]}
     best, res = T.tune_family("stencil3d", space=space, reps=1)
-    assert len(res) == 4 and set(best) == {"team_vec_min_len", "use_window"}
+    assert 2 <= len(res) <= 4 and set(best) == {"team_vec_min_len", "use_window"}
+    assert res[json.dumps(best, sort_keys=True)] == min(res.values())
     assert all(v > 0 for v in res.values())
     path = tmp_path / "tuned.json"
     path.write_text(json.dumps({"stencil3d": {"options": best}}))

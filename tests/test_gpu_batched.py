@@ -117,3 +117,37 @@ def test_batched_learned_matches_oracle(pred):
         op.sync()
         scaled = [(I.CSR(A.m, A.n, A.rowptr, A.colind, A.vals * -2.0), B) for A, B in pairs]
         _check_batch(scaled, rowptr, off, colind2[:total], vals2[:total])
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_persistent_batch_with_heavy_rows(graph):
+    """A batch whose rows exceed the persistent kernels' accumulators (rows of
+    about 26,000 products over 60,000 columns beside ordinary pairs): the persistent
+    mode hands the batch to the block-diagonal form inside the same call; every
+    product still matches the oracle, on repeated calls and a numeric refresh."""
+    import torch
+    from paper_2103_11991_gb300 import spgemm as K
+    pairs = _pairs(10, 7100)
+    heavy_a = I.random_rows(30, 400, 180, 220, seed=91)
+    heavy_b = I.random_rows(400, 60000, 120, 140, seed=92)
+    pairs.insert(3, (heavy_a, heavy_b))
+    dA = [K.DeviceCSR.from_host(A) for A, _ in pairs]
+    dB = [K.DeviceCSR.from_host(B) for _, B in pairs]
+    stream = torch.cuda.Stream() if graph else None
+    ctx = torch.cuda.stream(stream) if stream is not None else torch.cuda.stream(torch.cuda.current_stream())
+    with ctx:
+        with K.BatchedSpGEMM(stream=stream, batched_graph=graph, batched_mode=1) as op:
+            for _ in range(2):
+                rowptr, off, total = op.symbolic(dA, dB)
+                colind, vals = op.numeric(dA, dB, rowptr, total)
+                op.sync()
+                torch.cuda.synchronize()
+                _check_batch(pairs, rowptr, off, colind[:total], vals[:total])
+            for d in dA:
+                d.vals.mul_(0.5)
+            op.numeric(dA, dB, rowptr, total, colind, vals)
+            op.sync()
+            torch.cuda.synchronize()
+    for A, _ in pairs:
+        A.vals = A.vals * 0.5
+    _check_batch(pairs, rowptr, off, colind[:total], vals[:total])
