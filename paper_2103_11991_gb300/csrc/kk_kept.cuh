@@ -17,9 +17,10 @@ namespace {
 
 constexpr int kKeptSlots = 256;
 constexpr unsigned long long kKeptEmpty = ~0ull;
-// A entries whose B loads are issued together; 4 keeps the kernel within 40
-// registers (six 256-thread CTAs per SM), which measured faster than 8 at 64.
-constexpr int kKeptBatch = 4;
+// A entries whose B loads are issued together: 3 keeps the kernel within 40
+// registers (six 256-thread CTAs per SM); measured on the 27-point product in
+// float64 against 2, 4 and 5 (1.90 ms against 1.90, 1.98 and 2.23) and 8.
+constexpr int kKeptBatch = 3;
 
 // Rank of column o (relative to the row's first word) through the table, or
 // the spare slot kWindowMaxNnz when o is not a column of the row.  CHECK =
@@ -105,8 +106,8 @@ __device__ __forceinline__ void kept_batch(const int4* ainfo, int t0, int lo_c, 
 }
 
 // Value pass over one chunk of at most 32 A entries: batches of kKeptBatch,
-// a tail of 3 in one more (entries past the chunk have length 0), a tail of 1
-// or 2 in a batch of 2.
+// a tail of more than 2 in one more batch (entries past the chunk have length
+// 0), a tail of 1 or 2 in a batch of 2.
 template <bool DFM, bool PROBE, bool CHECK>
 __device__ __forceinline__ void kept_chunk(const int4* ainfo, int nch, int lo_c, const unsigned long long* table,
                                            unsigned long long* vacc, const int32_t* __restrict__ bcol,
