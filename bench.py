@@ -39,6 +39,10 @@ HEAD_ARITH = 1
 # a throughput probe on the GB300, 0.505 T fused multiply-adds per second): the
 # bound of a numeric phase that does one float64 fma per multiply-add.
 DFMA_PEAK_PER_S = 0.505e12
+# A warp-level float64 FMA occupies the FP64 pipe for the same time with any
+# number of active lanes (profiles/gb300_pipes.md): 0.01647 T warp FMAs/s.  A
+# value pass with lanes over one A entry's B row issues one per A entry.
+DFMA_WARP_PER_S = 0.01647e12
 WORKLOAD_DESC = ("C=A*A, A = 3D 27-point stencil on 100^3 (1,000,000 rows, 26,463,592 nnz, "
                  "26/-1), CSR int32/f64; C 120,553,784 nnz")
 
@@ -885,6 +889,9 @@ def run_ours(args, rank, world, local_rank):
             "bound": "fp64_fma", "achieved": dfma / 1e12, "peak": DFMA_PEAK_PER_S / 1e12,
             "unit": "T FMA/s", "frac": dfma / DFMA_PEAK_PER_S, "madds_per_step": dom_madds,
             "floor_ms": dom_madds / DFMA_PEAK_PER_S * 1e3,
+            # one warp FMA per A entry of the tier's rows (B rows of at most 32)
+            "warp_fma_floor_ms": tst[f"num_{t}_a"] / DFMA_WARP_PER_S * 1e3,
+            "warp_fma_frac": (tst[f"num_{t}_a"] / DFMA_WARP_PER_S * 1e3) / dom_ms_per_step,
             "peak_source": "measured FP64 FMA probe on this GPU model (profiles/gb300_pipes.md)"}
     kernels = {k: {"ms_per_step": v[0] / reps, "launches_per_step": v[1] / reps} for k, v in kt.items()}
 
