@@ -479,6 +479,21 @@ def bench_jacobi(args):
     step_ms = _events_ms(step, 5, stream)
     jac_ms = _events_ms(lambda: op.jacobi_numeric(dA, dP, rp, nnz, omega, ci, va), 10, stream)
     plain_ms = _events_ms(lambda: op.numeric(dA, dP, rp, nnz, ci, va), 10, stream)
+    # the unfused sequence the fused phase replaces: E = A P (the plain numeric
+    # phase above), then the sum of E and P through the library's SpAdd
+    # (symbolic + numeric; its per-row scaling by -omega/D(i) left out, which
+    # only makes the unfused sequence cheaper)
+    dE = K.DeviceCSR(A.m, P.n, rp.to(torch.int32), ci, va)
+    sa = K.SpGEMM()
+    erp, enz = sa.spadd_symbolic(dE, dP)
+    eci, eva = sa.spadd_numeric(1.0, dE, 1.0, dP, erp, enz)
+
+    def add_step():
+        r2, n2 = sa.spadd_symbolic(dE, dP)
+        sa.spadd_numeric(1.0, dE, 1.0, dP, r2, n2, eci, eva)
+
+    add_ms = _events_ms(add_step, 10, stream)
+    sa.close()
     op.jacobi_numeric(dA, dP, rp, nnz, omega, ci, va)  # C holds the fused result again
     op.sync()
     op.close()
@@ -508,6 +523,8 @@ def bench_jacobi(args):
             "ms_per_step": step_ms, "value": 2.0 * madds / (step_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
             "jacobi_numeric_ms": jac_ms, "plain_numeric_ms": plain_ms,
             "fused_over_plain": jac_ms / plain_ms,
+            "unfused_ms": plain_ms + add_ms, "unfused_add_ms": add_ms,
+            "fused_speedup_vs_unfused": (plain_ms + add_ms) / jac_ms,
             "numeric_hbm_gbs": byts / (jac_ms * 1e-3) / 1e9, "cpu_baseline": cpu}
 
 

@@ -609,64 +609,57 @@ __global__ void __launch_bounds__(kFpThreads) k_fingerprint(FpArrays arr, unsign
 // diagonal entry, s_i = -omega / D(i), D(i) = the sum of the row's stored
 // diagonal entries.  One team of kJacTeam lanes per row.
 // ---------------------------------------------------------------------------
-// 1/d to about one unit in the last place without the float64 divide (a long
-// sequence on the FP64 pipe, which is slow on this part): a float32 reciprocal
-// refined by two Newton-Raphson steps x <- x + x(1 - d x), each of which about
-// doubles the correct bits (24 -> 48 -> 53).  Outside the float32 range the
-// float64 divide is used.
-__device__ __forceinline__ double jacobi_recip(double d) {
-  // |d| in [2^-99, 2^99], decided on the exponent bits (no float64 compare)
-  const uint32_t e = ((uint32_t)(__double_as_longlong(d) >> 52)) & 0x7FFu;
-  if (e < 1023u - 99u || e > 1023u + 99u) return 1.0 / d;
-  double x = (double)__frcp_rn((float)d);
-  x = fma(x, fma(-d, x, 1.0), x);
-  x = fma(x, fma(-d, x, 1.0), x);
-  return x;
-}
-
-// T lanes per row, the loads of U entries per lane in flight; a row of at most
-// T * U entries is written from registers.  The next row's bounds are loaded
-// while a row is processed.
+// The row scaling of the Jacobi-fused product (paper Sec. "Jacobi-Fused SpGEMM
+// Kernel", C = (I - omega D^-1 A) B): per row i, D(i) = the sum of the row's
+// stored diagonal entries, s_i = -omega / D(i) and the position of the row's
+// first diagonal entry.  The numeric kernels then take A(i,j) as s_i * a_ij,
+// plus 1 at that entry (so B(i,:) is added once per row), as they load it: A
+// is not rewritten.  The thread tier, whose rows are short, finds s_i itself;
+// this kernel serves the rows of the other tiers, the rows[0..nrows) of one
+// numeric bin.  T lanes per row, the column loads of U entries per lane in
+// flight (a value is loaded only for a diagonal entry); the next row's bounds
+// are loaded while a row is processed.  A row without a stored diagonal, or
+// whose diagonal sums to 0, is reported (KK_ERR_INVALID_ARG).
 template <int T, int U>
-__global__ void __launch_bounds__(256) k_jacobi_values(CsrView A, double omega, double* __restrict__ out,
-                                                       int* status) {
+__global__ void __launch_bounds__(256) k_jacobi_rows(CsrView A, const int32_t* __restrict__ rows, int32_t nrows,
+                                                     double omega, double* __restrict__ out_s,
+                                                     int32_t* __restrict__ out_p, int* status) {
   const int tl = threadIdx.x % T;
   const unsigned mask = team_mask<T>();
   const long long team0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / T;
   const long long nteams = (long long)gridDim.x * blockDim.x / T;
   int bad = 0;
-  long long r = team0;
-  int pa_n = 0, pe_n = 0;
-  if (r < A.m) {
-    pa_n = A.rowptr[r];
-    pe_n = A.rowptr[r + 1];
+  long long t = team0;
+  int pa_n = 0, pe_n = 0, r_n = 0;
+  if (t < nrows) {
+    r_n = rows[t];
+    pa_n = A.rowptr[r_n];
+    pe_n = A.rowptr[r_n + 1];
   }
-  for (; r < A.m; r += nteams) {
-    const int pa = pa_n, pe = pe_n;
-    if (r + nteams < A.m) {
-      pa_n = A.rowptr[r + nteams];
-      pe_n = A.rowptr[r + nteams + 1];
+  for (; t < nrows; t += nteams) {
+    const int pa = pa_n, pe = pe_n, r = r_n;
+    if (t + nteams < nrows) {
+      r_n = rows[t + nteams];
+      pa_n = A.rowptr[r_n];
+      pe_n = A.rowptr[r_n + 1];
     }
-    // The float64 work is kept to one operation per entry plus the row's
-    // reciprocal (FP64 is the scarce pipe on this part): the diagonal value is
-    // picked by selects, repeats of it are added on a branch taken only when a
-    // row has them, and every entry gets one fma with 1 or 0 as the addend.
+    // the diagonal value is picked by selects; repeats of it are added on a
+    // branch taken only when a row has them
     double d = 0.0, dx = 0.0;
     int first = 0x7fffffff, nd = 0;
-    double v[U];
     for (int p0 = pa; p0 < pe; p0 += T * U) {
       int c[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int p = p0 + u * T + tl;
         c[u] = p < pe ? A.colind[p] : -1;
-        v[u] = p < pe ? A.vals[p] : 0.0;
       }
       const int nd0 = nd;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const bool on = c[u] == (int)r;
-        d = (on && nd == 0) ? v[u] : d;
+        const bool on = c[u] == r;
+        const double v = on ? A.vals[p0 + u * T + tl] : 0.0;
+        d = (on && nd == 0) ? v : d;
         nd += on ? 1 : 0;
         first = on ? min(first, p0 + u * T + tl) : first;
       }
@@ -675,8 +668,8 @@ __global__ void __launch_bounds__(256) k_jacobi_values(CsrView A, double omega, 
         int k = nd0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          if (c[u] == (int)r) {
-            if (k > 0) dx += v[u];
+          if (c[u] == r) {
+            if (k > 0) dx += A.vals[p0 + u * T + tl];
             ++k;
           }
         }
@@ -691,19 +684,17 @@ __global__ void __launch_bounds__(256) k_jacobi_values(CsrView A, double omega, 
         first = min(first, __shfl_xor_sync(mask, first, o, T));
       }
     }
+    double sc = 0.0;
+    int fp = -1;
     if (nd == 0 || (__double_as_longlong(d) << 1) == 0) {
       bad = 1;
-      continue;
-    }
-    const double s = -omega * jacobi_recip(d);
-    if (pe - pa <= T * U) {  // the row's values are still in registers
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int p = pa + u * T + tl;
-        if (p < pe) out[p] = fma(s, v[u], p == first ? 1.0 : 0.0);
-      }
     } else {
-      for (int p = pa + tl; p < pe; p += T) out[p] = fma(s, A.vals[p], p == first ? 1.0 : 0.0);
+      sc = -omega * jacobi_recip(d);
+      fp = first;
+    }
+    if (tl == 0) {
+      out_s[r] = sc;
+      out_p[r] = fp;
     }
   }
   if (bad) set_status(status, KK_ERR_INVALID_ARG);
@@ -768,7 +759,8 @@ struct kk_spgemm_handle_s {
   DevBuf d_binstart;   // int32[2 * (kMaxBins + 1)]
   DevBuf d_scan;       // long long[nblk]
   DevBuf d_bsplit;     // float2[nnzB]
-  DevBuf d_jvals;      // float64[nnzA]: A's values scaled for the Jacobi-fused numeric phase
+  DevBuf d_jvals;      // float64[m]: row scales s_i of the Jacobi-fused numeric phase
+  DevBuf d_jpos;       // int32[m]: position of each row's first diagonal entry (Jacobi)
   DevBuf d_apos, d_bpos;  // SpAdd: slot in C's row of every entry of A and of B (int32)
   DevBuf d_acnt;          // SpAdd: nnz(C(i,:)) (int32[m])
   DevBuf d_along;         // SpAdd: [0] long-row count, [1..] long rows (int32[m + 1])
@@ -1211,18 +1203,35 @@ kk_status check_device_status(kk_spgemm_handle h, int status) {
 
 }  // namespace
 
-// Jacobi scaling pass with teams of T lanes, one resident wave of blocks.
+// Jacobi row scaling of rows[0..nrows) with teams of T lanes, one resident
+// wave of blocks.
 template <int T, int U>
-static void launch_jacobi_values(kk_spgemm_handle h, const kk_csr* A, double omega) {
+static void launch_jacobi_rows_t(kk_spgemm_handle h, const CsrView& av, const int32_t* rows, int32_t nrows) {
   static int per_sm = 0;
   if (per_sm == 0 &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_values<T, U>, 256, 0) != cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_rows<T, U>, 256, 0) != cudaSuccess) {
     (void)cudaGetLastError();
     per_sm = 4;
   }
-  k_jacobi_values<T, U><<<grid_for((long long)A->m * T, 256, h->num_sms * (per_sm > 0 ? per_sm : 1)), 256,
-                          0, h->stream>>>(view(A), omega, h->d_jvals.as<double>(),
-                                          &h->d_misc.as<Misc>()->status);
+  k_jacobi_rows<T, U><<<grid_for((long long)nrows * T, 256, h->num_sms * (per_sm > 0 ? per_sm : 1)), 256, 0,
+                        h->stream>>>(av, rows, nrows, av.jac_omega, const_cast<double*>(av.jac_s),
+                                     const_cast<int32_t*>(av.jac_p), &h->d_misc.as<Misc>()->status);
+}
+
+// Team width by the mean row length of A: one lane per row for short rows (AMG
+// operators), a warp for long ones.
+static cudaError_t launch_jacobi_rows(kk_spgemm_handle h, const CsrView& av, const int32_t* rows,
+                                      int32_t nrows) {
+  timer_begin(h->timer, h->stream, "jacobi_rows");
+  const long long avg = av.m > 0 ? (long long)av.nnz / av.m : 0;
+  if (avg <= 8)
+    launch_jacobi_rows_t<1, 8>(h, av, rows, nrows);
+  else if (avg <= 32)
+    launch_jacobi_rows_t<4, 8>(h, av, rows, nrows);
+  else
+    launch_jacobi_rows_t<32, 4>(h, av, rows, nrows);
+  timer_end(h->timer, h->stream);
+  return cudaGetLastError();
 }
 
 // Analysis of A with teams of T lanes, one resident wave of blocks (the kernel
@@ -1490,8 +1499,10 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   return KK_OK;
 }
 
-kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B,
-                            const int64_t* c_rowptr, int32_t* c_colind, double* c_vals) {
+// The numeric phase; jac makes it the Jacobi-fused phase (see CsrView) with
+// weight omega, in float64.
+static kk_status numeric_impl(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B, const int64_t* c_rowptr,
+                              int32_t* c_colind, double* c_vals, bool jac, double omega) {
   if (!h) return KK_ERR_INVALID_ARG;
   if (!h->have_symbolic) return fail(h, KK_ERR_NOT_SYMBOLIC, "numeric before symbolic");
   kk_status st;
@@ -1501,12 +1512,22 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
     return fail(h, KK_ERR_STRUCTURE_MISMATCH, "A/B dims or nnz differ from the symbolic call");
   if (!c_rowptr) return fail(h, KK_ERR_INVALID_ARG, "c_rowptr is NULL");
   if (h->nnz_c > 0 && (!c_colind || !c_vals)) return fail(h, KK_ERR_INVALID_ARG, "C arrays are NULL");
-  const CsrView av = view(A), bv = view(B);
+  CsrView av = view(A);
+  if (jac && h->am > 0) {
+    KK_CUDA(h, h->d_jvals.ensure(sizeof(double) * (size_t)h->am), "alloc Jacobi row scales");
+    KK_CUDA(h, h->d_jpos.ensure(sizeof(int32_t) * (size_t)h->am), "alloc Jacobi row scales");
+    av.jac_s = h->d_jvals.as<double>();
+    av.jac_p = h->d_jpos.as<int32_t>();
+    av.jac_omega = omega;
+  }
+  const CsrView bv = view(B);
   cudaStream_t s = h->stream;
   Misc* dm = h->d_misc.as<Misc>();
   // DF32 needs B's rows strictly ascending (its error bound counts at most
-  // nnz(A(i,:)) contributions per entry); otherwise the product runs in float64
-  const int32_t arith = (h->opt.arith == KK_ARITH_FP64 || !h->b_sorted) ? kArithF64 : kArithDF32;
+  // nnz(A(i,:)) contributions per entry); otherwise the product runs in float64,
+  // as does the Jacobi-fused product (its scaled values are formed in float64)
+  const int32_t arith =
+      (h->opt.arith == KK_ARITH_FP64 || !h->b_sorted || jac) ? kArithF64 : kArithDF32;
   h->last_arith = arith;
   if (h->am == 0 || h->nnz_c == 0) return KK_OK;
   const float2* bsplit = nullptr;
@@ -1543,6 +1564,12 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
     if (cnt <= 0) continue;
     h->stats[9] += 1;
     const int32_t* rows = h->d_nrows.as<int32_t>() + h->num_start[b];
+    if (jac && h->num_bins[b].tier != kTierThread) {
+      // the row scales of this bin's rows (the thread tier forms its own)
+      cudaError_t e = launch_jacobi_rows(h, av, rows, cnt);
+      if (e != cudaSuccess) return cuda_fail(h, e, "Jacobi launch");
+      h->stats[9] += 1;
+    }
     cudaError_t e = h->num_bins[b].tier == kTierWindow
                         ? launch_numeric_window(ctx, h->num_bins[b], av, bv, bcomp, wview, wscratch, bsplit,
                                                 &dm->range_bad, arith, c_rowptr, rows, cnt, c_colind,
@@ -1558,6 +1585,12 @@ kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
 // ---------------------------------------------------------------------------
 // Jacobi-fused numeric phase (kk_jacobi.h)
 // ---------------------------------------------------------------------------
+
+kk_status kk_spgemm_numeric(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B,
+                            const int64_t* c_rowptr, int32_t* c_colind, double* c_vals) {
+  return numeric_impl(h, A, B, c_rowptr, c_colind, c_vals, false, 0.0);
+}
+
 kk_status kk_spgemm_jacobi_numeric(kk_spgemm_handle h, double omega, const kk_csr* A,
                                    const kk_csr* B, const int64_t* c_rowptr, int32_t* c_colind,
                                    double* c_vals) {
@@ -1566,25 +1599,8 @@ kk_status kk_spgemm_jacobi_numeric(kk_spgemm_handle h, double omega, const kk_cs
   if ((st = check_csr(h, A, "A", true)) != KK_OK) return st;
   if (A->m != A->n) return fail(h, KK_ERR_INVALID_ARG, "Jacobi needs a square A");
   if (!std::isfinite(omega)) return fail(h, KK_ERR_INVALID_ARG, "omega is not finite");
-  if (A->nnz > 0) {
-    KK_CUDA(h, h->d_jvals.ensure(sizeof(double) * (size_t)A->nnz), "alloc Jacobi values");
-  }
-  if (A->m > 0) {
-    timer_begin(h->timer, h->stream, "jacobi_values");
-    // one lane per row for short rows (AMG operators), a warp for long ones
-    const long long avg = (long long)A->nnz / A->m;
-    if (avg <= 8)
-      launch_jacobi_values<1, 8>(h, A, omega);
-    else if (avg <= 32)
-      launch_jacobi_values<4, 8>(h, A, omega);
-    else
-      launch_jacobi_values<32, 4>(h, A, omega);
-    timer_end(h->timer, h->stream);
-    KK_CUDA(h, cudaGetLastError(), "Jacobi launch");
-  }
-  kk_csr Aj = *A;
-  Aj.vals = A->nnz > 0 ? h->d_jvals.as<double>() : A->vals;
-  return kk_spgemm_numeric(h, &Aj, B, c_rowptr, c_colind, c_vals);
+  // the numeric tiers scale A's values by row as they load them
+  return numeric_impl(h, A, B, c_rowptr, c_colind, c_vals, true, omega);
 }
 
 // ---------------------------------------------------------------------------

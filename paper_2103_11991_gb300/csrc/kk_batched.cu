@@ -301,15 +301,15 @@ __device__ __forceinline__ void warp_num_row(const PairDesc& p, int i, long long
       const int slot = map_slot(keys, bcol[q], log2s, status);
       if (slot >= 0) upd_df(vals, slot, a, load_b(bspl, q), atomic, status);
     };
-    if (flat) visit_products<32, true, DF>(pa, pe, 0, 1, lane, 0xffffffffu, rng, PrepDF{p.A.vals}, f);
-    else visit_products<32, false, DF>(pa, pe, 0, 1, lane, 0xffffffffu, rng, PrepDF{p.A.vals}, f);
+    if (flat) visit_products<32, true, DF>(pa, pe, 0, 1, lane, 0xffffffffu, rng, PrepDF{p.A, i}, f);
+    else visit_products<32, false, DF>(pa, pe, 0, 1, lane, 0xffffffffu, rng, PrepDF{p.A, i}, f);
   } else {
     auto f = [&](double a, int, int q) {
       const int slot = map_slot(keys, bcol[q], log2s, status);
       if (slot >= 0) upd_f64(vals, slot, a, bval[q], atomic);
     };
-    if (flat) visit_products<32, true, double>(pa, pe, 0, 1, lane, 0xffffffffu, rng, PrepF64{p.A.vals}, f);
-    else visit_products<32, false, double>(pa, pe, 0, 1, lane, 0xffffffffu, rng, PrepF64{p.A.vals}, f);
+    if (flat) visit_products<32, true, double>(pa, pe, 0, 1, lane, 0xffffffffu, rng, PrepF64{p.A, i}, f);
+    else visit_products<32, false, double>(pa, pe, 0, 1, lane, 0xffffffffu, rng, PrepF64{p.A, i}, f);
   }
   __syncwarp();
   int n = 0;
@@ -360,13 +360,13 @@ __device__ __forceinline__ void cta_num_row(const PairDesc& p, int i, long long 
   const double* bval = p.B.vals;
   const float2* bspl = split + p.split_base;
   if (df) {
-    visit_products<32, true, DF>(pa, pe, warp, kBWarps, lane, 0xffffffffu, rng, PrepDF{p.A.vals},
+    visit_products<32, true, DF>(pa, pe, warp, kBWarps, lane, 0xffffffffu, rng, PrepDF{p.A, i},
                                  [&](DF a, int, int q) {
                                    const int slot = map_slot(keys, bcol[q], log2s, status);
                                    if (slot >= 0) upd_df(vals, slot, a, load_b(bspl, q), true, status);
                                  });
   } else {
-    visit_products<32, true, double>(pa, pe, warp, kBWarps, lane, 0xffffffffu, rng, PrepF64{p.A.vals},
+    visit_products<32, true, double>(pa, pe, warp, kBWarps, lane, 0xffffffffu, rng, PrepF64{p.A, i},
                                      [&](double a, int, int q) {
                                        const int slot = map_slot(keys, bcol[q], log2s, status);
                                        if (slot >= 0) upd_f64(vals, slot, a, bval[q], true);

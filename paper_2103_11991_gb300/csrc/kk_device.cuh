@@ -283,4 +283,20 @@ __device__ __forceinline__ void df_atomic_fma(unsigned long long* slot, const DF
   set_status(status, KK_ERR_TIMEOUT);
 }
 
+// Jacobi-fused product's 1/D(i) to about one unit in the last place without
+// the float64 divide (a long sequence on the FP64 pipe, which is slow on this
+// part): a float32 reciprocal
+// refined by two Newton-Raphson steps x <- x + x(1 - d x), each of which about
+// doubles the correct bits (24 -> 48 -> 53).  Outside the float32 range the
+// float64 divide is used.
+__device__ __forceinline__ double jacobi_recip(double d) {
+  // |d| in [2^-99, 2^99], decided on the exponent bits (no float64 compare)
+  const uint32_t e = ((uint32_t)(__double_as_longlong(d) >> 52)) & 0x7FFu;
+  if (e < 1023u - 99u || e > 1023u + 99u) return 1.0 / d;
+  double x = (double)__frcp_rn((float)d);
+  x = fma(x, fma(-d, x, 1.0), x);
+  x = fma(x, fma(-d, x, 1.0), x);
+  return x;
+}
+
 }  // namespace kk

@@ -45,7 +45,41 @@ struct CsrView {
   const int32_t* rowptr;
   const int32_t* colind;
   const double* vals;
+  // Jacobi-fused numeric phase (null otherwise): row i of A enters the product
+  // as jac_s[i] * A(i,:) plus 1 at entry jac_p[i] (the row's first diagonal
+  // entry), i.e. as row i of I - omega D^-1 A, without a scaled copy of A.  The
+  // thread tier forms s_i and that position from the row itself with
+  // jac_omega; the other tiers' rows get them from a row-scale kernel.
+  const double* jac_s;
+  const int32_t* jac_p;
+  double jac_omega;
 };
+
+#ifdef __CUDACC__
+// Row i's Jacobi scaling (loaded once per row): on = false for the plain product.
+struct ARowScale {
+  double s;
+  int p;
+  bool on;
+};
+__device__ __forceinline__ ARowScale a_row_scale(const CsrView& A, int i) {
+  ARowScale r{1.0, -1, A.jac_s != nullptr};
+  if (r.on) {
+    r.s = A.jac_s[i];
+    r.p = A.jac_p[i];
+  }
+  return r;
+}
+// Value of A's entry p as the numeric phase multiplies it: the stored value v,
+// or for the Jacobi-fused product s_i * v (+ 1 at the row's first diagonal
+// entry), formed once per A entry as it is loaded.
+__device__ __forceinline__ double a_scaled(const ARowScale& r, int p, double v) {
+  return r.on ? (p == r.p ? fma(r.s, v, 1.0) : r.s * v) : v;
+}
+__device__ __forceinline__ double a_value(const CsrView& A, int i, int p) {
+  return a_scaled(a_row_scale(A, i), p, A.vals[p]);
+}
+#endif
 
 // Accumulator tiers.  The thread tier counts as the team tier in statistics.
 enum Tier : int32_t { kTierTeam = 0, kTierCta = 1, kTierDense = 2, kTierWindow = 3, kTierThread = 4 };

@@ -31,7 +31,7 @@ struct KeptGeom {
 // CHECK = false: the index arrays were verified against the symbolic call by
 // their fingerprints fp[0] (symbolic) and fp[1] (this call), so products are
 // not checked one by one against the kept structure.
-template <bool CHECK>
+template <bool CHECK, bool JAC>
 __global__ void __launch_bounds__(kKeptWarps * 32, 6)
 k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__ row_lo,
            const float2* __restrict__ bspl, const int32_t* __restrict__ b_range_bad, int32_t arith,
@@ -106,9 +106,9 @@ k_num_kept(CsrView A, CsrView B, WinCacheView cache, const int32_t* __restrict__
     // arithmetic of this row: DF32 unless a value of the row is outside its window
     int missing = 0;
     const bool df =
-        probe ? kept_values<true, CHECK>(pa, pe, df_all, A.colind, A.vals, B.rowptr, ainfo, lo_c, table,
+        probe ? kept_values<true, CHECK, JAC>(pa, pe, df_all, A, i, B.rowptr, ainfo, lo_c, table,
                                          vacc, B.colind, bspl, B.vals, lane, missing)
-              : kept_values<false, CHECK>(pa, pe, df_all, A.colind, A.vals, B.rowptr, ainfo, lo_c,
+              : kept_values<false, CHECK, JAC>(pa, pe, df_all, A, i, B.rowptr, ainfo, lo_c,
                                           table, vacc, B.colind, bspl, B.vals, lane, missing);
     if (missing) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
     const int n = min(cnt, kWindowMaxNnz);
@@ -131,7 +131,9 @@ cudaError_t launch_num_kept(const LaunchCtx& ctx, const CsrView& A, const CsrVie
                             int32_t* c_colind, double* c_vals, int32_t* left_rows, int32_t* left_count) {
   const size_t smem = (size_t)kKeptWarps * KeptGeom::kWarpBytes;
   const bool check = ctx.fingerprint == nullptr;
-  auto kern = check ? k_num_kept<true> : k_num_kept<false>;
+  const bool jac = A.jac_s != nullptr;
+  auto kern = check ? (jac ? k_num_kept<true, true> : k_num_kept<true, false>)
+                    : (jac ? k_num_kept<false, true> : k_num_kept<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // one resident wave: the rows in flight form one contiguous band, so the B

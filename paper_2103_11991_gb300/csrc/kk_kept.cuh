@@ -165,18 +165,18 @@ __device__ __forceinline__ void kept_chunk_long(const int4* ainfo, int nch, int 
 // Chunk setup: lane t holds A entry p0 + t (B row start, length, A value
 // split for DF32 or as raw float64 halves).  Returns 1 if the lane's value is
 // outside the DF32 window.
-__device__ __forceinline__ int kept_info(int p0, int pe, const int32_t* __restrict__ acol,
-                                         const double* __restrict__ aval,
+template <bool JAC>
+__device__ __forceinline__ int kept_info(int p0, int pe, const CsrView& A, int i,
                                          const int32_t* __restrict__ brp, int lane, int4& info,
                                          DF& ad, double& a) {
   const int p = p0 + lane;
   info = make_int4(0, 0, 0, 0);
   a = 0.0;
   if (p < pe) {
-    const int j = acol[p];
+    const int j = A.colind[p];
     info.x = brp[j];
     info.y = brp[j + 1] - info.x;
-    a = aval[p];
+    a = JAC ? a_value(A, i, p) : A.vals[p];
   }
   return df_split(a, ad) ? 0 : 1;
 }
@@ -213,10 +213,10 @@ __device__ __forceinline__ void kept_store_and_run(int4 info, const DF& ad, doub
 // Value pass of a row; returns whether it ran in DF32.  Rows of at most 32 A
 // entries decide the arithmetic from their own split values; longer rows
 // check all their values first.
-template <bool PROBE, bool CHECK>
-__device__ __forceinline__ bool kept_values(int pa, int pe, bool df_all,
-                                            const int32_t* __restrict__ acol,
-                                            const double* __restrict__ aval,
+// JAC: A's values scaled for the Jacobi-fused product (a template switch so the
+// plain product keeps its registers)
+template <bool PROBE, bool CHECK, bool JAC = false>
+__device__ __forceinline__ bool kept_values(int pa, int pe, bool df_all, const CsrView& A, int i,
                                             const int32_t* __restrict__ brp, int4* ainfo, int lo_c,
                                             const unsigned long long* table, unsigned long long* vacc,
                                             const int32_t* __restrict__ bcol,
@@ -224,12 +224,12 @@ __device__ __forceinline__ bool kept_values(int pa, int pe, bool df_all,
                                             const double* __restrict__ bval, int lane, int& missing) {
   df_all = df_all && df_row_terms_ok(pa, pe);
   bool df = df_all;
-  if (df_all && pe - pa > 32) df = row_df_ok<32>(aval, pa, pe, lane, 0xffffffffu);
+  if (df_all && pe - pa > 32) df = row_df_ok<32>(A.vals, pa, pe, lane, 0xffffffffu);
   for (int p0 = pa; p0 < pe; p0 += 32) {
     int4 info;
     DF ad;
     double a;
-    const int bad = kept_info(p0, pe, acol, aval, brp, lane, info, ad, a);
+    const int bad = kept_info<JAC>(p0, pe, A, i, brp, lane, info, ad, a);
     if (df_all && pe - pa <= 32) df = __any_sync(0xffffffffu, bad) == 0;
     kept_store_and_run<PROBE, CHECK>(info, ad, a, df, ainfo, min(32, pe - p0), lo_c, table, vacc, bcol,
                               bspl, bval, lane, missing);

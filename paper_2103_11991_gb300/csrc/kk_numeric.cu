@@ -95,13 +95,13 @@ __global__ void __launch_bounds__(kTeamBlock) k_num_team(NumArgs g) {
     const int pa = g.A.rowptr[i], pe = g.A.rowptr[i + 1];
     const bool df = df_all && df_row_terms_ok(pa, pe) && row_df_ok<TEAM>(g.A.vals, pa, pe, tl, mask);
     if (df) {
-      visit_products<TEAM, FLAT, DF>(pa, pe, 0, 1, tl, mask, rng, PrepDF{g.A.vals},
+      visit_products<TEAM, FLAT, DF>(pa, pe, 0, 1, tl, mask, rng, PrepDF{g.A, i},
                                      [&](DF a, int, int q) {
                                        const int slot = map_slot(keys, bcol[q], LOG2S, status);
                                        if (slot >= 0) upd_df(vals, slot, a, load_b(bspl, q), atomic, status);
                                      });
     } else {
-      visit_products<TEAM, FLAT, double>(pa, pe, 0, 1, tl, mask, rng, PrepF64{g.A.vals},
+      visit_products<TEAM, FLAT, double>(pa, pe, 0, 1, tl, mask, rng, PrepF64{g.A, i},
                                          [&](double a, int, int q) {
                                            const int slot = map_slot(keys, bcol[q], LOG2S, status);
                                            if (slot >= 0) upd_f64(vals, slot, a, bval[q], atomic);
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256, 3) k_num_warp_vec(NumArgs g) {
         const int bs = brp[j];
         info.x = bs;
         info.y = brp[j + 1] - bs;
-        a64 = aval[p];
+        a64 = a_value(g.A, i, p);
         if (df) {
           DF ad;
           bad = df_split(a64, ad) ? 0 : 1;
@@ -492,14 +492,14 @@ __global__ void __launch_bounds__(kCtaBlock) k_num_cta(NumArgs g) {
     const int pa = g.A.rowptr[i], pe = g.A.rowptr[i + 1];
     const bool df = df_all && df_row_terms_ok(pa, pe) && block_df_ok(g.A.vals, pa, pe, &flag);  // syncs
     if (df) {
-      visit_products<32, true, DF>(pa, pe, warp, nwarps, lane, 0xffffffffu, rng, PrepDF{g.A.vals},
+      visit_products<32, true, DF>(pa, pe, warp, nwarps, lane, 0xffffffffu, rng, PrepDF{g.A, i},
                                    [&](DF a, int, int q) {
                                      const int slot = map_slot(keys, bcol[q], LOG2S, status);
                                      if (slot >= 0) upd_df(vals, slot, a, load_b(bspl, q), true, status);
                                    });
     } else {
       visit_products<32, true, double>(pa, pe, warp, nwarps, lane, 0xffffffffu, rng,
-                                       PrepF64{g.A.vals}, [&](double a, int, int q) {
+                                       PrepF64{g.A, i}, [&](double a, int, int q) {
                                          const int slot = map_slot(keys, bcol[q], LOG2S, status);
                                          if (slot >= 0) upd_f64(vals, slot, a, bval[q], true);
                                        });
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(kDenseBlock) k_num_dense(NumArgs g) {
       };
       if (df) {
         visit_products<32, true, DF>(pa, pe, warp, nwarps, lane, 0xffffffffu, rng,
-                                     PrepDF{g.A.vals}, [&](DF a, int, int q) {
+                                     PrepDF{g.A, i}, [&](DF a, int, int q) {
                                        const uint32_t o = (uint32_t)(bcol[q] - c0);
                                        if (o < (uint32_t)W) {
                                          atomicOr(&bits[o >> 5], 1u << (o & 31));
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(kDenseBlock) k_num_dense(NumArgs g) {
                                      });
       } else {
         visit_products<32, true, double>(pa, pe, warp, nwarps, lane, 0xffffffffu, rng,
-                                         PrepF64{g.A.vals}, [&](double a, int, int q) {
+                                         PrepF64{g.A, i}, [&](double a, int, int q) {
                                            const uint32_t o = (uint32_t)(bcol[q] - c0);
                                            if (o < (uint32_t)W) {
                                              atomicOr(&bits[o >> 5], 1u << (o & 31));

@@ -192,9 +192,9 @@ k_onepass_table(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ r
       __syncwarp();
       int missing = 0;
       const bool df =
-          probe ? kept_values<true, true>(pa, pe, df_all, A.colind, A.vals, B.rowptr, ainfo, lo_c, table,
+          probe ? kept_values<true, true>(pa, pe, df_all, A, i, B.rowptr, ainfo, lo_c, table,
                                     vacc, B.colind, bspl, B.vals, lane, missing)
-                : kept_values<false, true>(pa, pe, df_all, A.colind, A.vals, B.rowptr, ainfo, lo_c, table,
+                : kept_values<false, true>(pa, pe, df_all, A, i, B.rowptr, ainfo, lo_c, table,
                                      vacc, B.colind, bspl, B.vals, lane, missing);
       for (int e = lane; e < run; e += 32) {
         const u64 v = vacc[e];

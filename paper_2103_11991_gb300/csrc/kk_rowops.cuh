@@ -20,15 +20,21 @@ struct FullRange {
   }
 };
 
+// A's value at entry p of the row (row i of A; see a_value), as float64 or
+// split into DF32.
 struct PrepF64 {
   const double* av;
-  __device__ __forceinline__ double operator()(int p) const { return av[p]; }
+  ARowScale r;
+  __device__ PrepF64(const CsrView& A, int i) : av(A.vals), r(a_row_scale(A, i)) {}
+  __device__ __forceinline__ double operator()(int p) const { return a_scaled(r, p, av[p]); }
 };
 struct PrepDF {
   const double* av;
+  ARowScale r;
+  __device__ PrepDF(const CsrView& A, int i) : av(A.vals), r(a_row_scale(A, i)) {}
   __device__ __forceinline__ DF operator()(int p) const {
     DF t;
-    df_split(av[p], t);
+    df_split(a_scaled(r, p, av[p]), t);
     return t;
   }
 };

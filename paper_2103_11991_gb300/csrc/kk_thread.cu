@@ -54,12 +54,12 @@ k_sym_thread(CsrView A, CsrView B, const int32_t* __restrict__ rows, int32_t nro
   if (over) set_status(status, KK_ERR_CAPACITY);
 }
 
-template <int N>
+template <int N, bool JAC>
 __global__ void __launch_bounds__(kThreadBlock)
 k_num_thread(CsrView A, CsrView B, const int64_t* __restrict__ c_rowptr,
              const int32_t* __restrict__ rows, int32_t nrows, int32_t* __restrict__ c_colind,
              double* __restrict__ c_vals, int* status) {
-  int over = 0, mismatch = 0;
+  int over = 0, mismatch = 0, bad = 0;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
        r += (long long)gridDim.x * blockDim.x) {
     const int i = rows[r];
@@ -69,9 +69,32 @@ k_num_thread(CsrView A, CsrView B, const int64_t* __restrict__ c_rowptr,
     int key[N];
     double val[N];
     int n = 0;
+    // JAC (a template switch: the plain kernel keeps its registers): the
+    // Jacobi-fused product, A(i,:) taken as s_i A(i,:) plus 1 at the row's first
+    // diagonal entry, s_i = -omega / D(i) with D(i) the sum of the row's stored
+    // diagonal entries in storage order.  The row is short, so a first pass over
+    // it finds D(i); the second pass below reads it again from L1.
+    ARowScale ars{1.0, -1, JAC};
+    if (JAC) {
+      double d = 0.0;
+      int first = -1;
+      for (int p = pa; p < pe; ++p) {
+        if (A.colind[p] == i) {
+          d = first < 0 ? A.vals[p] : d + A.vals[p];
+          first = first < 0 ? p : first;
+        }
+      }
+      if (first < 0 || (__double_as_longlong(d) << 1) == 0) {
+        bad = 1;
+        ars.s = 0.0;
+      } else {
+        ars.s = -A.jac_omega * jacobi_recip(d);
+      }
+      ars.p = first;
+    }
     for (int p = pa; p < pe; ++p) {
       const int j = A.colind[p];
-      const double a = A.vals[p];
+      const double a = JAC ? a_scaled(ars, p, A.vals[p]) : A.vals[p];
       const int be = B.rowptr[j + 1];
       for (int q = B.rowptr[j]; q < be; ++q) {
         const int c = B.colind[q];
@@ -128,6 +151,8 @@ k_num_thread(CsrView A, CsrView B, const int64_t* __restrict__ c_rowptr,
   }
   if (over) set_status(status, KK_ERR_CAPACITY);
   if (mismatch) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
+  // a row without a stored diagonal, or whose diagonal sums to 0
+  if (JAC && bad) set_status(status, KK_ERR_INVALID_ARG);
 }
 
 int thread_grid(const LaunchCtx& ctx, int nrows) {
@@ -154,7 +179,9 @@ cudaError_t launch_numeric_thread(const LaunchCtx& ctx, const CsrView& A, const 
                                   int32_t* c_colind, double* c_vals) {
   if (nrows <= 0) return cudaSuccess;
   timer_begin(ctx.timer, ctx.stream, "num_thread");
-  k_num_thread<kThreadNumMax><<<thread_grid(ctx, nrows), kThreadBlock, 0, ctx.stream>>>(
+  auto kern = A.jac_s != nullptr ? k_num_thread<kThreadNumMax, true>
+                                 : k_num_thread<kThreadNumMax, false>;
+  kern<<<thread_grid(ctx, nrows), kThreadBlock, 0, ctx.stream>>>(
       A, B, c_rowptr, rows, nrows, c_colind, c_vals, ctx.status);
   timer_end(ctx.timer, ctx.stream);
   return cudaGetLastError();

@@ -109,7 +109,7 @@ struct WalkSmem {
 // the column (and with VALS the product a*b in float64).  Ends with a barrier.
 template <bool VALS, class Use>
 __device__ __forceinline__ void wide_walk(const CsrView& A, const CsrView& B, int pa, int pe,
-                                          WalkSmem& ws, int& bad, Use use) {
+                                          WalkSmem& ws, int& bad, Use use, int row = 0) {
   const int lane = threadIdx.x & 31;
   const int32_t* __restrict__ bcol = B.colind;
   const double* __restrict__ bval = B.vals;
@@ -166,7 +166,7 @@ __device__ __forceinline__ void wide_walk(const CsrView& A, const CsrView& B, in
         if (tl >= ns) rel = 0x7fffffff;
         const int bsl = tl < ns ? ws.bst[tl] : 0;
         double al = 0.0;
-        if (VALS && tl < ns) al = A.vals[s0 + tl];
+        if (VALS && tl < ns) al = a_value(A, row, s0 + tl);
         const long long wend = t0 + 32 < ns ? ws.pre[t0 + 32] : total;
         const int lim = (int)min((long long)ilen, wend - fb);
         for (int g = done; g < lim; g += 32 * kWideU) {
@@ -295,7 +295,7 @@ struct LongSmem {
 template <bool VALS, class Use>
 __device__ __forceinline__ void wide_walk_long(const CsrView& A, const CsrView& B, int pa, int pe,
                                                LongSmem& ls, int& bad, Use use, StageState* st = nullptr,
-                                               int* status = nullptr) {
+                                               int* status = nullptr, int row = 0) {
   const int lane = threadIdx.x & 31;
   const int32_t* __restrict__ bcol = B.colind;
   const double* __restrict__ bval = B.vals;
@@ -349,7 +349,7 @@ __device__ __forceinline__ void wide_walk_long(const CsrView& A, const CsrView& 
         stage_walk(B, *st, q0, n, status, [&](int c) { use(c, 0.0); });
         continue;
       }
-      const double a = VALS ? A.vals[s0 + t] : 0.0;
+      const double a = VALS ? a_value(A, row, s0 + t) : 0.0;
       for (int g = 0; g < n; g += 32 * kWideU) {
         int col[kWideU];
         double ab[kWideU];
@@ -634,8 +634,8 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
         }
       }
     };
-    if (lng) wide_walk_long<true>(A, B, pa, pe, walk.ls, bad, add);
-    else wide_walk<true>(A, B, pa, pe, walk.ws, bad, add);
+    if (lng) wide_walk_long<true>(A, B, pa, pe, walk.ls, bad, add, nullptr, nullptr, i);
+    else wide_walk<true>(A, B, pa, pe, walk.ws, bad, add, i);
     if (sparse) {
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) c_vals[off + e] = vals[e];
     }

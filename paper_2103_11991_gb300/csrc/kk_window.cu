@@ -81,6 +81,8 @@ __device__ __forceinline__ void bc_bounds(int p, int pe, const int32_t* __restri
   }
 }
 
+// (Numeric phases: a pair outside the window means B's structure is not the
+// one the symbolic phase sized the window for: KK_ERR_STRUCTURE_MISMATCH.)
 // OR the compressed rows B_C(j,:) of the entries [pa, pe) of A(i,:) into the
 // window whose word 0 is column word lo_w, and the word's summary bit.  Lanes
 // take the pairs of 32 / G A entries at a time, G the power of two that covers
@@ -152,7 +154,7 @@ __device__ __forceinline__ void bc_set_bits(uint32_t* bits, uint32_t* sum, int l
       }
     }
   }
-  if (bad) set_status(status, KK_ERR_CAPACITY);
+  if (bad) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
   __syncwarp();
 }
 
@@ -529,7 +531,7 @@ k_num_window(CsrView A, CsrView B, BComp bcomp, WinCacheView cache,
         const int j = acol[p];
         info.x = brp[j];
         info.y = brp[j + 1] - info.x;
-        a = aval[p];
+        a = a_value(A, i, p);
       }
       DF ad;
       const int split_bad = df_row ? (df_split(a, ad) ? 0 : 1) : 1;
@@ -652,8 +654,7 @@ __device__ __forceinline__ void df_add(DF& s, const DF b) {
 // pairs when df, else float64 in storage order; ranks from the window's bits
 // and prefix counts.  One warp.
 template <int WORDS, int VMAX>
-__device__ __forceinline__ void window_values(int p_lo, int p_hi, bool df, const int32_t* __restrict__ acol,
-                                              const double* __restrict__ aval,
+__device__ __forceinline__ void window_values(int p_lo, int p_hi, bool df, const CsrView& A, int i,
                                               const int32_t* __restrict__ brp,
                                               const int32_t* __restrict__ bcol,
                                               const float2* __restrict__ bspl,
@@ -665,10 +666,10 @@ __device__ __forceinline__ void window_values(int p_lo, int p_hi, bool df, const
     int4 info = make_int4(0, 0, 0, 0);
     double a = 0.0;
     if (p < p_hi) {
-      const int j = acol[p];
+      const int j = A.colind[p];
       info.x = brp[j];
       info.y = brp[j + 1] - info.x;
-      a = aval[p];
+      a = a_value(A, i, p);
     }
     if (df) {
       DF ad;
@@ -885,10 +886,10 @@ k_num_window_cta(CsrView A, CsrView B, BComp bcomp, const int32_t* __restrict__ 
     const bool df = df_all && df_row_terms_ok(pa, pe) && row_df_ok<32>(aval, pa, pe, lane, kFull);
     int missing = 0;
     if (df)
-      window_values<WORDS, VMAX>(p_lo, p_hi, true, acol, aval, B.rowptr, B.colind, bspl, B.vals, bits, pre,
+      window_values<WORDS, VMAX>(p_lo, p_hi, true, A, i, B.rowptr, B.colind, bspl, B.vals, bits, pre,
                                  lo_c, vacc, ainfo, lane, missing);
     else if (warp == 0)
-      window_values<WORDS, VMAX>(pa, pe, false, acol, aval, B.rowptr, B.colind, bspl, B.vals, bits, pre,
+      window_values<WORDS, VMAX>(pa, pe, false, A, i, B.rowptr, B.colind, bspl, B.vals, bits, pre,
                                  lo_c, vacc, ainfo, lane, missing);
     if (missing) set_status(status, KK_ERR_STRUCTURE_MISMATCH);
     __syncthreads();

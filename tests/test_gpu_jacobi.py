@@ -129,9 +129,31 @@ def test_jacobi_errors():
                       A.colind[keep], A.vals[keep])
     Bi = I.identity(6)
     dA, dB = K.DeviceCSR.from_host(A2), K.DeviceCSR.from_host(Bi)
-    with K.SpGEMM() as op:
-        rp, nnz = op.symbolic(dA, dB)
-        with pytest.raises(K.KKError) as e:
-            op.jacobi_numeric(dA, dB, rp, nnz, 0.5)
-            op.sync()
-        assert e.value.status == 1
+    # automatic tiers (the thread tier finds the row's diagonal itself) and each
+    # forced tier (the row-scale kernel finds it)
+    for tier in (-1, 0, 1, 2, 3):
+        with K.SpGEMM(force_tier=tier) as op:
+            rp, nnz = op.symbolic(dA, dB)
+            with pytest.raises(K.KKError) as e:
+                op.jacobi_numeric(dA, dB, rp, nnz, 0.5)
+                op.sync()
+            assert e.value.status == 1, tier
+    # a diagonal that sums to zero (two stored entries cancel)
+    rows = np.repeat(np.arange(6), np.diff(A.rowptr))
+    cols = A.colind.copy()
+    vals = A.vals.copy()
+    d3 = int(np.nonzero((rows == 3) & (cols == 3))[0][0])
+    rows = np.concatenate([rows, [3]])
+    cols = np.concatenate([cols, [3]])
+    vals = np.concatenate([vals, [-vals[d3]]])
+    order = np.argsort(rows, kind="stable")
+    A3 = I.ensure_csr(6, 6, np.concatenate(([0], np.cumsum(np.bincount(rows, minlength=6)))),
+                      cols[order], vals[order])
+    dA = K.DeviceCSR.from_host(A3)
+    for tier in (-1, 0):
+        with K.SpGEMM(force_tier=tier) as op:
+            rp, nnz = op.symbolic(dA, dB)
+            with pytest.raises(K.KKError) as e:
+                op.jacobi_numeric(dA, dB, rp, nnz, 0.5)
+                op.sync()
+            assert e.value.status == 1, tier
