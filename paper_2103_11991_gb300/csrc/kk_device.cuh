@@ -283,6 +283,46 @@ __device__ __forceinline__ void df_atomic_fma(unsigned long long* slot, const DF
   set_status(status, KK_ERR_TIMEOUT);
 }
 
+// Position (0..31) of the k-th (0-based) set bit of m, k < popc(m): a binary
+// search on the popcounts of the word's halves, quarters, ...
+__device__ __forceinline__ int select_set_bit(uint32_t m, int k) {
+  int pos = 0, c;
+  c = __popc(m & 0xFFFFu);
+  if (k >= c) { k -= c; pos += 16; m >>= 16; }
+  c = __popc(m & 0xFFu);
+  if (k >= c) { k -= c; pos += 8; m >>= 8; }
+  c = __popc(m & 0xFu);
+  if (k >= c) { k -= c; pos += 4; m >>= 4; }
+  c = __popc(m & 0x3u);
+  if (k >= c) { k -= c; pos += 2; m >>= 2; }
+  if (k >= (int)(m & 1u)) pos += 1;
+  return pos;
+}
+
+// The columns of a warp's 32 bit-vector words in ascending order, written by
+// consecutive lanes to consecutive entries (coalesced stores, whatever the
+// words' popcounts): lane l holds word index w and bits m, incl = the
+// inclusive scan of the popcounts over the lanes, total = incl of lane 31.
+// write(e, col) is called for the e-th column, e < total.  All 32 lanes call.
+template <class Write>
+__device__ __forceinline__ void warp_expand_bits(int w, uint32_t m, int incl, int total, Write write) {
+  const int lane = threadIdx.x & 31;
+  for (int e0 = 0; e0 < total; e0 += 32) {
+    const int e = e0 + lane;
+    // source lane: the number of lanes whose inclusive count is <= e
+    int src = 0;
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1) {
+      const int v = __shfl_sync(0xffffffffu, incl, src + st - 1);
+      if (v <= e) src += st;
+    }
+    const uint32_t mm = __shfl_sync(0xffffffffu, m, src);
+    const int ws = __shfl_sync(0xffffffffu, w, src);
+    const int start = __shfl_sync(0xffffffffu, incl, src) - __popc(mm);
+    if (e < total) write(e, ws * 32 + select_set_bit(mm, e - start));
+  }
+}
+
 // Jacobi-fused product's 1/D(i) to about one unit in the last place without
 // the float64 divide (a long sequence on the FP64 pipe, which is slow on this
 // part): a float32 reciprocal

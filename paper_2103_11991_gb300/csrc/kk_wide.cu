@@ -31,6 +31,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWideU = 4;      // warp steps whose loads are issued together
 constexpr int kWideBlock = 1024;
+constexpr int kKeepU = 4;      // 16-byte loads in flight per thread when a kept bit vector is loaded
 
 // Words of the column bit vector: ceil(k / 32) rounded up to a multiple of
 // 1024 (one run of 32 words per lane of every warp of the CTA).
@@ -278,11 +279,13 @@ __device__ __forceinline__ void stage_walk(const CsrView& B, StageState& st, int
 }
 
 // Walk for rows whose B rows are long (mean length >= kLongMean): work items
-// are the row's A entries cut into pieces of at most kPiece products; a warp
+// are the row's A entries cut into pieces of at most psz products (sized per
+// row by wide_piece so that every warp gets several; with one or two items per
+// warp the row's closing barrier waited for the largest piece); a warp
 // claims an item from a shared counter, finds its entry by a 32-ary search over
 // the item prefix (once per item, not per product) and its lanes stride the
 // piece's B entries, kWideU loads in flight.  Same contract as wide_walk.
-constexpr int kPiece = 2048;
+constexpr int kPieceMin = 256, kPieceMax = 2048;
 constexpr long long kLongMean = 64;
 struct LongSmem {
   int ipre[kSeg + 1];
@@ -294,7 +297,7 @@ struct LongSmem {
 
 template <bool VALS, class Use>
 __device__ __forceinline__ void wide_walk_long(const CsrView& A, const CsrView& B, int pa, int pe,
-                                               LongSmem& ls, int& bad, Use use, StageState* st = nullptr,
+                                               LongSmem& ls, int psz, int& bad, Use use, StageState* st = nullptr,
                                                int* status = nullptr, int row = 0) {
   const int lane = threadIdx.x & 31;
   const int32_t* __restrict__ bcol = B.colind;
@@ -314,7 +317,7 @@ __device__ __forceinline__ void wide_walk_long(const CsrView& A, const CsrView& 
         }
       }
       int total;
-      const int ex = block_exscan<int>((len + kPiece - 1) / kPiece, ls.tmp, &total);
+      const int ex = block_exscan<int>((len + psz - 1) / psz, ls.tmp, &total);
       ls.ipre[t] = ex;
       ls.bst[t] = bs;
       ls.blen[t] = len;
@@ -343,8 +346,8 @@ __device__ __forceinline__ void wide_walk_long(const CsrView& A, const CsrView& 
       }
       const int t = lo;
       const int piece = it - ls.ipre[t];
-      const int q0 = ls.bst[t] + piece * kPiece;
-      const int n = min(kPiece, ls.blen[t] - piece * kPiece);
+      const int q0 = ls.bst[t] + piece * psz;
+      const int n = min(psz, ls.blen[t] - piece * psz);
       if (!VALS && st != nullptr && st->ok && n >= 2 * kStageCols) {
         stage_walk(B, *st, q0, n, status, [&](int c) { use(c, 0.0); });
         continue;
@@ -371,22 +374,27 @@ __device__ __forceinline__ void wide_walk_long(const CsrView& A, const CsrView& 
   }
 }
 
-// OR the column bits of the products of A entries [pa, pe) into bits (and,
-// with SUM, the summary bits of their words).  Ends with a barrier.
 // The two walks' shared state (never used at the same time).
 union WideWalkSmem {
   WalkSmem ws;
   LongSmem ls;
 };
 
-// Mean B-row length of row i's A entries decides the walk.
-__device__ __forceinline__ bool wide_long_rows(const long long* flop, int i, int pa, int pe) {
-  return flop != nullptr && pe > pa && flop[i] >= kLongMean * (long long)(pe - pa);
+// Walk of row i: 0 for the flattened walk, else the piece size of the
+// entry-piece walk.  The mean B-row length of the row's A entries decides the
+// walk; the pieces spread the row's products over about eight items per warp
+// of the CTA, kPieceMin .. kPieceMax products each.
+__device__ __forceinline__ int wide_piece(const long long* flop, int i, int pa, int pe) {
+  if (flop == nullptr || pe <= pa || flop[i] < kLongMean * (long long)(pe - pa)) return 0;
+  const long long per = flop[i] / (kWideBlock / 32 * 8);
+  return per <= kPieceMin ? kPieceMin : per >= kPieceMax ? kPieceMax : (int)per;
 }
 
+// OR the column bits of the products of A entries [pa, pe) into bits (and,
+// with SUM, the summary bits of their words).  Ends with a barrier.
 template <bool SUM>
 __device__ __forceinline__ void wide_set_bits(const CsrView& A, const CsrView& B, int pa, int pe,
-                                              bool long_rows, WideWalkSmem& wsm, uint32_t* bits,
+                                              int psz, WideWalkSmem& wsm, uint32_t* bits,
                                               uint32_t* sum, int words, int& bad, StageState* st = nullptr,
                                               int* status = nullptr) {
   auto set = [&](int c, double) {
@@ -399,7 +407,7 @@ __device__ __forceinline__ void wide_set_bits(const CsrView& A, const CsrView& B
       }
     }
   };
-  if (long_rows) wide_walk_long<false>(A, B, pa, pe, wsm.ls, bad, set, st, status);
+  if (psz > 0) wide_walk_long<false>(A, B, pa, pe, wsm.ls, psz, bad, set, st, status);
   else wide_walk<false>(A, B, pa, pe, wsm.ws, bad, set);
 }
 
@@ -435,7 +443,7 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, uint32_t stage
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int i = rows[r];
     const bool sparse = flop[i] < (long long)words;  // few words touched: walk the summary
-    const bool lng = wide_long_rows(flop, i, A.rowptr[i], A.rowptr[i + 1]);
+    const int lng = wide_piece(flop, i, A.rowptr[i], A.rowptr[i + 1]);
     int c = 0;
     if (sparse) {
       // few words touched: count and clear them through the summary (such rows
@@ -492,6 +500,90 @@ k_sym_wide(CsrView A, CsrView B, int32_t words, uint32_t sum_off, uint32_t stage
   if (bad) set_status(status, KK_ERR_BAD_INDEX);
 }
 
+// Rank tables of a row whose values go to C (rank of column c = gpre[c >> 8]
+// + wpre8[c >> 5] + the popcount of its word's bits below c), from one block
+// scan: thread t owns the wpt consecutive words [t * wpt, (t + 1) * wpt),
+// wpt in {8, 16, 32}, and visits its 16-byte pieces in the lane-rotated order
+// q = k ^ (lane & (wpt / 4 - 1)), so that a warp's loads spread over the
+// shared-memory banks.  Pass 1 sums the popcounts of the thread's 8-word
+// groups, the block scan gives the thread's base (and *total, the row's
+// count), pass 2 writes each group's prefix and each word's offset in its
+// group (at most 7 * 32, a byte).  Ends with the scan's barrier behind it; the
+// caller synchronises before the tables are read.
+__device__ __forceinline__ void wide_prefix_owned(const uint32_t* bits, uint32_t* gpre, uint8_t* wpre8, int wpt,
+                                                  int* tmp, int* total) {
+  const int t = threadIdx.x;
+  const int nq = wpt >> 2;  // 16-byte pieces per thread: 2, 4 or 8
+  const int sw = (t & 31) & (nq - 1);
+  const uint4* b4 = reinterpret_cast<const uint4*>(bits) + (size_t)t * nq;
+  int gs0 = 0, gs1 = 0, gs2 = 0, gs3 = 0;  // the thread's group popcounts (nq / 2 <= 4 groups)
+  for (int k = 0; k < nq; ++k) {
+    const int q = k ^ sw;
+    const uint4 v = b4[q];
+    const int p = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+    const int g = q >> 1;
+    gs0 += g == 0 ? p : 0;
+    gs1 += g == 1 ? p : 0;
+    gs2 += g == 2 ? p : 0;
+    gs3 += g == 3 ? p : 0;
+  }
+  const int base = block_exscan<int>(gs0 + gs1 + gs2 + gs3, tmp, total);
+  const int ng = nq >> 1;
+  uint32_t* gp = gpre + (size_t)t * ng;
+  gp[0] = (uint32_t)base;
+  if (ng > 1) gp[1] = (uint32_t)(base + gs0);
+  if (ng > 2) {
+    gp[2] = (uint32_t)(base + gs0 + gs1);
+    gp[3] = (uint32_t)(base + gs0 + gs1 + gs2);
+  }
+  uint32_t* w8 = reinterpret_cast<uint32_t*>(wpre8) + (size_t)t * nq;
+  for (int k = 0; k < nq; ++k) {
+    const int q = k ^ sw;
+    const uint4 v = b4[q];
+    int o = 0;
+    if (q & 1) {  // second piece of its group: after the first piece's columns
+      const uint4 e = b4[q ^ 1];
+      o = __popc(e.x) + __popc(e.y) + __popc(e.z) + __popc(e.w);
+    }
+    const int o1 = o + __popc(v.x), o2 = o1 + __popc(v.y), o3 = o2 + __popc(v.z);
+    w8[q] = (uint32_t)o | ((uint32_t)o1 << 8) | ((uint32_t)o2 << 16) | ((uint32_t)o3 << 24);
+  }
+}
+
+// C's columns of a row from its bit vector and rank tables, written to
+// out[0..cnt): the row's words in rounds of 32 consecutive words that warps
+// claim from the shared counter *next (dense rounds cost more; claiming
+// balances them across the warps, where fixed word ranges left the warps
+// holding a row's dense columns behind).  In a round lane l holds word
+// 32 r + l and its rank from the tables; a round whose words hold at most one
+// column each is written by the lanes directly (consecutive entries), any
+// other by the warp-cooperative expansion.
+__device__ __forceinline__ void wide_write_columns(const uint32_t* bits, const uint32_t* gpre, const uint8_t* wpre8,
+                                                   int words, int cnt, int32_t* __restrict__ out, int* next) {
+  const int lane = threadIdx.x & 31;
+  const int nr = words >> 5;
+  for (;;) {
+    int r = 0;
+    if (lane == 0) r = atomicAdd(next, 1);
+    r = __shfl_sync(kFull, r, 0);
+    if (r >= nr) break;
+    const int w = r * 32 + lane;
+    const uint32_t m = bits[w];
+    const int pos = (int)gpre[w >> 3] + (int)wpre8[w];
+    const int c = __popc(m);
+    if (__all_sync(kFull, c <= 1)) {
+      if (c != 0 && pos < cnt) out[pos] = w * 32 + (__ffs(m) - 1);
+    } else {
+      const int p0 = __shfl_sync(kFull, pos, 0);
+      const int incl = pos - p0 + c;
+      const int rtot = __shfl_sync(kFull, incl, 31);
+      warp_expand_bits(w, m, incl, rtot, [&](int e, int col) {
+        if (p0 + e < cnt) out[p0 + e] = col;
+      });
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kWideBlock, 1)
 k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, uint32_t reg_off,
            uint32_t val_off, const int64_t* __restrict__ c_rowptr, const long long* __restrict__ flop,
@@ -507,6 +599,7 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
   uint16_t* list = reinterpret_cast<uint16_t*>(wsm + val_off);
   __shared__ WideWalkSmem walk;
   __shared__ int tmp[33];
+  __shared__ int col_next;
   const int nsum = words >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps_blk = blockDim.x >> 5;
@@ -520,7 +613,7 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
     const int pa = A.rowptr[i], pe = A.rowptr[i + 1];
     const int64_t off = c_rowptr[i];
     const int cnt = (int)(c_rowptr[i + 1] - off);
-    const bool lng = wide_long_rows(flop, i, pa, pe);
+    const int lng = wide_piece(flop, i, pa, pe);
     // values in shared memory (and the word list in their place) when the row fits
     const bool sparse = cnt <= vcap && cnt <= 65535;
     bool row_bad = false;
@@ -576,40 +669,65 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
     } else {
       const int sl = keep.max_slots > 0 ? keep.slot[i] : -1;
       if (sl >= 0) {  // the symbolic phase kept this row's bits
-        const uint32_t* src = keep.bits + (size_t)sl * words;
-        for (int w = threadIdx.x * 4; w < words; w += blockDim.x * 4)
-          *reinterpret_cast<uint4*>(&bits[w]) = *reinterpret_cast<const uint4*>(&src[w]);
+        // kKeepU 16-byte pieces per thread in flight at once; read once, so
+        // streamed past L2
+        const uint4* src = reinterpret_cast<const uint4*>(keep.bits + (size_t)sl * words);
+        uint4* dst4 = reinterpret_cast<uint4*>(bits);
+        const int n4 = words >> 2;
+        for (int v0 = threadIdx.x; v0 < n4; v0 += blockDim.x * kKeepU) {
+          uint4 t[kKeepU];
+#pragma unroll
+          for (int u = 0; u < kKeepU; ++u) {
+            const int v = v0 + u * blockDim.x;
+            if (v < n4) t[u] = __ldcs(&src[v]);
+          }
+#pragma unroll
+          for (int u = 0; u < kKeepU; ++u) {
+            const int v = v0 + u * blockDim.x;
+            if (v < n4) dst4[v] = t[u];
+          }
+        }
         __syncthreads();
       } else {
         wide_set_bits<false>(A, B, pa, pe, lng, walk, bits, sum, words, bad);
       }
-      // Each warp owns a contiguous range of words, its lanes consecutive
-      // words in it (conflict-free shared loads, and consecutive lanes write
-      // consecutive columns of C): a warp sum, the block scan of the warp
-      // sums, then per round of 32 words a warp scan gives every word its
-      // prefix, kept as a u32 per 8-word group plus a byte per word.
       const int wpw = words / nwarps_blk;  // words per warp (words is a multiple of 32 * 32)
       const int w0 = warp * wpw;
-      int mine = 0;
-      for (int j = lane; j < wpw; j += 32) mine += __popc(bits[w0 + j]);
-      mine = team_sum<32>(mine, kFull);
-      int run = block_exscan<int>(lane == 0 ? mine : 0, tmp, &total);
-      run = __shfl_sync(kFull, run, 0);
-      for (int j0 = 0; j0 < wpw; j0 += 32) {
-        const int w = w0 + j0 + lane;
-        uint32_t m = bits[w];
-        const int c = __popc(m);
-        const int incl = team_inclusive_scan<32>(c, lane, kFull);
-        int pos = run + incl - c;
-        run += __shfl_sync(kFull, incl, 31);
-        const int gbase = __shfl_sync(kFull, pos, lane & ~7);
-        if ((lane & 7) == 0) gpre[w >> 3] = (uint32_t)pos;
-        wpre8[w] = (uint8_t)(pos - gbase);
-        while (m) {
-          const int b = __ffs(m) - 1;
-          m &= m - 1;
-          if (pos < cnt) c_colind[off + pos] = w * 32 + b;
-          ++pos;
+      const int wpt = words / (int)blockDim.x;
+      if (wpt == 8 || wpt == 16 || wpt == 32) {
+        // prefixes from one block scan over threads owning consecutive words
+        if (threadIdx.x == 0) col_next = 0;  // read after the scan's barriers
+        wide_prefix_owned(bits, gpre, wpre8, wpt, tmp, &total);
+        __syncthreads();
+        // C's columns: rounds of 32 words claimed by the warps
+        wide_write_columns(bits, gpre, wpre8, words, cnt, c_colind + off, &col_next);
+      } else {
+        // Each warp owns a contiguous range of words, its lanes consecutive
+        // words in it (conflict-free shared loads, and consecutive lanes write
+        // consecutive columns of C): a warp sum, the block scan of the warp
+        // sums, then per round of 32 words a warp scan gives every word its
+        // prefix, kept as a u32 per 8-word group plus a byte per word.
+        int mine = 0;
+        for (int j = lane; j < wpw; j += 32) mine += __popc(bits[w0 + j]);
+        mine = team_sum<32>(mine, kFull);
+        int run = block_exscan<int>(lane == 0 ? mine : 0, tmp, &total);
+        run = __shfl_sync(kFull, run, 0);
+        for (int j0 = 0; j0 < wpw; j0 += 32) {
+          const int w = w0 + j0 + lane;
+          uint32_t m = bits[w];
+          const int c = __popc(m);
+          const int incl = team_inclusive_scan<32>(c, lane, kFull);
+          int pos = run + incl - c;
+          run += __shfl_sync(kFull, incl, 31);
+          const int gbase = __shfl_sync(kFull, pos, lane & ~7);
+          if ((lane & 7) == 0) gpre[w >> 3] = (uint32_t)pos;
+          wpre8[w] = (uint8_t)(pos - gbase);
+          while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            if (pos < cnt) c_colind[off + pos] = w * 32 + b;
+            ++pos;
+          }
         }
       }
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) c_vals[off + e] = 0.0;
@@ -634,7 +752,7 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
         }
       }
     };
-    if (lng) wide_walk_long<true>(A, B, pa, pe, walk.ls, bad, add, nullptr, nullptr, i);
+    if (lng) wide_walk_long<true>(A, B, pa, pe, walk.ls, lng, bad, add, nullptr, nullptr, i);
     else wide_walk<true>(A, B, pa, pe, walk.ws, bad, add, i);
     if (sparse) {
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) c_vals[off + e] = vals[e];

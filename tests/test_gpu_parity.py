@@ -315,3 +315,22 @@ def test_wide_rows_beyond_shared_values(seed, stage):
     ref = check_against_oracle(A, B, rp_, ci, va)
     assert np.diff(ref.rowptr).max() > 20000
     assert st["num_dense_rows"] + st["num_cta_rows"] > 0
+@pytest.mark.parametrize("kbits", [18, 19])
+def test_wide_rows_beyond_shared_values_narrower_k(kbits):
+    """The same wide-tier rows with k = 2^18 and 2^19 columns: 8 and 16
+    bit-vector words per thread of the numeric kernel's rank tables (2^20 gives
+    32), rows from 15,000 columns to more than half of k."""
+    k = 1 << kbits
+    n = 3000
+    B = I.random_rows(n, k, 600, 2600, seed=160 + kbits)
+    A1 = I.random_rows(24, n, 10, 30, seed=170 + kbits)
+    A2 = I.random_rows(4, n, 1100, 1300, seed=180 + kbits)
+    rp = np.concatenate([A1.rowptr, A1.rowptr[-1] + A2.rowptr[1:]]).astype(np.int64)
+    A = I.CSR(28, n, rp, np.concatenate([A1.colind, A2.colind]),
+              I.uniform01(kbits, "wide.a", int(rp[-1])) * 2 - 1)
+    rp_, ci, va, _, st = run_gpu(A, B)
+    ref = check_against_oracle(A, B, rp_, ci, va)
+    assert np.diff(ref.rowptr).max() > k // 2
+    assert st["num_dense_rows"] + st["num_cta_rows"] > 0
+
+
