@@ -173,16 +173,17 @@ __device__ __forceinline__ uint8_t classify(const BinTable& t, long long q, int 
 // One team of T lanes per row.  The kernel is bound by its dependent gathers
 // (A column -> B row bounds -> B's first and last column), so each lane issues
 // those of U entries together and the next row's bounds are loaded while a row
-// is processed; T and U follow A's mean row length.
-template <int T, int U>
+// is processed; T and U follow A's mean row length.  STATS (the learned
+// form): also the longest and shortest referenced B row of each row, to stat.
+template <int T, int U, bool STATS>
 __global__ void __launch_bounds__(256, 6)
 k_analyze_a(CsrView A, const int32_t* __restrict__ brp,
                             const int32_t* __restrict__ bcol, int32_t nb_rows,
                             const int32_t* __restrict__ b_sorted, BinTable tab,
                             int32_t vec_min_len, long long* __restrict__ flop,
                             uint8_t* __restrict__ bin, int32_t* __restrict__ row_lo,
-                            int32_t* __restrict__ row_span, unsigned long long* total_flop,
-                            int* status) {
+                            int32_t* __restrict__ row_span, int2* __restrict__ stat,
+                            unsigned long long* total_flop, int* status) {
   const int sorted = *b_sorted;
   const int tl = threadIdx.x % T;
   const unsigned mask = team_mask<T>();
@@ -205,6 +206,7 @@ k_analyze_a(CsrView A, const int32_t* __restrict__ brp,
     long long f = 0;
     int bad = 0;
     int lo = 0x7fffffff, hi = -1;
+    int mx = 0, mn = 0x7fffffff;
     if (r < A.m) {
       if (pa < 0 || pe < pa || pe > A.nnz || (r == 0 && pa != 0)) {
         bad = 1;
@@ -233,6 +235,10 @@ k_analyze_a(CsrView A, const int32_t* __restrict__ brp,
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           f += be[u] - bs[u];
+          if (STATS && j[u] >= 0) {
+            mx = max(mx, be[u] - bs[u]);
+            mn = min(mn, be[u] - bs[u]);
+          }
           if (sorted && be[u] > bs[u]) {
             lo = min(lo, bcol[bs[u]]);
             hi = max(hi, bcol[be[u] - 1]);
@@ -245,6 +251,10 @@ k_analyze_a(CsrView A, const int32_t* __restrict__ brp,
       f += __shfl_xor_sync(mask, f, o, T);
       lo = min(lo, __shfl_xor_sync(mask, lo, o, T));
       hi = max(hi, __shfl_xor_sync(mask, hi, o, T));
+      if (STATS) {
+        mx = max(mx, __shfl_xor_sync(mask, mx, o, T));
+        mn = min(mn, __shfl_xor_sync(mask, mn, o, T));
+      }
     }
     if (bad) set_status(status, KK_ERR_BAD_INDEX);
     if (r < A.m && tl == 0) {
@@ -255,6 +265,7 @@ k_analyze_a(CsrView A, const int32_t* __restrict__ brp,
       row_span[r] = sp;
       const int flat = (f < (long long)vec_min_len * (pe - pa)) ? 1 : 0;
       bin[r] = classify(tab, f, flat, sp, f, sorted);
+      if (STATS) stat[r] = make_int2(mx, pe > pa ? mn : 0);
       acc += (unsigned long long)f;
     }
   }
@@ -474,20 +485,6 @@ k_scan_final(int32_t m, const int32_t* __restrict__ cnt, const long long* __rest
 
 // Symbolic bin of every row from its flop bound and span (learned form: the
 // rows left to the plain path are picked from these afterwards).
-__global__ void k_sym_classify(int32_t m, const long long* __restrict__ flop,
-                               const int32_t* __restrict__ arp, const int32_t* __restrict__ row_span,
-                               const int32_t* __restrict__ b_sorted, BinTable tab,
-                               int32_t vec_min_len, uint8_t* __restrict__ bin) {
-  const int sorted = *b_sorted;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < m;
-       r += (long long)gridDim.x * blockDim.x) {
-    const long long f = flop[r];
-    const int nza = arp[r + 1] - arp[r];
-    const int flat = (f < (long long)vec_min_len * nza) ? 1 : 0;
-    bin[r] = classify(tab, f, flat, row_span[r], f, sorted);
-  }
-}
-
 // Per numeric tier: C entries and A entries of the rows binned to it (for the
 // per-kernel roofline accounting).
 struct TierOfBin {
@@ -771,6 +768,7 @@ struct kk_spgemm_handle_s {
   DevBuf d_lbin;       // uint8[m]  learned bin (one-pass class / heavy / none)
   DevBuf d_plain;      // uint8[m]  1 = row takes the plain path
   DevBuf d_cap;        // int32[m]  staging capacity
+  DevBuf d_lstat;      // int2[m]   learned form: longest / shortest referenced B row
   DevBuf d_soff;       // int64[m+1] staging offsets
   DevBuf d_scol;       // int32[staging]
   DevBuf d_sval;       // double[staging]
@@ -1236,20 +1234,22 @@ static cudaError_t launch_jacobi_rows(kk_spgemm_handle h, const CsrView& av, con
 
 // Analysis of A with teams of T lanes, one resident wave of blocks (the kernel
 // strides over rows).
-template <int T, int U>
+// bin receives the symbolic bin ids; with STATS, stat the learned form's row
+// statistics.
+template <int T, int U, bool STATS = false>
 static void launch_analyze_a(kk_spgemm_handle h, const CsrView& av, const CsrView& bv, Misc* dm,
-                             cudaStream_t s) {
+                             cudaStream_t s, uint8_t* bin, int2* stat = nullptr) {
   static int per_sm = 0;
   if (per_sm == 0 &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_analyze_a<T, U>, 256, 0) != cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_analyze_a<T, U, STATS>, 256, 0) != cudaSuccess) {
     (void)cudaGetLastError();
     per_sm = 4;
   }
   const int64_t m = av.m;
-  k_analyze_a<T, U><<<grid_for(m * T, 256, h->num_sms * (per_sm > 0 ? per_sm : 1)), 256, 0, s>>>(
+  k_analyze_a<T, U, STATS><<<grid_for(m * T, 256, h->num_sms * (per_sm > 0 ? per_sm : 1)), 256, 0, s>>>(
       av, bv.rowptr, bv.colind, bv.m, &dm->sorted, to_table(h->sym_bins), h->opt.team_vec_min_len,
-      h->d_flop.as<long long>(), h->d_sbin.as<uint8_t>(), h->d_rowlo.as<int32_t>(),
-      h->d_span.as<int32_t>(), &dm->total_flop, &dm->status);
+      h->d_flop.as<long long>(), bin, h->d_rowlo.as<int32_t>(), h->d_span.as<int32_t>(), stat,
+      &dm->total_flop, &dm->status);
 }
 
 extern "C" {
@@ -1396,9 +1396,9 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
     // round (more rows in flight per SM; measured against teams of 4 and 8)
     const long long avg = m > 0 ? (long long)av.nnz / m : 0;
     if (avg <= 8)
-      launch_analyze_a<1, 8>(h, av, bv, dm, s);
+      launch_analyze_a<1, 8>(h, av, bv, dm, s, h->d_sbin.as<uint8_t>());
     else
-      launch_analyze_a<4, 8>(h, av, bv, dm, s);
+      launch_analyze_a<4, 8>(h, av, bv, dm, s, h->d_sbin.as<uint8_t>());
     timer_end(h->timer, s);
     KK_CUDA(h, cudaGetLastError(), "analyze launch");
     if ((st = run_binning(h, m, h->d_sbin.as<uint8_t>(), nbs, h->d_srows.as<int32_t>(), sym_start)) != KK_OK)
@@ -1777,6 +1777,7 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
                     &h->d_lrows, &h->d_lrows2})
     KK_CUDA(h, b->ensure(sizeof(int32_t) * mm1), "alloc rows");
   KK_CUDA(h, h->d_flop.ensure(sizeof(long long) * mm1), "alloc flop");
+  KK_CUDA(h, h->d_lstat.ensure(sizeof(int2) * mm1), "alloc row statistics");
   KK_CUDA(h, h->d_soff.ensure(sizeof(int64_t) * (mm1 + 1)), "alloc staging offsets");
   KK_CUDA(h, h->d_binstart.ensure(sizeof(int32_t) * 4 * (kMaxBins + 1)), "alloc bins");
   int32_t* sym_start = h->d_binstart.as<int32_t>();
@@ -1789,12 +1790,22 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
   KK_CUDA(h, cudaMemcpyAsync(dm, &init, sizeof(Misc), cudaMemcpyHostToDevice, s), "init");
   LaunchCtx ctx = ctx_of(h);
   if (m > 0) {
+    timer_begin(h->timer, s, "analyze");
     if ((st = analyze_b(h, bv)) != KK_OK) return st;
-    cudaError_t e = launch_learned_analyze(
-        ctx, av, bv, &dm->sorted, h->opt.use_window, h->have_pred ? h->d_params.as<float>() : nullptr,
-        h->quantile,
-        h->have_pred ? 1 : 0, h->d_flop.as<long long>(), h->d_rowlo.as<int32_t>(),
-        h->d_span.as<int32_t>(), h->d_lbin.as<uint8_t>(), h->d_cap.as<int32_t>(), &dm->total_flop);
+    timer_end(h->timer, s);
+    // the plain row analysis (flop bound, span, symbolic bin of every row,
+    // the B-row statistics the features need), then the classification
+    timer_begin(h->timer, s, "learned_analyze");
+    const long long avg = (long long)av.nnz / m;
+    if (avg <= 8)
+      launch_analyze_a<1, 8, true>(h, av, bv, dm, s, h->d_sball.as<uint8_t>(), h->d_lstat.as<int2>());
+    else
+      launch_analyze_a<4, 8, true>(h, av, bv, dm, s, h->d_sball.as<uint8_t>(), h->d_lstat.as<int2>());
+    cudaError_t e = launch_learned_classify(
+        ctx, av, bv.n, &dm->sorted, h->opt.use_window, h->have_pred ? h->d_params.as<float>() : nullptr,
+        h->quantile, h->have_pred ? 1 : 0, h->d_flop.as<long long>(), h->d_span.as<int32_t>(),
+        h->d_lstat.as<int2>(), h->d_lbin.as<uint8_t>(), h->d_cap.as<int32_t>());
+    timer_end(h->timer, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "learned analyze");
     timer_begin(h->timer, s, "learned_plan");
     if ((st = run_scan(h, m, h->d_cap.as<int32_t>(), h->d_soff.as<int64_t>(), &dm->grand2, av, nullptr)) != KK_OK)
@@ -1856,10 +1867,8 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
       if (e != cudaSuccess) return cuda_fail(h, e, "one-pass launch");
     }
     heavy = lstart[kLearnedHeavy + 1] - lstart[kLearnedHeavy];
-    // rows left to the plain two-phase path: heavy rows and overflowed rows
-    k_sym_classify<<<grid_for(m, 256, h->num_sms * 8), 256, 0, s>>>(
-        m, h->d_flop.as<long long>(), av.rowptr, h->d_span.as<int32_t>(), &dm->sorted,
-        to_table(h->sym_bins), h->opt.team_vec_min_len, h->d_sball.as<uint8_t>());
+    // rows left to the plain two-phase path (heavy rows and overflowed rows),
+    // with the symbolic bins the analysis gave every row
     cudaError_t e = launch_learned_leftover(ctx, m, h->d_lbin.as<uint8_t>(), h->d_cnt.as<int32_t>(),
                                             h->d_plain.as<uint8_t>(), h->d_sball.as<uint8_t>(),
                                             h->d_sbin.as<uint8_t>());
@@ -2422,7 +2431,7 @@ kk_status kk_spgemm_destroy(kk_spgemm_handle h) {
   h->d_binstart.release();
   h->d_scan.release();
   h->d_bsplit.release();
-  for (DevBuf* b : {&h->d_params, &h->d_lbin, &h->d_plain, &h->d_cap, &h->d_soff, &h->d_scol,
+  for (DevBuf* b : {&h->d_params, &h->d_lbin, &h->d_plain, &h->d_cap, &h->d_lstat, &h->d_soff, &h->d_scol,
                     &h->d_sval, &h->d_sball, &h->d_nbin2, &h->d_lrows, &h->d_lrows2, &h->d_mm,
                     &h->d_bdesc, &h->d_rowpair, &h->d_bflop, &h->d_bsbin, &h->d_bnbin, &h->d_bsrows,
                     &h->d_bnrows, &h->d_bcnt, &h->d_btiles, &h->d_bstart, &h->d_bqueue, &h->d_bsplit2,
