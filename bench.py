@@ -922,7 +922,7 @@ def run_ours(args, rank, world, local_rank):
     # behind it on a copy engine.  The host link (~0.2 TB/s each way) bounds both.
     hA = {k: torch.from_numpy(np.ascontiguousarray(getattr(A, k))).pin_memory()
           for k in ("rowptr", "colind", "vals")}
-    e2e_steps = max(2, min(args.steps, 6))
+    e2e_steps = max(2, min(args.steps, 10))
     h2d = sum(t.numel() * t.element_size() for t in hA.values())
     d2h = ((A.m + 1) * 8) + nnz * 12
 
@@ -972,11 +972,15 @@ def run_ours(args, rank, world, local_rank):
             K.kk_copy_to_host(ho[1], gci, st_)
             K.kk_copy_to_host(ho[2], gva, st_)
 
-    e2e_ms = timed(piped, e2e_steps)
+    e2e_piped_ms = timed(piped, e2e_steps)
     e2e_ok = bool(torch.equal(houts[0][2][:1000], houts[1][2][:1000]))
     for h_ in pops:
         h_.close()
     del pbuf, houts, hout0
+    # the end-to-end figure is the faster of the two serving loops (both use
+    # only the public API; which one wins depends on the host link of the box)
+    e2e_mode = "two streams" if e2e_piped_ms <= e2e_serial_ms else "serial"
+    e2e_ms = min(e2e_piped_ms, e2e_serial_ms)
     e2e_value = job_gflops(madds, e2e_ms, world)
 
     forms = {}
@@ -1027,9 +1031,12 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "mode": "two streams",
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "mode": e2e_mode,
+                    "steps": e2e_steps,
                     "serial_ms_per_step": e2e_serial_ms,
                     "serial_value": job_gflops(madds, e2e_serial_ms, world),
+                    "two_streams_ms_per_step": e2e_piped_ms,
+                    "two_streams_value": job_gflops(madds, e2e_piped_ms, world),
                     "outputs_agree": e2e_ok},
             "gpu_launches": int(round(launches_per_step)) * args.steps,
             "clocks": clk,
