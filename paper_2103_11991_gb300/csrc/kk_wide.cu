@@ -735,25 +735,41 @@ k_num_wide(CsrView A, CsrView B, int32_t words, int32_t vcap, uint32_t sum_off, 
     if (total != cnt) row_bad = true;
     if (row_bad) mismatch = 1;
     __syncthreads();
-    // values: rank = prefix of the word + popc(bits below the column)
-    auto add = [&](int c, double ab) {
-      if (c >= 0 && (unsigned)c < (unsigned)(words * 32)) {
+    // values: rank = prefix of the word + popc(bits below the column); one
+    // walk per accumulator (shared memory or C), so that a product carries
+    // only its own rank lookup and add
+    auto add_smem = [&](int c, double ab) {
+      if ((unsigned)c < (unsigned)(words * 32)) {  // also skips the idle lanes' -1
         const int w = c >> 5;
         const uint32_t word = bits[w];
         if (!((word >> (c & 31)) & 1u)) {  // a column outside the (kept) structure
           mismatch = 1;
           return;
         }
-        const int below = __popc(word & ((1u << (c & 31)) - 1u));
-        const int rank = sparse ? (int)wpre16[w] + below : (int)gpre[w >> 3] + (int)wpre8[w] + below;
-        if (rank < cnt) {
-          if (sparse) atomicAdd(&vals[rank], ab);
-          else atomicAdd(&c_vals[off + rank], ab);
-        }
+        const int rank = (int)wpre16[w] + __popc(word & ((1u << (c & 31)) - 1u));
+        if (rank < cnt) atomicAdd(&vals[rank], ab);
       }
     };
-    if (lng) wide_walk_long<true>(A, B, pa, pe, walk.ls, lng, bad, add, nullptr, nullptr, i);
-    else wide_walk<true>(A, B, pa, pe, walk.ws, bad, add, i);
+    double* __restrict__ crow = c_vals + off;
+    auto add_glob = [&](int c, double ab) {
+      if ((unsigned)c < (unsigned)(words * 32)) {  // also skips the idle lanes' -1
+        const int w = c >> 5;
+        const uint32_t word = bits[w];
+        if (!((word >> (c & 31)) & 1u)) {  // a column outside the (kept) structure
+          mismatch = 1;
+          return;
+        }
+        const int rank = (int)gpre[w >> 3] + (int)wpre8[w] + __popc(word & ((1u << (c & 31)) - 1u));
+        if (rank < cnt) atomicAdd(&crow[rank], ab);
+      }
+    };
+    if (sparse) {
+      if (lng) wide_walk_long<true>(A, B, pa, pe, walk.ls, lng, bad, add_smem, nullptr, nullptr, i);
+      else wide_walk<true>(A, B, pa, pe, walk.ws, bad, add_smem, i);
+    } else {
+      if (lng) wide_walk_long<true>(A, B, pa, pe, walk.ls, lng, bad, add_glob, nullptr, nullptr, i);
+      else wide_walk<true>(A, B, pa, pe, walk.ws, bad, add_glob, i);
+    }
     if (sparse) {
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) c_vals[off + e] = vals[e];
     }
