@@ -116,6 +116,12 @@ typedef struct {
                                  (cp.async.bulk, two buffers of 256 columns per warp, mbarrier
                                  completion) instead of per-lane loads (default 0: on GB300 the
                                  per-lane loads measured faster, R-MAT scale 20 47 ms against 62) */
+  int32_t small_max_rows;     /* products with A of at most this many rows (0..8192, default 4096)
+                                 and rows of A averaging at most 32 products run each phase as one
+                                 launch of one CTA (C rows of at most 16 columns, counted and
+                                 accumulated in registers; float64 in A-row storage order); a row
+                                 with more columns sends the call to the tiered path.  Only with
+                                 force_tier = -1; 0 = never */
 } kk_spgemm_options;
 
 typedef struct kk_spgemm_handle_s* kk_spgemm_handle;
@@ -190,7 +196,10 @@ kk_status kk_spgemm_kernel_times(kk_spgemm_handle h, int32_t max_kernels, const 
  * numeric phase (options.structure_cache), stats[25] = (word, mask) pairs of
  * the compressed B it built (compare with nnz(B)); after a plain symbolic
  * call stats[26..29] = multiply-adds of the rows in each numeric tier (team,
- * CTA, dense, window), for the FP64-pipe bound; stats[30..31] = 0. */
+ * CTA, dense, window), for the FP64-pipe bound; stats[30] = rows of A when the
+ * last symbolic call took the small-product path (options.small_max_rows; the
+ * other entries are then 0 but stats[6], stats[8], stats[9]), else 0;
+ * stats[31] = 0. */
 kk_status kk_spgemm_stats(kk_spgemm_handle h, int64_t stats[32]);
 
 #ifdef __cplusplus

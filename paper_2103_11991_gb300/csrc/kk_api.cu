@@ -801,6 +801,7 @@ struct kk_spgemm_handle_s {
   void* h_pinned = nullptr;  // host staging for readbacks
   // symbolic state
   bool have_symbolic = false;
+  bool small = false;  // the last symbolic call took the small-product path (kk_small.cu)
   int32_t am = 0, an = 0, bn = 0, annz = 0, bnnz = 0;
   int64_t nnz_c = 0;
   int32_t b_sorted = 1;
@@ -852,6 +853,7 @@ struct Misc {
   unsigned long long kept;       // window rows whose structure was kept
   unsigned long long bc_pairs;   // pairs of the compressed B
   unsigned long long fp[2];      // structure fingerprints: symbolic call, numeric call
+  int32_t small_flags[4];        // small-product path: row beyond it, bad index, CTA ticket
 };
 
 kk_status fail(kk_spgemm_handle h, kk_status s, const std::string& msg) {
@@ -1290,6 +1292,7 @@ kk_status kk_spgemm_options_default(kk_spgemm_options* opt) {
   opt->wide_cache_mb = 0;
   opt->batched_mode = 0;
   opt->stage_long_rows = 0;
+  opt->small_max_rows = 4096;
   return KK_OK;
 }
 
@@ -1304,6 +1307,7 @@ kk_status kk_spgemm_handle_create(kk_spgemm_handle* out, const kk_spgemm_options
       h->opt.sym_load_pct < 10 || h->opt.sym_load_pct > 100 || h->opt.num_load_pct < 10 ||
       h->opt.num_load_pct > 50 || h->opt.structure_cache < 0 || h->opt.structure_cache > 1 || h->opt.wide_cache_mb < -1 || h->opt.batched_mode < 0 ||
       h->opt.batched_mode > 2 || h->opt.stage_long_rows < 0 || h->opt.stage_long_rows > 1 ||
+      h->opt.small_max_rows < 0 || h->opt.small_max_rows > kSmallMaxRowsCap ||
       h->opt.team_vec_min_len < 0) {
     delete h;
     return KK_ERR_INVALID_ARG;
@@ -1386,6 +1390,46 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   KK_CUDA(h, cudaMemcpyAsync(dm, &init, sizeof(Misc), cudaMemcpyHostToDevice, s), "init");
   // NOTE: &init is pageable; cudaMemcpyAsync from pageable memory is staged
   // synchronously with respect to the host, so the stack copy is safe.
+
+  // Small products: one launch counts every row and scans the counts
+  // (small_flags: a row beyond the path, a bad index; grand / grand2: nnz(C)
+  // and the multiply-adds); a row beyond the path sends the call on to the
+  // tiered path below.
+  h->small = false;
+  if (m > 0 && m <= h->opt.small_max_rows && h->opt.force_tier == -1 &&
+      (long long)av.nnz * (long long)bv.nnz <=
+          (long long)kSmallMaxMeanFlop * (long long)m * (long long)(bv.m > 0 ? bv.m : 1)) {
+    timer_begin(h->timer, s, "small_symbolic");
+    cudaError_t e = launch_small_symbolic(ctx_of(h), av, bv, c_rowptr, h->d_cnt.as<int32_t>(), dm->small_flags,
+                                          &dm->grand);
+    timer_end(h->timer, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "small symbolic launch");
+    KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
+    KK_CUDA(h, cudaStreamSynchronize(s), "sync");
+    if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
+    if (hm->small_flags[1]) return fail(h, KK_ERR_BAD_INDEX, "a row pointer or column index of A or B is out of range");
+    if (!hm->small_flags[0]) {
+      for (int k = 0; k < 32; ++k) h->stats[k] = 0;
+      h->stats[6] = (int64_t)hm->grand2;
+      h->stats[8] = 1;
+      h->stats[30] = m;
+      h->small = true;
+      h->cache_valid = false;
+      h->keep = WideKeep{nullptr, nullptr, nullptr, 0, 0};
+      h->keep_valid = false;
+      h->learned_valid = false;
+      h->nnz_c = hm->grand;
+      h->am = m;
+      h->an = A->n;
+      h->bn = B->n;
+      h->annz = A->nnz;
+      h->bnnz = B->nnz;
+      h->have_symbolic = true;
+      *nnz_c = h->nnz_c;
+      return KK_OK;
+    }
+    KK_CUDA(h, cudaMemcpyAsync(dm, &init, sizeof(Misc), cudaMemcpyHostToDevice, s), "init");
+  }
 
   int32_t* sym_start = h->d_binstart.as<int32_t>();
   int32_t* num_start = sym_start + (kMaxBins + 1);
@@ -1523,6 +1567,16 @@ static kk_status numeric_impl(kk_spgemm_handle h, const kk_csr* A, const kk_csr*
   const CsrView bv = view(B);
   cudaStream_t s = h->stream;
   Misc* dm = h->d_misc.as<Misc>();
+  if (h->small) {  // after a small-path symbolic call: one launch, float64
+    h->last_arith = kArithF64;
+    if (h->am == 0 || h->nnz_c == 0) return KK_OK;
+    timer_begin(h->timer, s, "small_numeric");
+    cudaError_t e = launch_small_numeric(ctx_of(h), av, bv, c_rowptr, c_colind, c_vals);
+    timer_end(h->timer, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "small numeric launch");
+    h->stats[9] = 1;
+    return KK_OK;
+  }
   // DF32 needs B's rows strictly ascending (its error bound counts at most
   // nnz(A(i,:)) contributions per entry); otherwise the product runs in float64,
   // as does the Jacobi-fused product (its scaled values are formed in float64)
@@ -1755,6 +1809,7 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
   if (A->n != B->m) return fail(h, KK_ERR_INVALID_ARG, "A.n != B.m");
   if (!c_rowptr || !nnz_c) return fail(h, KK_ERR_INVALID_ARG, "c_rowptr / nnz_c is NULL");
   h->have_symbolic = false;
+  h->small = false;
   h->learned_valid = false;
   h->keep = WideKeep{nullptr, nullptr, nullptr, 0, 0};
   h->keep_valid = false;
@@ -2181,6 +2236,7 @@ kk_status kk_spgemm_batched_symbolic(kk_spgemm_handle h, int32_t count, const kk
     return fail(h, KK_ERR_INVALID_ARG, "bad batch arguments");
   h->b_valid = false;
   h->have_symbolic = false;
+  h->small = false;
   h->learned_valid = false;
   kk_status st;
   long long R = 0, nnzb = 0;

@@ -89,6 +89,15 @@ __host__ __device__ constexpr int32_t stat_tier(int32_t t) { return t == kTierTh
 constexpr int kThreadSymMax = 16;     // symbolic rows: flop bound <= this
 constexpr int kThreadNumMax = 8;      // numeric rows: nnz(C(i,:)) <= this ...
 constexpr int kThreadNumMaxFlop = 16; // ... and flop bound <= this
+// Small products (kk_small.cu): one launch per phase, a thread per row, for A
+// with at most options.small_max_rows rows (at most kSmallMaxRowsCap), C rows
+// of at most kSmallN columns, tried when A's rows average at most
+// kSmallMaxMeanFlop products.
+constexpr int kSmallThreads = 256;     // symbolic CTA
+constexpr int kSmallNumThreads = 64;   // numeric CTA (more CTAs for a few thousand rows)
+constexpr int kSmallMaxRowsCap = 8192;
+constexpr int kSmallN = 16;
+constexpr int kSmallMaxMeanFlop = 32;
 
 // Window tier: a row whose columns of C all lie in [row_lo, row_lo + W) gets a
 // dense bit vector of W bits (plus per-word ranks in the numeric phase).
@@ -203,6 +212,10 @@ cudaError_t launch_numeric_wide(const LaunchCtx& ctx, const CsrView& A, const Cs
 
 cudaError_t launch_symbolic_thread(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
                                    const int32_t* rows, int32_t nrows, int32_t* cnt);
+cudaError_t launch_small_symbolic(const LaunchCtx& ctx, const CsrView& A, const CsrView& B, int64_t* c_rowptr,
+                                  int32_t* cnt, int32_t* flags, long long* out);
+cudaError_t launch_small_numeric(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
+                                 const int64_t* c_rowptr, int32_t* c_colind, double* c_vals);
 cudaError_t launch_numeric_thread(const LaunchCtx& ctx, const CsrView& A, const CsrView& B,
                                   const int64_t* c_rowptr, const int32_t* rows, int32_t nrows,
                                   int32_t* c_colind, double* c_vals);

@@ -52,7 +52,8 @@ class KkOptions(ctypes.Structure):
                 ("batched_graph", ctypes.c_int32), ("sym_load_pct", ctypes.c_int32),
                 ("num_load_pct", ctypes.c_int32), ("structure_cache", ctypes.c_int32),
                 ("wide_cache_mb", ctypes.c_int32), ("batched_mode", ctypes.c_int32),
-                ("batched_learned", ctypes.c_int32), ("stage_long_rows", ctypes.c_int32)]
+                ("batched_learned", ctypes.c_int32), ("stage_long_rows", ctypes.c_int32),
+                ("small_max_rows", ctypes.c_int32)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -261,7 +262,8 @@ def kk_spgemm_stats(h) -> dict:
             "sym_window_rows", "num_window_rows", "onepass_rows", "overflow_rows", "heavy_rows",
             "staging_entries", "num_team_c", "num_cta_c", "num_dense_c", "num_window_c",
             "num_team_a", "num_cta_a", "num_dense_a", "num_window_a", "kept_structure_rows",
-            "compressed_b_pairs", "num_team_f", "num_cta_f", "num_dense_f", "num_window_f"]
+            "compressed_b_pairs", "num_team_f", "num_cta_f", "num_dense_f", "num_window_f",
+            "small_path_rows"]
     return {k: int(arr[i]) for i, k in enumerate(keys)}
 
 
