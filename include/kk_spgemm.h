@@ -66,7 +66,9 @@ typedef struct {
 
 /* Arithmetic of the numeric phase's accumulator. */
 typedef enum {
-  KK_ARITH_AUTO = 0,  /* DF32 where every value's exponent fits its safe range, FP64 otherwise */
+  KK_ARITH_AUTO = 0,  /* DF32 where every value's exponent fits its safe range and the row's
+                         error bound holds, FP64 otherwise; the window tier's rows of at most 256
+                         columns run in FP64 (measured faster there on GB300) */
   KK_ARITH_FP64 = 1,  /* native float64 fused multiply-add in storage order */
   KK_ARITH_DF32 = 2   /* float64 emulated as an unevaluated pair of float32 on the FP32 pipe */
 } kk_arith;

@@ -984,7 +984,7 @@ BinTable to_table(const std::vector<BinSpec>& bins) {
 LaunchCtx ctx_of(kk_spgemm_handle h) {
   return LaunchCtx{h->stream, h->timer, &h->d_misc.as<Misc>()->status, h->num_sms, h->max_smem,
                    h->d_rowlo.as<int32_t>(), h->d_flop.as<long long>(), h->keep, h->opt.debug_checks,
-                   h->opt.stage_long_rows, nullptr};
+                   h->opt.stage_long_rows, nullptr, h->opt.arith == KK_ARITH_AUTO ? 1 : 0};
 }
 
 // Analysis of B at the start of a symbolic call; with the window tier on, the

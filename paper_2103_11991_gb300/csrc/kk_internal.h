@@ -38,6 +38,11 @@ struct LaunchCtx {
   // structure fingerprints of the index arrays at the symbolic call ([0]) and
   // at this numeric call ([1]); null when the kept structure is not in use
   const unsigned long long* fingerprint;
+  // 1: the window tier's rows of at most kWindowMaxNnz columns (the
+  // kept-structure value pass and its rebuild) run in float64 whatever the
+  // call's arithmetic (options.arith = AUTO: on GB300 native float64 measured
+  // faster there, 1.91 ms against 2.42 for the 27-point value pass)
+  int kept_f64;
 };
 
 struct CsrView {

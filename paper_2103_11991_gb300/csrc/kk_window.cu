@@ -1052,6 +1052,10 @@ cudaError_t launch_numeric_window(const LaunchCtx& ctx, const BinSpec& bin, cons
     timer_end(ctx.timer, ctx.stream);
     return e;
   }
+  // rows of at most kWindowMaxNnz columns: with the automatic arithmetic in
+  // float64, whether the kept structure or the rebuild serves them (so that a
+  // row's values do not depend on which one did)
+  if (ctx.kept_f64) arith = kArithF64;
   const int32_t* wrows = rows;
   const int32_t* wcount = nullptr;
   if (cache.n && scratch.rows) {

@@ -159,3 +159,15 @@ def test_large_value_window_bins(n, lens, arith):
     if lens[0] >= 24:
         assert (per_row > 512).any()
     check_against_oracle(A, B, rp, ci, va)
+
+
+def test_automatic_arithmetic_runs_the_kept_pass_in_float64():
+    """With options.arith = AUTO the kept-structure value pass runs in float64
+    (on this part faster than DF32 there) while other tiers may take DF32: on a
+    27-point stencil with random values, where every row keeps its structure,
+    the result equals the oracle bit for bit (float64 in A-row storage order)."""
+    A0 = I.stencil_3d(18, 18, 18, 27, 26.0, -1.0)
+    A = I.ensure_csr(A0.m, A0.n, A0.rowptr, A0.colind, I.uniform01(7, "auto.vals", A0.nnz) * 2 - 1)
+    rp, ci, va, _, st = run_gpu(A, A, arith=0)
+    assert st["kept_structure_rows"] == A.m
+    check_against_oracle(A, A, rp, ci, va, exact=True)
