@@ -531,7 +531,7 @@ TierOfBin tier_of_bins(const std::vector<BinSpec>& bins) {
 
 // ---------------------------------------------------------------------------
 // Structure fingerprint: a 64-bit sum over the elements of the index arrays
-// (A's and B's row pointers and columns) of a mix of (value, position, array),
+// (A's and B's row pointers and columns) of a term of (value, position, array),
 // order-independent so blocks add their parts atomically.  The symbolic call
 // that keeps window structure records it; a numeric call that uses that
 // structure recomputes it, and a difference (index arrays changed in place
@@ -542,14 +542,13 @@ struct FpArrays {
   long long n[4];
 };
 
+// The term of element x at position i of array a: x XORed with a value of
+// (i, a), times an odd constant.  For a fixed position it is a bijection of x,
+// and the terms are summed as 32-bit values into 64 bits (no wrap below 2^32
+// elements), so changing any one element always changes the sum; three
+// integer operations per element keep the pass at memory speed.
 __device__ __forceinline__ unsigned long long fp_mix(uint32_t x, uint32_t i, uint32_t a) {
-  uint32_t h = x * 0x9E3779B1u + (i ^ (a << 29)) * 0x85EBCA77u + a;
-  h ^= h >> 16;
-  h *= 0x7FEB352Du;
-  h ^= h >> 15;
-  h *= 0x846CA68Bu;
-  h ^= h >> 16;
-  return (unsigned long long)h * 0xD6E8FEB86659FD93ull;
+  return (unsigned long long)((x ^ (i * 0x9E3779B1u + a * 0x7F4A7C15u)) * 0x85EBCA6Bu);
 }
 
 // blockIdx.y = the array.  The aligned middle of the array is read as int4 with
