@@ -1856,7 +1856,8 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
     else
       launch_analyze_a<4, 8, true>(h, av, bv, dm, s, h->d_sball.as<uint8_t>(), h->d_lstat.as<int2>());
     cudaError_t e = launch_learned_classify(
-        ctx, av, bv.n, &dm->sorted, h->opt.use_window, h->have_pred ? h->d_params.as<float>() : nullptr,
+        ctx, av, bv.n, &dm->sorted, h->opt.use_window, h->opt.structure_cache ? 0 : 1,
+        h->have_pred ? h->d_params.as<float>() : nullptr,
         h->quantile, h->have_pred ? 1 : 0, h->d_flop.as<long long>(), h->d_span.as<int32_t>(),
         h->d_lstat.as<int2>(), h->d_lbin.as<uint8_t>(), h->d_cap.as<int32_t>());
     timer_end(h->timer, s);

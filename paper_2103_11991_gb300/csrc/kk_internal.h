@@ -262,7 +262,8 @@ cudaError_t launch_onepass_table(const LaunchCtx& ctx, const CsrView& A, const C
                                  const int32_t* cap, const int32_t* rows, int32_t nrows,
                                  int32_t* scol, double* sval, int32_t* cnt_out);
 cudaError_t launch_learned_classify(const LaunchCtx& ctx, const CsrView& A, int32_t bn,
-                                    const int32_t* b_sorted, int32_t use_window, const float* params,
+                                    const int32_t* b_sorted, int32_t use_window, int32_t window_onepass,
+                                    const float* params,
                                     float quantile, int32_t use_pred, const long long* flop,
                                     const int32_t* row_span, const int2* stat, uint8_t* lbin, int32_t* cap);
 cudaError_t launch_learned_leftover(const LaunchCtx& ctx, int32_t m, const uint8_t* lbin,

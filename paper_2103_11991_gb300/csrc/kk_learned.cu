@@ -19,6 +19,7 @@ constexpr int kLearnedBlock = 256;
 // kLearnedHeavy = heavy (plain path), 0xFF = no products.
 __global__ void __launch_bounds__(kLearnedBlock)
 k_learned_classify(CsrView A, int32_t bn, const int32_t* __restrict__ b_sorted, int32_t use_window,
+                   int32_t window_onepass,
                    const float* __restrict__ params, float quantile, int32_t use_pred,
                    const long long* __restrict__ flop, const int32_t* __restrict__ row_span,
                    const int2* __restrict__ stat, uint8_t* __restrict__ lbin, int32_t* __restrict__ cap) {
@@ -60,7 +61,10 @@ k_learned_classify(CsrView A, int32_t bn, const int32_t* __restrict__ b_sorted, 
       lb = (uint8_t)c;  // warp hash one-pass
       for (int w = 0; use_window && w < kNumWindowClasses; ++w) {  // needs B_C
         if (span <= window_bits(w) && (long long)window_bits(w) <= (long long)kWindowFlopRatio * f) {
-          lb = (uint8_t)(kOnepassClasses + w);  // window one-pass
+          // window one-pass; with the structure cache on, the plain path
+          // instead (its numeric phase is then the value pass alone, which
+          // the one-pass measured slower than)
+          lb = (uint8_t)(window_onepass ? kOnepassClasses + w : kLearnedHeavy);
           break;
         }
       }
@@ -122,12 +126,13 @@ int grid1(long long n, int block, int cap) {
 }  // namespace
 
 cudaError_t launch_learned_classify(const LaunchCtx& ctx, const CsrView& A, int32_t bn,
-                                    const int32_t* b_sorted, int32_t use_window, const float* params,
+                                    const int32_t* b_sorted, int32_t use_window, int32_t window_onepass,
+                                    const float* params,
                                     float quantile, int32_t use_pred, const long long* flop,
                                     const int32_t* row_span, const int2* stat, uint8_t* lbin, int32_t* cap) {
   if (A.m <= 0) return cudaSuccess;
   k_learned_classify<<<grid1(A.m, kLearnedBlock, ctx.num_sms * 8), kLearnedBlock, 0, ctx.stream>>>(
-      A, bn, b_sorted, use_window, params, quantile, use_pred, flop, row_span, stat, lbin, cap);
+      A, bn, b_sorted, use_window, window_onepass, params, quantile, use_pred, flop, row_span, stat, lbin, cap);
   return cudaGetLastError();
 }
 
