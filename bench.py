@@ -973,14 +973,29 @@ def run_ours(args, rank, world, local_rank):
             K.kk_copy_to_host(ho[2], gva, st_)
 
     e2e_piped_ms = timed(piped, e2e_steps)
+
+    def piped_ce(k):
+        # the same loop with C downloaded by the copy engines (the library's
+        # small read-backs go through a kernel, so they do not queue behind it)
+        st_, h_, (dci, dva), ho = streams[k % 2], pops[k % 2], pbuf[k % 2], houts[k % 2]
+        with torch.cuda.stream(st_):
+            gA = upload()
+            grp, gnnz = h_.symbolic(gA, gA)
+            gci, gva = h_.numeric(gA, gA, grp, gnnz, dci, dva)
+            ho[0].copy_(grp, non_blocking=True)
+            ho[1].copy_(gci, non_blocking=True)
+            ho[2].copy_(gva, non_blocking=True)
+
+    e2e_ce_ms = timed(piped_ce, e2e_steps)
     e2e_ok = bool(torch.equal(houts[0][2][:1000], houts[1][2][:1000]))
     for h_ in pops:
         h_.close()
     del pbuf, houts, hout0
-    # the end-to-end figure is the faster of the two serving loops (both use
-    # only the public API; which one wins depends on the host link of the box)
-    e2e_mode = "two streams" if e2e_piped_ms <= e2e_serial_ms else "serial"
-    e2e_ms = min(e2e_piped_ms, e2e_serial_ms)
+    # the end-to-end figure is the fastest of the serving loops (all use only
+    # the public API; which one wins depends on the host link of the box)
+    loops = {"two streams": e2e_piped_ms, "two streams, copy engines": e2e_ce_ms, "serial": e2e_serial_ms}
+    e2e_mode = min(loops, key=loops.get)
+    e2e_ms = loops[e2e_mode]
     e2e_value = job_gflops(madds, e2e_ms, world)
 
     forms = {}
@@ -1037,6 +1052,8 @@ def run_ours(args, rank, world, local_rank):
                     "serial_value": job_gflops(madds, e2e_serial_ms, world),
                     "two_streams_ms_per_step": e2e_piped_ms,
                     "two_streams_value": job_gflops(madds, e2e_piped_ms, world),
+                    "two_streams_copy_engines_ms_per_step": e2e_ce_ms,
+                    "two_streams_copy_engines_value": job_gflops(madds, e2e_ce_ms, world),
                     "outputs_agree": e2e_ok},
             "gpu_launches": int(round(launches_per_step)) * args.steps,
             "clocks": clk,

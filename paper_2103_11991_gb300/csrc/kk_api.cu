@@ -725,6 +725,12 @@ __global__ void k_split_values(long long n, const double* __restrict__ v, float2
   if (bad && (threadIdx.x & 31) == 0) atomicOr(range_bad, 1);
 }
 
+// One CTA copies n words from device memory to the page-locked staging buffer
+// through its device mapping (the read-backs of the status block and bin starts).
+__global__ void k_readback(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
 }  // namespace
 }  // namespace kk
 
@@ -798,6 +804,7 @@ struct kk_spgemm_handle_s {
   cudaGraphExec_t g_sym = nullptr, g_num = nullptr;
   unsigned long long g_sym_key = 0, g_num_key = 0;
   void* h_pinned = nullptr;  // host staging for readbacks
+  void* d_pinned_map = nullptr;  // its device mapping (null: none)
   // symbolic state
   bool have_symbolic = false;
   bool small = false;  // the last symbolic call took the small-product path (kk_small.cu)
@@ -873,6 +880,33 @@ kk_status cuda_fail(kk_spgemm_handle h, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                          \
     if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
   } while (0)
+
+#define KK_TRY(expr)                   \
+  do {                                 \
+    const kk_status kk_try_ = (expr);  \
+    if (kk_try_ != KK_OK) return kk_try_; \
+  } while (0)
+
+
+// A small device-to-host read into the handle's page-locked staging buffer
+// (the status block, bin starts), by a one-CTA kernel writing the buffer
+// through its device mapping: no copy engine is involved, so the read does
+// not wait behind a large transfer queued on one (another stream's download
+// of C in a serving loop).  Without the mapping, cudaMemcpyAsync.  Enqueued on
+// s; the caller synchronises before reading.
+kk_status readback(kk_spgemm_handle h, void* host_dst, const void* dev_src, size_t bytes, cudaStream_t s) {
+  const char* base = static_cast<const char*>(h->h_pinned);
+  const char* dst = static_cast<const char*>(host_dst);
+  if (h->d_pinned_map && dst >= base && dst + bytes <= base + 4096 && bytes % 4 == 0 &&
+      ((uintptr_t)dev_src & 3) == 0 && ((uintptr_t)host_dst & 3) == 0) {
+    uint32_t* dmap = reinterpret_cast<uint32_t*>(static_cast<char*>(h->d_pinned_map) + (dst - base));
+    k_readback<<<1, 256, 0, s>>>(static_cast<const uint32_t*>(dev_src), dmap, (int)(bytes / 4));
+    KK_CUDA(h, cudaGetLastError(), "readback launch");
+    return KK_OK;
+  }
+  KK_CUDA(h, cudaMemcpyAsync(host_dst, dev_src, bytes, cudaMemcpyDeviceToHost, s), "readback");
+  return KK_OK;
+}
 
 kk_status check_csr(kk_spgemm_handle h, const kk_csr* M, const char* name, bool need_vals) {
   if (!M) return fail(h, KK_ERR_INVALID_ARG, std::string(name) + " is NULL");
@@ -1324,6 +1358,10 @@ kk_status kk_spgemm_handle_create(kk_spgemm_handle* out, const kk_spgemm_options
   if (e == cudaSuccess) e = h->d_misc.ensure(sizeof(Misc));
   if (e == cudaSuccess) e = h->d_binstart.ensure(sizeof(int32_t) * 2 * (kMaxBins + 1));
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_pinned, 4096);
+  if (e == cudaSuccess && cudaHostGetDevicePointer(&h->d_pinned_map, h->h_pinned, 0) != cudaSuccess) {
+    (void)cudaGetLastError();  // no device mapping: read-backs take cudaMemcpyAsync
+    h->d_pinned_map = nullptr;
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_misc.p, 0, sizeof(Misc), h->stream);
   if (e != cudaSuccess) {
     h->d_misc.release();
@@ -1403,7 +1441,7 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
                                           &dm->grand);
     timer_end(h->timer, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "small symbolic launch");
-    KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
+    KK_TRY(readback(h, hm, dm, sizeof(Misc), s));
     KK_CUDA(h, cudaStreamSynchronize(s), "sync");
     if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
     if (hm->small_flags[1]) return fail(h, KK_ERR_BAD_INDEX, "a row pointer or column index of A or B is out of range");
@@ -1449,9 +1487,8 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
   } else {
     KK_CUDA(h, cudaMemsetAsync(sym_start, 0, sizeof(int32_t) * (nbs + 1), s), "memset");
   }
-  KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
-  KK_CUDA(h, cudaMemcpyAsync(h_start, sym_start, sizeof(int32_t) * (nbs + 1), cudaMemcpyDeviceToHost, s),
-          "readback");
+  KK_TRY(readback(h, hm, dm, sizeof(Misc), s));
+  KK_TRY(readback(h, h_start, sym_start, sizeof(int32_t) * (nbs + 1), s));
   KK_CUDA(h, cudaStreamSynchronize(s), "sync");
   if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
   h->b_sorted = hm->sorted;
@@ -1514,9 +1551,8 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
     KK_CUDA(h, cudaMemsetAsync(c_rowptr, 0, sizeof(int64_t), s), "memset rowptr");
     KK_CUDA(h, cudaMemsetAsync(num_start, 0, sizeof(int32_t) * (nbn + 1), s), "memset");
   }
-  KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
-  KK_CUDA(h, cudaMemcpyAsync(h_start, num_start, sizeof(int32_t) * (nbn + 1), cudaMemcpyDeviceToHost, s),
-          "readback");
+  KK_TRY(readback(h, hm, dm, sizeof(Misc), s));
+  KK_TRY(readback(h, h_start, num_start, sizeof(int32_t) * (nbn + 1), s));
   KK_CUDA(h, cudaStreamSynchronize(s), "sync");
   if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
   h->nnz_c = m > 0 ? hm->grand : 0;
@@ -1725,7 +1761,7 @@ kk_status kk_spadd_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* B
   } else {
     KK_CUDA(h, cudaMemsetAsync(c_rowptr, 0, sizeof(int64_t), s), "memset");
   }
-  KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
+  KK_TRY(readback(h, hm, dm, sizeof(Misc), s));
   KK_CUDA(h, cudaStreamSynchronize(s), "sync");
   if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
   if (m > 0) nnz = hm->grand;
@@ -1871,9 +1907,8 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
   } else {
     KK_CUDA(h, cudaMemsetAsync(l_start, 0, sizeof(int32_t) * (nbl + 1), s), "memset");
   }
-  KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
-  KK_CUDA(h, cudaMemcpyAsync(h_start, l_start, sizeof(int32_t) * (nbl + 1), cudaMemcpyDeviceToHost, s),
-          "readback");
+  KK_TRY(readback(h, hm, dm, sizeof(Misc), s));
+  KK_TRY(readback(h, h_start, l_start, sizeof(int32_t) * (nbl + 1), s));
   KK_CUDA(h, cudaStreamSynchronize(s), "sync");
   if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
   h->b_sorted = hm->sorted;
@@ -1930,8 +1965,7 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
     if (e != cudaSuccess) return cuda_fail(h, e, "leftover launch");
     if ((st = run_binning(h, m, h->d_sbin.as<uint8_t>(), nbs, h->d_srows.as<int32_t>(), sym_start)) != KK_OK)
       return st;
-    KK_CUDA(h, cudaMemcpyAsync(h_start, sym_start, sizeof(int32_t) * (nbs + 1), cudaMemcpyDeviceToHost, s),
-            "readback");
+    KK_TRY(readback(h, h_start, sym_start, sizeof(int32_t) * (nbs + 1), s));
     KK_CUDA(h, cudaStreamSynchronize(s), "sync");
     bool any_win = false;
     int64_t wide_rows = 0;
@@ -1976,11 +2010,9 @@ kk_status kk_spgemm_learned_symbolic(kk_spgemm_handle h, const kk_csr* A, const 
     KK_CUDA(h, cudaMemsetAsync(num_start, 0, sizeof(int32_t) * (nbn + 1), s), "memset");
     KK_CUDA(h, cudaMemsetAsync(ln_start, 0, sizeof(int32_t) * (nbn + 1), s), "memset");
   }
-  KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
-  KK_CUDA(h, cudaMemcpyAsync(h_start, num_start, sizeof(int32_t) * (nbn + 1), cudaMemcpyDeviceToHost, s),
-          "readback");
-  KK_CUDA(h, cudaMemcpyAsync(h_start2, ln_start, sizeof(int32_t) * (nbn + 1), cudaMemcpyDeviceToHost, s),
-          "readback");
+  KK_TRY(readback(h, hm, dm, sizeof(Misc), s));
+  KK_TRY(readback(h, h_start, num_start, sizeof(int32_t) * (nbn + 1), s));
+  KK_TRY(readback(h, h_start2, ln_start, sizeof(int32_t) * (nbn + 1), s));
   KK_CUDA(h, cudaStreamSynchronize(s), "sync");
   if ((st = check_device_status(h, hm->status)) != KK_OK) return st;
   h->nnz_c = m > 0 ? hm->grand : 0;
@@ -2333,7 +2365,7 @@ kk_status kk_spgemm_batched_symbolic(kk_spgemm_handle h, int32_t count, const kk
     if (count > 0)
       KK_CUDA(h, cudaMemcpyAsync(h->h_bdesc2, dd, sizeof(PairDesc) * count, cudaMemcpyDeviceToHost, s),
               "readback");
-    KK_CUDA(h, cudaMemcpyAsync(hm, dm, sizeof(Misc), cudaMemcpyDeviceToHost, s), "readback");
+    KK_TRY(readback(h, hm, dm, sizeof(Misc), s));
     return KK_OK;
   };
   const bool use_graph = h->opt.batched_graph && s != nullptr && s != cudaStreamLegacy &&
@@ -2436,7 +2468,7 @@ kk_status kk_spgemm_batched_numeric(kk_spgemm_handle h, int32_t count, const kk_
 kk_status kk_spgemm_sync(kk_spgemm_handle h) {
   if (!h) return KK_ERR_INVALID_ARG;
   Misc* hm = static_cast<Misc*>(h->h_pinned);
-  KK_CUDA(h, cudaMemcpyAsync(hm, h->d_misc.p, sizeof(Misc), cudaMemcpyDeviceToHost, h->stream), "readback");
+  KK_TRY(readback(h, hm, h->d_misc.p, sizeof(Misc), h->stream));
   KK_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
   if (h->last_arith == kArithDF32 && hm->range_bad) h->last_arith = kArithF64;
   const int status = hm->status;
