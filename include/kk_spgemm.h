@@ -78,7 +78,8 @@ typedef enum {
 typedef struct {
   int32_t arith;          /* kk_arith */
   int32_t debug_checks;   /* 1: extra device-side consistency checks in numeric */
-  int32_t timing;         /* 1: record CUDA events around every kernel (see kk_spgemm_kernel_times) */
+  int32_t timing;         /* 1: record CUDA events around every kernel (see kk_spgemm_kernel_times)
+                             and count the per-tier statistics (kk_spgemm_stats) */
   int32_t force_tier;     /* testing: -1 = automatic; 0 = team hash, 1 = CTA hash, 2 = dense chunks,
                              3 = window wherever a row qualifies (team hash elsewhere) */
   int32_t team_vec_min_len; /* mean B-row length from which a team walks B rows lane-parallel (else flattened) */
@@ -191,14 +192,15 @@ kk_status kk_spgemm_kernel_times(kk_spgemm_handle h, int32_t max_kernels, const 
  * the symbolic / numeric phase; after a learned symbolic call (kk_learned.h)
  * stats[12] = rows sent to the speculative one-pass, stats[13] = of those, rows
  * that overflowed and were re-run, stats[14] = rows predicted heavy (plain
- * path), stats[15] = staging entries; after a plain symbolic call
- * stats[16..19] = C entries and stats[20..23] = A entries of the rows in each
- * numeric tier (team, CTA, dense, window), for per-kernel byte accounting;
+ * path), stats[15] = staging entries; after a plain symbolic call on a handle
+ * with options.timing = 1 (else 0): stats[16..19] = C entries and
+ * stats[20..23] = A entries of the rows in each numeric tier (team, CTA,
+ * dense, window), for per-kernel byte accounting;
  * stats[24] = window rows whose structure the last symbolic call kept for the
  * numeric phase (options.structure_cache), stats[25] = (word, mask) pairs of
- * the compressed B it built (compare with nnz(B)); after a plain symbolic
- * call stats[26..29] = multiply-adds of the rows in each numeric tier (team,
- * CTA, dense, window), for the FP64-pipe bound; stats[30] = rows of A when the
+ * the compressed B it built (compare with nnz(B)); with options.timing = 1,
+ * after a plain symbolic call stats[26..29] = multiply-adds of the rows in each
+ * numeric tier (team, CTA, dense, window), for the FP64-pipe bound; stats[30] = rows of A when the
  * last symbolic call took the small-product path (options.small_max_rows; the
  * other entries are then 0 but stats[6], stats[8], stats[9]), else 0;
  * stats[31] = 0. */

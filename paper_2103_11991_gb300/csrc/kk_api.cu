@@ -1531,7 +1531,7 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
     int64_t nb_launched = 0;
     for (int b = 0; b < nbs; ++b) nb_launched += (h_start[b + 1] - h_start[b]) > 0 ? 1 : 0;
     // analyze (2) + binning (3) + symbolic bins + scan (3) + numeric binning (3)
-    h->stats[8] = (bv.m > 0 ? 1 : 0) + 1 + 3 + nb_launched + 3 + 3 + 1;
+    h->stats[8] = (bv.m > 0 ? 1 : 0) + 1 + 3 + nb_launched + 3 + 3 + (h->opt.timing ? 1 : 0);
     // scan + numeric bins
     timer_begin(h->timer, s, "scan");
     k_scan_partial<<<nblk_scan, kScanBlock, 0, s>>>(m, h->d_cnt.as<int32_t>(), h->d_scan.as<long long>());
@@ -1544,9 +1544,12 @@ kk_status kk_spgemm_symbolic(kk_spgemm_handle h, const kk_csr* A, const kk_csr* 
     KK_CUDA(h, cudaGetLastError(), "scan launch");
     if ((st = run_binning(h, m, h->d_nbin.as<uint8_t>(), nbn, h->d_nrows.as<int32_t>(), num_start)) != KK_OK)
       return st;
-    k_tier_sums<<<grid_for(m, 256, h->num_sms * 8), 256, 0, s>>>(
-        m, h->d_nbin.as<uint8_t>(), c_rowptr, av.rowptr, h->d_flop.as<long long>(), tier_of_bins(h->num_bins),
-        dm->tier_c, dm->tier_a, dm->tier_f);
+    // per-tier C entries, A entries and multiply-adds (statistics for
+    // per-kernel accounting): only on a handle that times its kernels
+    if (h->opt.timing)
+      k_tier_sums<<<grid_for(m, 256, h->num_sms * 8), 256, 0, s>>>(
+          m, h->d_nbin.as<uint8_t>(), c_rowptr, av.rowptr, h->d_flop.as<long long>(), tier_of_bins(h->num_bins),
+          dm->tier_c, dm->tier_a, dm->tier_f);
   } else {
     KK_CUDA(h, cudaMemsetAsync(c_rowptr, 0, sizeof(int64_t), s), "memset rowptr");
     KK_CUDA(h, cudaMemsetAsync(num_start, 0, sizeof(int32_t) * (nbn + 1), s), "memset");
